@@ -1,0 +1,167 @@
+"""Pins of the whole oracle step against closed forms and invariants of the
+method (Sections 2, 5 and 6 of the paper):
+
+* constant preservation for divergence-free drift and any D;
+* the conditionally exact translate: with constant u and D every sample is
+  phi0(x - X^s), X^s = u t + sqrt(2D) sum dW^s (one Wiener increment per
+  sample per step, Section 5.2), with spectral (exponential) convergence in N;
+* the translating, spreading Gaussian mean (Eq. conv-diffusion) within the
+  Monte-Carlo standard error;
+* the paper's 1D sine diffusion test (Section 6.1) and its mass conservation;
+* conservation of the element-integrated mean for the divergence form with
+  non-constant drift;
+* the time-step condition (Eq. 1d_timestep) and the moment bookkeeping.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import sl_inputs as I
+
+
+def _mass(orc, pb, field):
+    w = orc.quad_weights(pb["N"])
+    if pb["dim"] == 1:
+        h = (pb["hi"][0] - pb["lo"][0]) / pb["K"][0]
+        return float((field @ w).sum() * h)
+    W = np.outer(w, w).ravel()
+    h = (pb["hi"][0] - pb["lo"][0]) / pb["K"][0] * (pb["hi"][1] - pb["lo"][1]) / pb["K"][1]
+    return float((field @ W).sum() * h)
+
+
+def test_constant_preserved_1d(orc):
+    pb = I.problem(1, (6,), (0.0,), (2.0,), 7, 5, 30, 2e-4, 3, ("const", [0.8, 0.0]),
+                   ("cos", [0.02, 0.5, 1.0]), ("sine", [1.7, 0.0, 1.0]))
+    r = orc.run(pb, ns=5, want_states=True)
+    assert np.max(np.abs(r["states"] - 1.7)) < 1e-12
+
+
+def test_constant_preserved_2d(orc):
+    pb = I.problem(2, (3, 3), (0.0, 0.0), (1.0, 1.0), 4, 2, 4, 1e-4, 3,
+                   ("rotation", [2 * np.pi, 0.5, 0.5]), ("sinsin", [0.005, 0.3, 2.0, 2.0]),
+                   ("sinsin", [1.3, 0.0, 1.0]))
+    r = orc.run(pb, ns=2, want_states=True)
+    assert np.max(np.abs(r["states"] - 1.3)) < 1e-11
+
+
+def _translate_error(orc, pb, ns, steps):
+    r = orc.run(pb, nsteps=steps, ns=ns, want_states=True)
+    x, _ = orc.node_coords(pb)
+    dW = orc.wiener(pb["seed"], 1, ns, 0, steps, pb["dt"])
+    u = pb["drift"][1][0]
+    D = pb["diffusion"][1][0]
+    amp, sig, c = pb["phi0"][1][0:3]
+    L = pb["hi"][0] - pb["lo"][0]
+    err = 0.0
+    for s in range(ns):
+        X = u * pb["dt"] * steps + math.sqrt(2 * D) * dW[:, s, 0].sum()
+        ex = sum(amp * np.exp(-((x - X) - c + m * L) ** 2 / (2 * sig * sig)) for m in (-1, 0, 1))
+        err = max(err, float(np.abs(r["states"][s] - ex).max()))
+    return err
+
+
+def test_conditional_translate_spectral_convergence(orc):
+    pb = I.config1()
+    errs = [_translate_error(orc, I.with_(pb, N=N), 3, 40) for N in (4, 6, 8, 10, 12)]
+    # exponential decay: each +2 nodes gains at least a factor 4, and the
+    # N=12 sample is a translate to better than 1e-6
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 4
+    assert errs[-1] < 1e-6
+
+
+def test_gaussian_mean_within_standard_error(orc):
+    pb = I.config1()  # M=256, 100 steps
+    mean, m2 = orc.moments(pb, nthreads=4)
+    M = pb["M"]
+    var = np.maximum(m2 - mean * mean, 0.0) * M / (M - 1)
+    se = np.sqrt(var / M)
+    x, _ = orc.node_coords(pb)
+    t = pb["dt"] * pb["steps"]
+    s0, D, u = 0.1, 0.01, 1.0
+    s2 = s0 * s0 + 2 * D * t
+    exact = sum(s0 / math.sqrt(s2) * np.exp(-(x - 1.0 - u * t + m * 2.0) ** 2 / (2 * s2))
+                for m in (-1, 0, 1))
+    # spatial error at N=6 over 100 steps is ~1e-3 (see the translate test)
+    assert np.all(np.abs(mean - exact) <= 4.5 * se + 5e-3)
+    # where the pulse is (elsewhere phi ~ 1e-14 and rounding dominates the SE)
+    on = exact > 1e-2
+    z = (mean - exact)[on] / se[on]
+    assert on.sum() >= 10 and np.mean(np.abs(z) < 2.5) > 0.8
+
+
+def test_sine_diffusion_closed_form_and_mass(orc):
+    # Section 6.1: u = 0, D = 1, phi0 = 2 + sin 2 pi x on periodic [0,1],
+    # dt = 1e-5, 50 steps.  Mean -> 2 + exp(-4 pi^2 t) sin 2 pi x, mass
+    # conserved to about six decimals.
+    pb = I.sine_diffusion_1d(K=2, N=8, M=800, steps=50)
+    r = orc.run(pb, nthreads=4, want_states=False)
+    M = pb["M"]
+    mean = r["sum"] / M
+    var = np.maximum(r["sumsq"] / M - mean ** 2, 0) * M / (M - 1)
+    se = np.sqrt(var / M)
+    x, _ = orc.node_coords(pb)
+    t = pb["dt"] * pb["steps"]
+    exact = 2.0 + math.exp(-4 * math.pi ** 2 * t) * np.sin(2 * math.pi * x)
+    assert np.all(np.abs(mean - exact) <= 4.5 * se + 1e-6)
+    m0 = _mass(orc, pb, orc.init_state(pb))
+    assert abs(_mass(orc, pb, mean) - m0) / m0 < 1e-6
+
+
+def test_mass_conservation_nonconstant_drift(orc):
+    # u = 1 + 0.5 sin(pi x) with the source -phi du/dx: the mean obeys the
+    # divergence form phi_t + (u phi)_x = (D phi_x)_x, so its integral over
+    # the periodic domain is conserved.  With constant D the per-sample noise
+    # term sqrt(2D) phi_x dW also integrates to zero, so every sample
+    # conserves mass up to the spatial error, which decays spectrally in N.
+    def mass(pb, f):
+        return float((f @ orc.quad_weights(pb["N"])).sum() * 2.0 / pb["K"][0])
+
+    drifts = []
+    for N in (6, 10, 14):
+        pb = I.config2(N=N, M=8, steps=200, K=16)
+        pb["diffusion"] = ("cos", [0.01, 0.0, 1.0])
+        pb["dt"] = 0.5 * orc.dt_max(pb)
+        r = orc.run(pb, ns=8, want_states=True, nthreads=4)
+        m0 = mass(pb, orc.init_state(pb))
+        drifts.append(max(abs(mass(pb, r["states"][s]) - m0) / m0 for s in range(8)))
+    assert drifts[0] < 3e-3 and drifts[1] < 2e-4 and drifts[2] < 2e-5
+    assert drifts[2] < drifts[1] / 5 < drifts[0] / 25
+    # variable D: only the mean is conserved, to within its standard error
+    pb = I.config2(N=10, M=64, steps=200, K=16)
+    pb["dt"] = 0.5 * orc.dt_max(pb)
+    r = orc.run(pb, ns=64, want_states=True, nthreads=4)
+    m0 = mass(pb, orc.init_state(pb))
+    ms = np.array([mass(pb, r["states"][s]) for s in range(64)])
+    assert abs(ms.mean() - m0) < 4 * ms.std() / 8 + 2e-4 * m0
+    assert ms.std() > 1e-6 * m0  # the per-sample noise term is really there
+
+
+def test_time_step_condition(orc):
+    # the stated dt of the two 1D/2D workloads is the Eq. (1d_timestep) bound
+    assert orc.dt_max(I.config2(N=16)) == pytest.approx(I.DT_CFG2, rel=1e-3)
+    assert orc.dt_max(I.config3()) == pytest.approx(I.DT_CFG3, rel=1e-3)
+    # pure diffusion reduces to dx^2 / (2 D) (Eq. 1d_difftimestep)
+    pb = I.sine_diffusion_1d(K=4, N=8)
+    xi = orc.nodes(8)
+    dx = np.min(np.diff(xi)) * 0.25
+    assert orc.dt_max(pb) == pytest.approx(dx * dx / 2.0, rel=1e-12)
+
+
+def test_moment_bookkeeping(orc):
+    pb = I.config2(N=4, M=6, steps=3, K=8)
+    r = orc.run(pb, ns=6, want_states=True)
+    assert np.allclose(r["sum"], r["states"].sum(0), rtol=1e-15, atol=0)
+    assert np.allclose(r["sumsq"], (r["states"] ** 2).sum(0), rtol=1e-15, atol=0)
+    # samples are independent: a sample run alone equals the same sample in a batch
+    one = orc.run(pb, s0=4, ns=1, want_states=True)["states"][0]
+    assert np.array_equal(one, r["states"][4])
+    # restart: 3 steps == 2 steps then 1 more from the saved state
+    two = orc.run(pb, nsteps=2, ns=6, want_states=True)["states"]
+    three = orc.run(pb, nsteps=1, step0=2, ns=6, state_in=two, want_states=True)["states"]
+    assert np.array_equal(three, r["states"])
+    # thread split changes only the summation grouping
+    r4 = orc.run(pb, ns=6, nthreads=3)
+    assert np.allclose(r4["sum"], r["sum"], rtol=1e-14)

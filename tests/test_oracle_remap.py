@@ -1,0 +1,135 @@
+"""Pins of the oracle's per-element remap (Section 5.3) against polynomial
+reproduction, brute-force least squares built independently in numpy (basis
+from a Chebyshev-Vandermonde solve, not the oracle's product formula), and the
+algebraically equivalent reduced (Woodbury) form of the 1D remap."""
+
+import numpy as np
+import pytest
+
+
+def _basis_np(nodes, x):
+    """Lagrange basis on `nodes` at points x, [len(x)][len(nodes)], from a
+    Chebyshev-Vandermonde solve (independent of the product formula)."""
+    N = len(nodes)
+    cv = np.polynomial.chebyshev.chebvander
+    Vn = cv(2.0 * np.asarray(nodes, float) - 1.0, N - 1)
+    Vx = cv(2.0 * np.atleast_1d(np.asarray(x, float)) - 1.0, N - 1)
+    return np.linalg.solve(Vn.T, Vx.T).T
+
+
+def _advected(orc, N, rng, scale=0.3):
+    xi = orc.nodes(N)
+    gap = np.min(np.diff(xi))
+    return xi, xi + rng.uniform(-scale, scale) * gap + rng.uniform(-0.05, 0.05, N) * gap
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6, 8, 12])
+def test_1d_polynomial_reproduction(orc, N):
+    rng = np.random.default_rng(10 + N)
+    for _ in range(5):
+        xi, xs = _advected(orc, N, rng)
+        c = rng.normal(size=N)
+        poly = np.polynomial.Polynomial(c)
+        e0, e1 = orc.faces_1d(xs, poly(xs))
+        assert e0 == pytest.approx(poly(0.0), abs=1e-9)
+        assert e1 == pytest.approx(poly(1.0), abs=1e-9)
+        q = orc.remap_1d(xs, poly(xs), poly(0.0), poly(1.0))
+        assert np.allclose(q, poly(xi), atol=1e-9)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6])
+def test_1d_remap_brute_force(orc, N):
+    rng = np.random.default_rng(20 + N)
+    for _ in range(10):
+        xi, xs = _advected(orc, N, rng, 0.5)
+        phs = rng.normal(size=N)
+        gL, gR = rng.normal(size=2)
+        V = _basis_np(xi, xs)
+        B = _basis_np(xi, [0.0, 1.0])
+        A = np.vstack([V, B])
+        rhs = np.concatenate([phs, [gL, gR]])
+        ref = np.linalg.lstsq(A, rhs, rcond=None)[0]
+        q = orc.remap_1d(xs, phs, gL, gR)
+        assert np.allclose(q, ref, rtol=1e-10, atol=1e-10)
+        # face values of the advected interpolant (Eq. remap_bnd)
+        Hs = _basis_np(xs, [0.0, 1.0])
+        e0, e1 = orc.faces_1d(xs, phs)
+        assert np.allclose([e0, e1], Hs @ phs, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("N", [3, 6, 8, 12, 16])
+def test_1d_reduced_form_identity(orc, N):
+    # q = H*(phi* - E^T mu), mu = (I + E E^T)^{-1}(E phi* - g), with H* the
+    # advected basis at the Gauss nodes and E the advected basis at the faces,
+    # equals the stacked least-squares solution (Woodbury identity)
+    rng = np.random.default_rng(30 + N)
+    for _ in range(5):
+        xi, xs = _advected(orc, N, rng, 0.4)
+        phs = 1.0 + 0.1 * rng.normal(size=N)
+        g = np.array(orc.faces_1d(xs, phs)) + 1e-3 * rng.normal(size=2)
+        Hs = _basis_np(xs, xi)
+        E = _basis_np(xs, [0.0, 1.0])
+        mu = np.linalg.solve(np.eye(2) + E @ E.T, E @ phs - g)
+        red = Hs @ (phs - E.T @ mu)
+        q = orc.remap_1d(xs, phs, g[0], g[1])
+        assert np.allclose(q, red, rtol=1e-11, atol=1e-11)
+
+
+def _advected_2d(orc, N, rng, scale=0.3):
+    xi = orc.nodes(N)
+    gap = np.min(np.diff(xi))
+    X, Y = np.meshgrid(xi, xi)  # [j][i] -> p = j*N + i
+    xs = X.ravel() + rng.uniform(-scale, scale, N * N) * gap
+    ys = Y.ravel() + rng.uniform(-scale, scale, N * N) * gap
+    return xi, xs, ys
+
+
+def _B2(xi):
+    N = len(xi)
+    h0, h1 = _basis_np(xi, [0.0, 1.0])
+    B = np.zeros((4 * N, N * N))
+    for j in range(N):
+        B[j, j * N:(j + 1) * N] = h0
+        B[N + j, j * N:(j + 1) * N] = h1
+    for i in range(N):
+        B[2 * N + i, i::N] = h0
+        B[3 * N + i, i::N] = h1
+    return B
+
+
+def _V2(xi, xs, ys):
+    Hx = _basis_np(xi, xs)
+    Hy = _basis_np(xi, ys)
+    return np.einsum("pj,pi->pji", Hy, Hx).reshape(len(xs), -1)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_2d_remap_brute_force(orc, N):
+    rng = np.random.default_rng(40 + N)
+    for _ in range(4):
+        xi, xs, ys = _advected_2d(orc, N, rng)
+        phs = rng.normal(size=N * N)
+        g = rng.normal(size=4 * N)
+        A = np.vstack([_V2(xi, xs, ys), _B2(xi)])
+        ref = np.linalg.lstsq(A, np.concatenate([phs, g]), rcond=None)[0]
+        q = orc.remap_2d(xs, ys, phs, g)
+        assert np.allclose(q, ref, rtol=1e-9, atol=1e-9)
+        alpha = np.linalg.solve(_V2(xi, xs, ys), phs)
+        assert np.allclose(orc.faces_2d(xs, ys, phs), _B2(xi) @ alpha, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("N", [2, 4, 6, 8])
+def test_2d_polynomial_reproduction(orc, N):
+    rng = np.random.default_rng(50 + N)
+    xi, xs, ys = _advected_2d(orc, N, rng)
+    C = rng.normal(size=(N, N))
+
+    def P(x, y):
+        return np.polynomial.polynomial.polyval2d(x, y, C)
+
+    X, Y = np.meshgrid(xi, xi)
+    f = orc.faces_2d(xs, ys, P(xs, ys))
+    want = np.concatenate([P(0 * xi, xi), P(1 + 0 * xi, xi), P(xi, 0 * xi), P(xi, 1 + 0 * xi)])
+    assert np.allclose(f, want, atol=1e-8)
+    q = orc.remap_2d(xs, ys, P(xs, ys), want)
+    assert np.allclose(q, P(X, Y).ravel(), atol=1e-8)
