@@ -71,6 +71,12 @@ def lib():
             L.orc_faces_1d.argtypes = [C.c_int, dp, dp, dp, dp]
             L.orc_remap_1d.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_double, dp]
             L.orc_faces_2d.argtypes = [C.c_int, dp, dp, dp, dp, dp]
+            L.orc_lagrange_split.restype = C.c_double
+            L.orc_lagrange_split.argtypes = [C.c_int, dp, dp, C.c_int, C.c_double, C.c_double]
+            L.orc_faces_1d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp]
+            L.orc_remap_1d_split.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_double, dp]
+            L.orc_faces_2d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp]
+            L.orc_remap_2d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_remap_2d.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_init_state.argtypes = [C.POINTER(_Problem), dp]
             L.orc_get_coeffs.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
@@ -227,6 +233,50 @@ def remap_2d(xs, ys, phs, g):
     xi = nodes(N)
     q = np.zeros(N * N)
     if lib().orc_remap_2d(N, _dp(xi), _dp(xs), _dp(ys), _dp(phs), _dp(g), _dp(q)) != 0:
+        raise np.linalg.LinAlgError("remap failed")
+    return q
+
+
+def lagrange_split(base, off, j, xb, xo):
+    base, off = _f64(base), _f64(off)
+    return lib().orc_lagrange_split(len(base), _dp(base), _dp(off), j, float(xb), float(xo))
+
+
+def faces_1d_split(d, phs):
+    """Face values with the particles at the Gauss nodes plus d."""
+    d, phs = _f64(d), _f64(phs)
+    xi = nodes(len(d))
+    e0, e1 = C.c_double(), C.c_double()
+    lib().orc_faces_1d_split(len(d), _dp(xi), _dp(d), _dp(phs), C.byref(e0), C.byref(e1))
+    return e0.value, e1.value
+
+
+def remap_1d_split(d, phs, gL, gR):
+    d, phs = _f64(d), _f64(phs)
+    N = len(d)
+    xi = nodes(N)
+    q = np.zeros(N)
+    if lib().orc_remap_1d_split(N, _dp(xi), _dp(d), _dp(phs), gL, gR, _dp(q)) != 0:
+        raise np.linalg.LinAlgError("remap failed")
+    return q
+
+
+def faces_2d_split(dx, dy, phs):
+    dx, dy, phs = _f64(dx), _f64(dy), _f64(phs)
+    N = int(round(np.sqrt(len(dx))))
+    xi = nodes(N)
+    f = np.zeros(4 * N)
+    if lib().orc_faces_2d_split(N, _dp(xi), _dp(dx), _dp(dy), _dp(phs), _dp(f)) != 0:
+        raise np.linalg.LinAlgError("singular")
+    return f
+
+
+def remap_2d_split(dx, dy, phs, g):
+    dx, dy, phs, g = _f64(dx), _f64(dy), _f64(phs), _f64(g)
+    N = int(round(np.sqrt(len(dx))))
+    xi = nodes(N)
+    q = np.zeros(N * N)
+    if lib().orc_remap_2d_split(N, _dp(xi), _dp(dx), _dp(dy), _dp(phs), _dp(g), _dp(q)) != 0:
         raise np.linalg.LinAlgError("remap failed")
     return q
 

@@ -199,14 +199,27 @@ void orc_nodes(int N, double *xi)
     for (int i = 0; i < N; ++i) xi[i] = 0.5 * (1.0 - cos((i + 0.5) * M_PI / N));
 }
 
-/* Lagrange polynomial h_j through the points pts[0..N-1] evaluated at x,   */
-/* by the product formula of Eq. (3.5) / Eq. (h_star).                      */
-double orc_lagrange(int N, const double *pts, int j, double x)
+/* Lagrange polynomial h_j through the points base[m] + off[m] (m < N),      */
+/* evaluated at xb + xo, by the product formula of Eq. (3.5) / Eq. (h_star).  */
+/* Points are passed as a base position plus an offset and every difference  */
+/* is formed as (base difference) + (offset difference): a particle position */
+/* x* = x + dx (Eq. def_dx) is never rounded as a whole, so a displacement    */
+/* much smaller than x keeps its full relative precision.                    */
+double orc_lagrange_split(int N, const double *base, const double *off, int j, double xb, double xo)
 {
     double v = 1.0;
     for (int m = 0; m < N; ++m)
-        if (m != j) v *= (x - pts[m]) / (pts[j] - pts[m]);
+        if (m != j)
+            v *= ((xb - base[m]) + (xo - off[m])) / ((base[j] - base[m]) + (off[j] - off[m]));
     return v;
+}
+
+static const double ORC_ZEROS[256] = {0.0}; /* offsets of unmoved points (n <= 256) */
+
+/* Lagrange polynomial h_j through pts[0..N-1] at x (Eq. 3.5). */
+double orc_lagrange(int N, const double *pts, int j, double x)
+{
+    return orc_lagrange_split(N, pts, ORC_ZEROS, j, x, 0.0);
 }
 
 /* Derivative of h_j at x: sum over the dropped factor (product rule). */
@@ -343,24 +356,54 @@ done:
 
 /* 1D: values of the advected interpolant (Eq. phi_stardef) at the element  */
 /* faces xi = 0 and xi = 1 (Eq. remap_bnd), using the Lagrange basis on the  */
-/* advected points (Eq. h_star).                                             */
-void orc_faces_1d(int N, const double *xs, const double *phs, double *e0, double *e1)
+/* advected points xi_j + d_j (Eq. h_star).                                  */
+void orc_faces_1d_split(int N, const double *xi, const double *d, const double *phs, double *e0,
+                        double *e1)
 {
     double a = 0.0, b = 0.0;
     for (int j = 0; j < N; ++j) {
-        a += phs[j] * orc_lagrange(N, xs, j, 0.0);
-        b += phs[j] * orc_lagrange(N, xs, j, 1.0);
+        a += phs[j] * orc_lagrange_split(N, xi, d, j, 0.0, 0.0);
+        b += phs[j] * orc_lagrange_split(N, xi, d, j, 1.0, 0.0);
     }
     *e0 = a;
     *e1 = b;
 }
 
 /* 1D remap: q = argmin |V q - phi*|^2 + |B q - g|^2 where V[p][i] =         */
-/* h_i(xs_p) (Gauss-node basis at the advected particles) and B holds the    */
-/* rows h_i(0), h_i(1) with the upwinded face values g = (gL, gR).           */
-int orc_remap_1d(int N, const double *xi, const double *xs, const double *phs, double gL,
-                 double gR, double *q)
+/* h_i(xi_p + d_p) (Gauss-node basis at the advected particles) and B holds  */
+/* the rows h_i(0), h_i(1) with the upwinded face values g = (gL, gR).       */
+int orc_remap_1d_split(int N, const double *xi, const double *d, const double *phs, double gL,
+                       double gR, double *q)
 {
+    int m = N + 2;
+    double *A = (double *)malloc(sizeof(double) * m * N);
+    double *rhs = (double *)malloc(sizeof(double) * m);
+    for (int p = 0; p < N; ++p) {
+        for (int i = 0; i < N; ++i) A[p * N + i] = orc_lagrange_split(N, xi, ORC_ZEROS, i, xi[p], d[p]);
+        rhs[p] = phs[p];
+    }
+    for (int i = 0; i < N; ++i) {
+        A[N * N + i] = orc_lagrange(N, xi, i, 0.0);
+        A[(N + 1) * N + i] = orc_lagrange(N, xi, i, 1.0);
+    }
+    rhs[N] = gL;
+    rhs[N + 1] = gR;
+    int rc = orc_lstsq(m, N, A, rhs, q);
+    free(A);
+    free(rhs);
+    return rc;
+}
+
+/* The same with the advected particles given as absolute positions xs.      */
+void orc_faces_1d(int N, const double *xs, const double *phs, double *e0, double *e1)
+{
+    orc_faces_1d_split(N, xs, ORC_ZEROS, phs, e0, e1);
+}
+
+int orc_remap_1d(int N, const double *xi, const double *xs, const double *phs, double gL, double gR,
+                 double *q)
+{
+    /* xs_p = xi_p + (xs_p - xi_p) would round; use the positions as bases */
     int m = N + 2;
     double *A = (double *)malloc(sizeof(double) * m * N);
     double *rhs = (double *)malloc(sizeof(double) * m);
@@ -381,28 +424,31 @@ int orc_remap_1d(int N, const double *xi, const double *xs, const double *phs, d
 }
 
 /* 2D tensor-product element, nodes p = j*N + i (x index i fastest).         */
-/* V[p][(i',j')] = h_i'(xs_p) h_j'(ys_p) on the scattered advected particles. */
-static void orc_build_V2(int N, const double *xi, const double *xs, const double *ys, double *V)
+/* V[p][(i',j')] = h_i'(x*_p) h_j'(y*_p) on the scattered advected particles, */
+/* particle p at (bx_p + ox_p, by_p + oy_p) (base plus offset, see           */
+/* orc_lagrange_split).                                                      */
+static void orc_build_V2(int N, const double *xi, const double *bx, const double *ox, const double *by,
+                         const double *oy, double *V)
 {
     int n = N * N;
     for (int p = 0; p < n; ++p)
         for (int jj = 0; jj < N; ++jj)
             for (int ii = 0; ii < N; ++ii)
-                V[p * n + jj * N + ii] =
-                    orc_lagrange(N, xi, ii, xs[p]) * orc_lagrange(N, xi, jj, ys[p]);
+                V[p * n + jj * N + ii] = orc_lagrange_split(N, xi, ORC_ZEROS, ii, bx[p], ox[p]) *
+                                         orc_lagrange_split(N, xi, ORC_ZEROS, jj, by[p], oy[p]);
 }
 
 /* 2D face values of the advected interpolant: alpha = V^{-1} phi* are its  */
 /* nodal values (Eq. phi_star in tensor form); then at the N Gauss-node      */
 /* positions of each face: left (xi=0), right (xi=1), bottom (eta=0), top.   */
 /* faces[0..N) left, [N..2N) right, [2N..3N) bottom, [3N..4N) top.           */
-int orc_faces_2d(int N, const double *xi, const double *xs, const double *ys, const double *phs,
-                 double *faces)
+static int orc_faces_2d_core(int N, const double *xi, const double *bx, const double *ox,
+                             const double *by, const double *oy, const double *phs, double *faces)
 {
     int n = N * N;
     double *V = (double *)malloc(sizeof(double) * n * n);
     double *alpha = (double *)malloc(sizeof(double) * n);
-    orc_build_V2(N, xi, xs, ys, V);
+    orc_build_V2(N, xi, bx, ox, by, oy, V);
     int rc = orc_lu_solve(n, V, phs, alpha);
     if (rc == 0) {
         for (int j = 0; j < N; ++j) {
@@ -430,14 +476,15 @@ int orc_faces_2d(int N, const double *xi, const double *xs, const double *ys, co
 }
 
 /* 2D remap: min |V q - phi*|^2 + |B q - g|^2, B = the 4N face rows at the   */
-/* Gauss-node positions along each face, g ordered as in orc_faces_2d.       */
-int orc_remap_2d(int N, const double *xi, const double *xs, const double *ys, const double *phs,
-                 const double *g, double *q)
+/* Gauss-node positions along each face, g ordered as in the face values.    */
+static int orc_remap_2d_core(int N, const double *xi, const double *bx, const double *ox,
+                             const double *by, const double *oy, const double *phs, const double *g,
+                             double *q)
 {
     int n = N * N, m = n + 4 * N;
     double *A = (double *)calloc((size_t)m * n, sizeof(double));
     double *rhs = (double *)malloc(sizeof(double) * m);
-    orc_build_V2(N, xi, xs, ys, A);
+    orc_build_V2(N, xi, bx, ox, by, oy, A);
     for (int p = 0; p < n; ++p) rhs[p] = phs[p];
     for (int j = 0; j < N; ++j)
         for (int ii = 0; ii < N; ++ii) {
@@ -453,6 +500,50 @@ int orc_remap_2d(int N, const double *xi, const double *xs, const double *ys, co
     int rc = orc_lstsq(m, n, A, rhs, q);
     free(A);
     free(rhs);
+    return rc;
+}
+
+/* Absolute particle positions xs, ys. */
+int orc_faces_2d(int N, const double *xi, const double *xs, const double *ys, const double *phs,
+                 double *faces)
+{
+    return orc_faces_2d_core(N, xi, xs, ORC_ZEROS, ys, ORC_ZEROS, phs, faces);
+}
+
+int orc_remap_2d(int N, const double *xi, const double *xs, const double *ys, const double *phs,
+                 const double *g, double *q)
+{
+    return orc_remap_2d_core(N, xi, xs, ORC_ZEROS, ys, ORC_ZEROS, phs, g, q);
+}
+
+/* Particles at the Gauss nodes plus displacements dx, dy (element units). */
+int orc_faces_2d_split(int N, const double *xi, const double *dx, const double *dy,
+                       const double *phs, double *faces)
+{
+    int n = N * N;
+    double *bx = (double *)malloc(sizeof(double) * n), *by = (double *)malloc(sizeof(double) * n);
+    for (int p = 0; p < n; ++p) {
+        bx[p] = xi[p % N];
+        by[p] = xi[p / N];
+    }
+    int rc = orc_faces_2d_core(N, xi, bx, dx, by, dy, phs, faces);
+    free(bx);
+    free(by);
+    return rc;
+}
+
+int orc_remap_2d_split(int N, const double *xi, const double *dx, const double *dy,
+                       const double *phs, const double *g, double *q)
+{
+    int n = N * N;
+    double *bx = (double *)malloc(sizeof(double) * n), *by = (double *)malloc(sizeof(double) * n);
+    for (int p = 0; p < n; ++p) {
+        bx[p] = xi[p % N];
+        by[p] = xi[p / N];
+    }
+    int rc = orc_remap_2d_core(N, xi, bx, dx, by, dy, phs, g, q);
+    free(bx);
+    free(by);
     return rc;
 }
 
@@ -554,6 +645,7 @@ typedef struct {
     double *ax, *ay;     /* [E][n] u_x dt, u_y dt at the nodes                */
     double *b;           /* [E][n] sqrt(2 D) at the nodes                     */
     double *c;           /* [E][n] 1 - dt div u (Eq. advection_phi)           */
+    double *div;         /* [E][n] du_j/dx_j at the nodes                     */
     double *afx, *bfx;   /* [Ky][Kx][N(2D) or 1] vertical faces: u_x dt, sqrt(2D) */
     double *afy, *bfy;   /* [Ky][Kx][N] horizontal faces (2D)                 */
 } orc_coeffs;
@@ -565,6 +657,7 @@ static void orc_coeffs_free(orc_coeffs *cf)
     free(cf->ay);
     free(cf->b);
     free(cf->c);
+    free(cf->div);
     free(cf->afx);
     free(cf->bfx);
     free(cf->afy);
@@ -604,6 +697,7 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
     cf->ay = (double *)calloc((size_t)E * n, sizeof(double));
     cf->b = (double *)calloc((size_t)E * n, sizeof(double));
     cf->c = (double *)calloc((size_t)E * n, sizeof(double));
+    cf->div = (double *)calloc((size_t)E * n, sizeof(double));
     int nf = d == 2 ? N : 1;
     cf->afx = (double *)calloc((size_t)E * nf, sizeof(double));
     cf->bfx = (double *)calloc((size_t)E * nf, sizeof(double));
@@ -638,6 +732,7 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
                 }
                 div = dx / cf->hx + dy / cf->hy;
             }
+            cf->div[e * n + p] = div;
             cf->c[e * n + p] = 1.0 - pb->dt * div;
         }
         /* faces at the low side of element e: vertical face x = x_kx, and   */
@@ -695,23 +790,24 @@ int orc_get_coeffs(const orc_problem *pb, double *ax, double *ay, double *b, dou
 }
 
 /* One SL step of one sample (Sections 5.2-5.3), state Q [E][n] in place.    */
-static int orc_step_1d(const orc_coeffs *cf, double dW, double *Q)
+static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, double *Q)
 {
     int N = cf->N, K = cf->Kx;
-    double *xs = (double *)malloc(sizeof(double) * K * N);
+    double *d = (double *)malloc(sizeof(double) * K * N);
     double *phs = (double *)malloc(sizeof(double) * K * N);
     double *e0 = (double *)malloc(sizeof(double) * K);
     double *e1 = (double *)malloc(sizeof(double) * K);
     double *g = (double *)malloc(sizeof(double) * K);
     int rc = 0;
-    /* advance (Eq. def_dx, mapped to the element: xi* = xi + (u dt + sqrt(2D) dW)/h) */
-    /* and the compositional update (Eq. advection_phi) */
+    /* advance (Eq. def_dx): particle p moves from xi_p by d_p = (u dt +      */
+    /* sqrt(2D) dW) / h in element units; compositional update              */
+    /* (Eq. advection_phi): phi* = phi + dt (-phi du/dx)                     */
     for (int k = 0; k < K; ++k)
         for (int p = 0; p < N; ++p) {
-            xs[k * N + p] = cf->xi[p] + (cf->ax[k * N + p] + cf->b[k * N + p] * dW) / cf->hx;
-            phs[k * N + p] = cf->c[k * N + p] * Q[k * N + p];
+            d[k * N + p] = (cf->ax[k * N + p] + cf->b[k * N + p] * dW) / cf->hx;
+            phs[k * N + p] = Q[k * N + p] + dt * (-Q[k * N + p] * cf->div[k * N + p]);
         }
-    for (int k = 0; k < K; ++k) orc_faces_1d(N, xs + k * N, phs + k * N, &e0[k], &e1[k]);
+    for (int k = 0; k < K; ++k) orc_faces_1d_split(N, cf->xi, d + k * N, phs + k * N, &e0[k], &e1[k]);
     /* upwinding (Eq. bnd_update): interface f sits between elements f-1 and */
     /* f (periodic); take the left element's value when u dt + sqrt(2D) dW > 0 */
     for (int f = 0; f < K; ++f) {
@@ -719,8 +815,8 @@ static int orc_step_1d(const orc_coeffs *cf, double dW, double *Q)
         g[f] = sigma > 0.0 ? e1[(f - 1 + K) % K] : e0[f];
     }
     for (int k = 0; k < K && rc == 0; ++k)
-        rc = orc_remap_1d(N, cf->xi, xs + k * N, phs + k * N, g[k], g[(k + 1) % K], Q + k * N);
-    free(xs);
+        rc = orc_remap_1d_split(N, cf->xi, d + k * N, phs + k * N, g[k], g[(k + 1) % K], Q + k * N);
+    free(d);
     free(phs);
     free(e0);
     free(e1);
@@ -728,11 +824,11 @@ static int orc_step_1d(const orc_coeffs *cf, double dW, double *Q)
     return rc;
 }
 
-static int orc_step_2d(const orc_coeffs *cf, const double dW[2], double *Q)
+static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], double *Q)
 {
     int N = cf->N, n = cf->n, Kx = cf->Kx, Ky = cf->Ky, E = cf->E;
-    double *xs = (double *)malloc(sizeof(double) * E * n);
-    double *ys = (double *)malloc(sizeof(double) * E * n);
+    double *dx = (double *)malloc(sizeof(double) * E * n);
+    double *dy = (double *)malloc(sizeof(double) * E * n);
     double *phs = (double *)malloc(sizeof(double) * E * n);
     double *faces = (double *)malloc(sizeof(double) * E * 4 * N);
     double *gv = (double *)malloc(sizeof(double) * E * N); /* vertical face at low x of e */
@@ -741,13 +837,12 @@ static int orc_step_2d(const orc_coeffs *cf, const double dW[2], double *Q)
     int rc = 0;
     for (int e = 0; e < E; ++e)
         for (int p = 0; p < n; ++p) {
-            int i = p % N, j = p / N;
-            xs[e * n + p] = cf->xi[i] + (cf->ax[e * n + p] + cf->b[e * n + p] * dW[0]) / cf->hx;
-            ys[e * n + p] = cf->xi[j] + (cf->ay[e * n + p] + cf->b[e * n + p] * dW[1]) / cf->hy;
-            phs[e * n + p] = cf->c[e * n + p] * Q[e * n + p];
+            dx[e * n + p] = (cf->ax[e * n + p] + cf->b[e * n + p] * dW[0]) / cf->hx;
+            dy[e * n + p] = (cf->ay[e * n + p] + cf->b[e * n + p] * dW[1]) / cf->hy;
+            phs[e * n + p] = Q[e * n + p] + dt * (-Q[e * n + p] * cf->div[e * n + p]);
         }
     for (int e = 0; e < E && rc == 0; ++e)
-        rc = orc_faces_2d(N, cf->xi, xs + e * n, ys + e * n, phs + e * n, faces + e * 4 * N);
+        rc = orc_faces_2d_split(N, cf->xi, dx + e * n, dy + e * n, phs + e * n, faces + e * 4 * N);
     for (int ky = 0; ky < Ky && rc == 0; ++ky)
         for (int kx = 0; kx < Kx; ++kx) {
             int e = ky * Kx + kx;
@@ -772,10 +867,10 @@ static int orc_step_2d(const orc_coeffs *cf, const double dW[2], double *Q)
                 g[2 * N + f] = gh[e * N + f];
                 g[3 * N + f] = gh[eT * N + f];
             }
-            rc = orc_remap_2d(N, cf->xi, xs + e * n, ys + e * n, phs + e * n, g, Q + e * n);
+            rc = orc_remap_2d_split(N, cf->xi, dx + e * n, dy + e * n, phs + e * n, g, Q + e * n);
         }
-    free(xs);
-    free(ys);
+    free(dx);
+    free(dy);
     free(phs);
     free(faces);
     free(gv);
@@ -817,7 +912,8 @@ static void *orc_worker(void *arg)
             orc_normals(jb->pb->seed, (uint32_t)(jb->step0 + t), (uint32_t)s, 0u, z);
             dW[0] = sdt * z[0];
             dW[1] = sdt * z[1];
-            jb->rc = cf->dim == 1 ? orc_step_1d(cf, dW[0], Q) : orc_step_2d(cf, dW, Q);
+            jb->rc = cf->dim == 1 ? orc_step_1d(cf, jb->pb->dt, dW[0], Q)
+                                  : orc_step_2d(cf, jb->pb->dt, dW, Q);
         }
         if (jb->state_out) memcpy(jb->state_out + (size_t)(s - jb->s0) * sz, Q, sizeof(double) * sz);
         if (jb->sum)

@@ -133,3 +133,63 @@ def test_2d_polynomial_reproduction(orc, N):
     assert np.allclose(f, want, atol=1e-8)
     q = orc.remap_2d(xs, ys, P(xs, ys), want)
     assert np.allclose(q, P(X, Y).ravel(), atol=1e-8)
+
+
+@pytest.mark.parametrize("N", [3, 6, 10, 16])
+def test_split_forms_equal_absolute_forms(orc, N):
+    # particles given as node + displacement evaluate the same polynomials as
+    # particles given by absolute position (up to the rounding of xi + d)
+    rng = np.random.default_rng(60 + N)
+    xi = orc.nodes(N)
+    gap = np.min(np.diff(xi))
+    d = rng.uniform(-0.4, 0.4, N) * gap
+    phs = 1 + 0.2 * rng.normal(size=N)
+    e_abs = orc.faces_1d(xi + d, phs)
+    e_spl = orc.faces_1d_split(d, phs)
+    assert np.allclose(e_abs, e_spl, rtol=1e-12, atol=1e-12)
+    g = np.array(e_spl) + 1e-3
+    assert np.allclose(orc.remap_1d(xi + d, phs, *g), orc.remap_1d_split(d, phs, *g), rtol=1e-12, atol=1e-12)
+    for j in range(N):
+        assert orc.lagrange_split(xi, d, j, 0.3, 0.0) == pytest.approx(orc.lagrange(xi + d, j, 0.3), rel=1e-11, abs=1e-13)
+
+
+@pytest.mark.parametrize("N", [3, 5, 8])
+def test_split_forms_2d(orc, N):
+    rng = np.random.default_rng(70 + N)
+    xi = orc.nodes(N)
+    gap = np.min(np.diff(xi))
+    X, Y = np.meshgrid(xi, xi)
+    dx = rng.uniform(-0.3, 0.3, N * N) * gap
+    dy = rng.uniform(-0.3, 0.3, N * N) * gap
+    C = rng.normal(size=(N, N))
+
+    def P(x, y):
+        return np.polynomial.polynomial.polyval2d(x, y, C)
+
+    xs, ys = X.ravel() + dx, Y.ravel() + dy
+    f = orc.faces_2d_split(dx, dy, P(xs, ys))
+    want = np.concatenate([P(0 * xi, xi), P(1 + 0 * xi, xi), P(xi, 0 * xi), P(xi, 1 + 0 * xi)])
+    assert np.allclose(f, want, atol=1e-8)
+    assert np.allclose(orc.remap_2d_split(dx, dy, P(xs, ys), want), P(X, Y).ravel(), atol=1e-8)
+    phs = rng.normal(size=N * N)
+    g = rng.normal(size=4 * N)
+    assert np.allclose(orc.remap_2d_split(dx, dy, phs, g), orc.remap_2d(xs, ys, phs, g), rtol=1e-9, atol=1e-9)
+
+
+def test_small_displacement_keeps_precision(orc):
+    # a displacement of 1e-6 of the element: the split form reproduces the
+    # first-order shift exactly to ~1e-10 relative, the absolute form loses
+    # digits to the rounding of xi + d
+    N = 8
+    xi = orc.nodes(N)
+    d = np.full(N, 1e-6)
+    c = np.array([0.3, -1.2, 0.7, 0.25, -0.4, 0.1, 0.05, -0.02])
+    poly = np.polynomial.Polynomial(c)
+    dpoly = poly.deriv()
+    phs = poly(xi)  # values carried by the particles (deg N-1 field)
+    e0, e1 = orc.faces_1d_split(d, phs)
+    # the advected polynomial is p(x - d): its face values
+    want0, want1 = poly(0.0 - 1e-6), poly(1.0 - 1e-6)
+    assert abs(e0 - want0) < 1e-13 and abs(e1 - want1) < 1e-13
+    # and the shift itself is resolved to 1e-7 relative
+    assert abs((e0 - poly(0.0)) / (-1e-6 * dpoly(0.0)) - 1) < 1e-6
