@@ -1,0 +1,175 @@
+/*
+ * sl.h -- C ABI of the GB300 (sm_103a) semi-Lagrangian Monte-Carlo solver.
+ *
+ * The library advances N_s Monte-Carlo samples of a nodal polynomial field on
+ * a periodic spectral-element mesh by the element-local semi-Lagrangian step
+ * of Natarajan, Popov & Jacobs (arXiv:2009.07340, Section 5):
+ *
+ *   1. particles are seeded at the element's Chebyshev-Gauss nodes
+ *      (Section 5.1, Eq. soln_init; nodes of Eq. gaussquad with (i+1/2)/N);
+ *   2. they move by one explicit Euler-Maruyama step,
+ *      x* = x + u(x) dt + sqrt(2 D(x)) dW^s, with ONE Wiener increment per
+ *      sample, step and dimension shared by every node of every element
+ *      (Section 5.2, Eq. def_dx and the paragraph after it), and the carried
+ *      value gets the compositional update phi* = phi (1 - dt div u)
+ *      (Eq. advection_phi);
+ *   3. the advected interpolant (Eq. phi_stardef, Eq. h_star) is evaluated at
+ *      the element faces (Eq. remap_bnd), an upwind value is taken at every
+ *      interface (Eq. bnd_update), and the field is remapped to the Gauss
+ *      nodes by the constrained least-squares fit
+ *      q = argmin |V q - phi*|^2 + |B q - g|^2 (Section 5.3);
+ *   4. samples are averaged on the nodes (Section 5.4, Eq. averaged).
+ *
+ * All arithmetic of these steps runs in the library's CUDA kernels.  The
+ * Wiener increments come from Philox4x32-10 (Salmon et al., SC'11) with key
+ * (seed low word, seed high word) and counter (step, sample, 0, 0), mapped to
+ * two 52-bit uniforms u = (2x+1) 2^-53 and Box-Muller normals, so a given
+ * (seed, step counter) fixes the result.
+ *
+ * Conventions
+ *   - Node layout: element-major, elements x-fastest; inside an element the
+ *     nodes are x-fastest (p = j*N + i in 2D).  Per-sample state is
+ *     [sample][element][node].
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *     "device" pointers are caller-owned CUDA device memory.
+ *   - Every entry point returns SL_OK (0) or a negative SL_ERR_* code.  After
+ *     SL_ERR_CUDA, SL_ERR_SINGULAR or SL_ERR_TIMEOUT the context is poisoned:
+ *     only sl_free is valid.  Argument errors leave the context usable.
+ *   - One context per host thread at a time; contexts are independent.
+ */
+#ifndef SL_H
+#define SL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SL_OK = 0,
+    SL_ERR_ARG = -1,         /* invalid argument (sizes, kinds, D < 0, NULL) */
+    SL_ERR_DT = -2,          /* dt above the Eq. (1d_timestep) bound with strict_dt set */
+    SL_ERR_OOM = -3,         /* device allocation failed */
+    SL_ERR_CUDA = -4,        /* a CUDA call failed */
+    SL_ERR_SINGULAR = -5,    /* coincident advected particles: non-finite remap */
+    SL_ERR_TIMEOUT = -6,     /* a bounded device wait expired */
+    SL_ERR_STATE = -7,       /* context poisoned by an earlier error */
+    SL_ERR_UNSUPPORTED = -8  /* valid but not provided (e.g. non-periodic mesh) */
+};
+
+/* Arithmetic of the step.  Wiener increments and moments are FP64 always.  */
+enum {
+    SL_FP64 = 0,  /* everything in FP64                                       */
+    SL_MIXED = 1, /* basis evaluation / remap contractions in FP32, the       */
+                  /* constrained least-squares (capacitance) factor in FP64  */
+    SL_FP32 = 2   /* as SL_MIXED but the factor in FP32 too                   */
+};
+
+/* Prescribed fields (all evaluated in physical coordinates).               */
+enum {
+    /* drift u */
+    SL_U_CONST = 1,    /* u = (p0, p1)                                        */
+    SL_U_SIN = 2,      /* u = p0 + p1 sin(p2 pi x)                       (1D) */
+    SL_U_ROTATION = 3, /* u = p0 (-(y - p2), x - p1)                     (2D) */
+    /* diffusion coefficient D >= 0 */
+    SL_D_CONST = 11,   /* D = p0                                              */
+    SL_D_COS = 12,     /* D = p0 (1 + p1 cos(p2 pi x))                        */
+    SL_D_SINSIN = 13,  /* D = p0 (1 + p1 sin(p2 pi x) sin(p3 pi y))           */
+    /* initial condition phi0 */
+    SL_PHI_GAUSS = 21,   /* p0 exp(-|x - (p2,p3)|^2 / (2 p1^2)), nearest periodic images */
+    SL_PHI_FOURIER = 22, /* p0 + sum_{k=1}^{p2} a_k cos(k p1 pi x) + b_k sin(k p1 pi x), */
+                         /* a_k = p[3+2(k-1)], b_k = p[4+2(k-1)], at most 18 modes (1D)  */
+    SL_PHI_SINE = 23,    /* p0 + p1 sin(2 pi p2 x)                               (1D)    */
+    SL_PHI_SINSIN = 24,  /* p0 + p1 sin(2 pi p2 x) sin(2 pi p2 y)                (2D)    */
+    SL_PHI_NODAL = 25    /* host array nodal[element][node] of the initial values        */
+};
+
+typedef struct {
+    int kind;
+    double p[40];
+    const double *nodal; /* SL_PHI_NODAL only: host [elements][N^dim], copied at sl_init */
+} sl_field;
+
+/* Uniform tensor mesh of K[0] (x K[1]) elements on [lo, hi]. */
+typedef struct {
+    int dim;         /* 1 or 2                                       */
+    int K[2];        /* elements per direction; K[1] ignored in 1D    */
+    double lo[2];
+    double hi[2];
+    int periodic[2]; /* must be 1 (Dirichlet ghost values: not provided) */
+} sl_mesh;
+
+typedef struct {
+    unsigned long long seed; /* Philox key                                           */
+    int precision;           /* SL_FP64, SL_MIXED or SL_FP32                          */
+    int strict_dt;           /* 1: sl_step refuses dt above the Eq. (1d_timestep) bound */
+    void *stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+    int device;              /* CUDA device ordinal; -1 = current device              */
+    long long sample0;       /* global index of sample 0 (Philox counter word 1): a run */
+                             /* split over GPUs gives each a disjoint sample range;    */
+                             /* sample0 + M <= 2^32                                     */
+} sl_options;
+
+typedef struct sl_ctx sl_ctx; /* opaque; owns all of its device memory */
+
+/* Creates a solver for M samples of order N (N Gauss nodes per direction,  */
+/* 2 <= N <= 16) on `mesh`, evaluates the fields at the nodes and faces and  */
+/* sets every sample to phi0 (Section 5.1).  1D: K <= 1024 elements.         */
+/* The step counter starts at 0.  opt may be NULL (seed 0, SL_FP64).         */
+int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift,
+            const sl_field *diffusion, const sl_field *phi0, const sl_options *opt);
+
+/* Advances every sample by `steps` SL steps of size dt (Sections 5.2-5.3):  */
+/* Wiener increments for the step counters [n, n+steps), particle advance,   */
+/* face values, upwinding, constrained least-squares remap.  Asynchronous on */
+/* the context's stream; the step counter advances by `steps`.  Returns      */
+/* SL_ERR_DT if strict_dt is set and dt exceeds sl_dt_max.                   */
+int sl_step(sl_ctx *c, double dt, int steps);
+
+/* Sample moments on the nodes, Eq. (averaged): mean = (1/M) sum_s Q^s and   */
+/* m2 = (1/M) sum_s (Q^s)^2, FP64 accumulation in a fixed order.  Host       */
+/* arrays [elements][N^dim]; m2 may be NULL.  Synchronises the stream and    */
+/* reports any deferred device error (SL_ERR_SINGULAR, SL_ERR_CUDA).         */
+int sl_moments(sl_ctx *c, double *mean, double *m2);
+
+/* As sl_moments into caller-owned device memory, asynchronously on the      */
+/* context's stream (no synchronisation, no error check of earlier steps).  */
+int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2);
+
+/* Largest dt satisfying |u|max dt + sqrt(2 Dmax dt) <= dx_min in every      */
+/* direction (Eq. 1d_timestep), dx_min = smallest node gap times h.          */
+int sl_dt_max(const sl_ctx *c, double *dt);
+
+/* Step counter (number of SL steps taken so far). */
+int sl_step_count(const sl_ctx *c, long long *n);
+
+/* Copies samples [s0, s0+count) of the state to host memory, FP64,          */
+/* [count][elements][N^dim].  Synchronises.                                   */
+int sl_get_samples(sl_ctx *c, int s0, int count, double *out);
+
+/* Overwrites samples [s0, s0+count) from host FP64 [count][elements][N^dim] */
+/* (checkpoint restore together with sl_set_step_count).  Synchronises.    */
+int sl_set_samples(sl_ctx *c, int s0, int count, const double *in);
+int sl_set_step_count(sl_ctx *c, long long n);
+
+/* Wiener increments dW for step counters [step0, step0+nsteps) and every    */
+/* sample, computed by the device generator: host out[nsteps][M][dim].       */
+int sl_wiener(sl_ctx *c, long long step0, int nsteps, double dt, double *out);
+
+/* Kernel timing hook.  While enabled, sl_step records a pair of CUDA events */
+/* on the context's stream around every launch of the step kernel (not the  */
+/* Wiener-increment kernel).  sl_profile_read synchronises, returns the     */
+/* summed event time (ms) and the number of such launches since the         */
+/* previous read, and clears them.                                          */
+int sl_profile(sl_ctx *c, int enable);
+int sl_profile_read(sl_ctx *c, double *kernel_ms, long long *launches);
+
+/* Releases the context and its device memory.  NULL is a no-op. */
+void sl_free(sl_ctx *c);
+
+/* Static string describing an SL_* code. */
+const char *sl_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SL_H */

@@ -1,0 +1,287 @@
+"""GB300 (sm_103a) semi-Lagrangian Monte-Carlo solver -- Python binding.
+
+Thin ctypes marshalling over the C ABI of ``include/sl.h`` (``libsl.so``):
+every step of the method runs in the library's CUDA kernels; this module
+only converts Python arguments to the C structs and buffers.  There is no
+CPU fallback: if ``libsl.so`` has not been built, or no CUDA device is
+present, calls raise.
+
+Problems are the plain dicts of ``sl_inputs`` (mesh, N, M, field kinds and
+parameters, dt, seed).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_init", "sl_step",
+           "sl_moments", "sl_moments_device", "sl_dt_max", "sl_step_count", "sl_get_samples",
+           "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_profile", "sl_profile_read", "sl_free",
+           "sl_strerror"]
+
+SL_FP64, SL_MIXED, SL_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": SL_FP64, "mixed": SL_MIXED, "fp32": SL_FP32}
+
+_U = {"const": 1, "sin": 2, "rotation": 3}
+_D = {"const": 11, "cos": 12, "sinsin": 13}
+_PHI = {"gauss": 21, "fourier": 22, "sine": 23, "sinsin": 24, "nodal": 25}
+
+
+class SLError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {sl_strerror(code)} ({code})")
+
+
+class sl_field(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 40), ("nodal", C.POINTER(C.c_double))]
+
+
+class sl_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("K", C.c_int * 2), ("lo", C.c_double * 2), ("hi", C.c_double * 2),
+                ("periodic", C.c_int * 2)]
+
+
+class sl_options(C.Structure):
+    _fields_ = [("seed", C.c_ulonglong), ("precision", C.c_int), ("strict_dt", C.c_int),
+                ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Loads libsl.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libsl.so is not built: run paper_2009_07340_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = C.CDLL(_build.LIB)
+        vp = C.c_void_p
+        L.sl_init.argtypes = [C.POINTER(vp), C.POINTER(sl_mesh), C.c_int, C.c_int, C.POINTER(sl_field),
+                              C.POINTER(sl_field), C.POINTER(sl_field), C.POINTER(sl_options)]
+        L.sl_step.argtypes = [vp, C.c_double, C.c_int]
+        L.sl_moments.argtypes = [vp, _dp, _dp]
+        L.sl_moments_device.argtypes = [vp, vp, vp]
+        L.sl_dt_max.argtypes = [vp, _dp]
+        L.sl_step_count.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.sl_set_step_count.argtypes = [vp, C.c_longlong]
+        L.sl_get_samples.argtypes = [vp, C.c_int, C.c_int, _dp]
+        L.sl_set_samples.argtypes = [vp, C.c_int, C.c_int, _dp]
+        L.sl_wiener.argtypes = [vp, C.c_longlong, C.c_int, C.c_double, _dp]
+        L.sl_profile.argtypes = [vp, C.c_int]
+        L.sl_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
+        L.sl_free.argtypes = [vp]
+        L.sl_free.restype = None
+        L.sl_strerror.argtypes = [C.c_int]
+        L.sl_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def sl_strerror(code):
+    try:
+        return lib().sl_strerror(int(code)).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SLError(rc, where)
+
+
+def _field(kind_map, spec):
+    f = sl_field()
+    kind, p = spec
+    f.kind = kind_map[kind]
+    for i, v in enumerate(p):
+        f.p[i] = float(v)
+    return f
+
+
+def _mesh(pb):
+    m = sl_mesh()
+    m.dim = pb["dim"]
+    for d in range(pb["dim"]):
+        m.K[d] = pb["K"][d]
+        m.lo[d] = pb["lo"][d]
+        m.hi[d] = pb["hi"][d]
+        m.periodic[d] = 1
+    return m
+
+
+def _f64p(a):
+    return a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, device=-1, phi0_nodal=None,
+            sample0=0):
+    """Returns an opaque context handle (int).  `stream` is a cudaStream_t
+    handle (int) or None."""
+    mesh = _mesh(pb)
+    u = _field(_U, pb["drift"])
+    D = _field(_D, pb["diffusion"])
+    keep = None
+    if phi0_nodal is not None:
+        keep = np.ascontiguousarray(phi0_nodal, dtype=np.float64)
+        phi = sl_field()
+        phi.kind = _PHI["nodal"]
+        phi.nodal = _f64p(keep)
+    else:
+        phi = _field(_PHI, pb["phi0"])
+    opt = sl_options()
+    opt.seed = int(pb["seed"] if seed is None else seed)
+    opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt.strict_dt = 1 if strict_dt else 0
+    opt.stream = C.c_void_p(stream) if stream else None
+    opt.device = device
+    opt.sample0 = int(sample0)
+    h = C.c_void_p()
+    _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
+                         C.byref(opt)), "sl_init")
+    return h.value
+
+
+def sl_step(ctx, dt, steps):
+    _check(lib().sl_step(C.c_void_p(ctx), float(dt), int(steps)), "sl_step")
+
+
+def sl_moments(ctx, V, want_m2=True):
+    mean = np.zeros(V)
+    m2 = np.zeros(V) if want_m2 else None
+    _check(lib().sl_moments(C.c_void_p(ctx), _f64p(mean), _f64p(m2) if want_m2 else None), "sl_moments")
+    return mean, m2
+
+
+def sl_moments_device(ctx, d_mean_ptr, d_m2_ptr=None):
+    _check(lib().sl_moments_device(C.c_void_p(ctx), C.c_void_p(d_mean_ptr),
+                                   C.c_void_p(d_m2_ptr) if d_m2_ptr else None), "sl_moments_device")
+
+
+def sl_dt_max(ctx):
+    v = C.c_double()
+    _check(lib().sl_dt_max(C.c_void_p(ctx), C.byref(v)), "sl_dt_max")
+    return v.value
+
+
+def sl_step_count(ctx):
+    v = C.c_longlong()
+    _check(lib().sl_step_count(C.c_void_p(ctx), C.byref(v)), "sl_step_count")
+    return v.value
+
+
+def sl_set_step_count(ctx, n):
+    _check(lib().sl_set_step_count(C.c_void_p(ctx), int(n)), "sl_set_step_count")
+
+
+def sl_get_samples(ctx, s0, count, V):
+    out = np.zeros((count, V))
+    _check(lib().sl_get_samples(C.c_void_p(ctx), s0, count, _f64p(out)), "sl_get_samples")
+    return out
+
+
+def sl_set_samples(ctx, s0, states):
+    a = np.ascontiguousarray(states, dtype=np.float64)
+    _check(lib().sl_set_samples(C.c_void_p(ctx), s0, a.shape[0], _f64p(a)), "sl_set_samples")
+
+
+def sl_wiener(ctx, step0, nsteps, dt, M, dim):
+    out = np.zeros((nsteps, M, dim))
+    _check(lib().sl_wiener(C.c_void_p(ctx), int(step0), int(nsteps), float(dt), _f64p(out)), "sl_wiener")
+    return out
+
+
+def sl_profile(ctx, enable):
+    _check(lib().sl_profile(C.c_void_p(ctx), 1 if enable else 0), "sl_profile")
+
+
+def sl_profile_read(ctx):
+    ms = C.c_double()
+    n = C.c_longlong()
+    _check(lib().sl_profile_read(C.c_void_p(ctx), C.byref(ms), C.byref(n)), "sl_profile_read")
+    return ms.value, n.value
+
+
+def sl_free(ctx):
+    if ctx:
+        lib().sl_free(C.c_void_p(ctx))
+
+
+# ------------------------------------------------------------------ convenience
+class Solver:
+    """One solver context for a problem dict (see ``sl_inputs``)."""
+
+    def __init__(self, pb, precision="fp64", seed=None, stream=None, strict_dt=False, phi0_nodal=None,
+                 sample0=0):
+        self.pb = pb
+        self.E = int(np.prod(pb["K"]))
+        self.n = pb["N"] ** pb["dim"]
+        self.V = self.E * self.n
+        self.M = pb["M"]
+        self.dim = pb["dim"]
+        self.ctx = sl_init(pb, precision, seed, stream, strict_dt, phi0_nodal=phi0_nodal, sample0=sample0)
+
+    def step(self, dt=None, steps=None):
+        sl_step(self.ctx, self.pb["dt"] if dt is None else dt, self.pb["steps"] if steps is None else steps)
+
+    def moments(self, want_m2=True):
+        mean, m2 = sl_moments(self.ctx, self.V, want_m2)
+        return mean.reshape(self.E, self.n), (m2.reshape(self.E, self.n) if m2 is not None else None)
+
+    def moments_device(self, mean_t, m2_t=None):
+        sl_moments_device(self.ctx, mean_t.data_ptr(), m2_t.data_ptr() if m2_t is not None else None)
+
+    def samples(self, s0=0, count=None):
+        count = self.M - s0 if count is None else count
+        return sl_get_samples(self.ctx, s0, count, self.V).reshape(count, self.E, self.n)
+
+    def set_samples(self, s0, states):
+        sl_set_samples(self.ctx, s0, np.asarray(states).reshape(-1, self.V))
+
+    def wiener(self, step0, nsteps, dt=None):
+        return sl_wiener(self.ctx, step0, nsteps, self.pb["dt"] if dt is None else dt, self.M, self.dim)
+
+    def profile(self, enable=True):
+        sl_profile(self.ctx, enable)
+
+    def profile_read(self):
+        """(summed step-kernel milliseconds, launches) since the last read."""
+        return sl_profile_read(self.ctx)
+
+    @property
+    def dt_max(self):
+        return sl_dt_max(self.ctx)
+
+    @property
+    def step_count(self):
+        return sl_step_count(self.ctx)
+
+    @step_count.setter
+    def step_count(self, n):
+        sl_set_step_count(self.ctx, n)
+
+    def close(self):
+        if self.ctx:
+            sl_free(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

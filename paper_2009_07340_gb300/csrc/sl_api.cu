@@ -1,0 +1,499 @@
+// sl_api.cu -- the C ABI declared in include/sl.h: argument checking, device
+// memory ownership, launch geometry and the step loop.  All arithmetic of the
+// method runs in the kernels of sl_step1d*.cu, sl_step2d.cu and sl_setup.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "sl_internal.cuh"
+
+struct sl_ctx {
+    sl::Mesh m;
+    int M = 0;
+    int precision = SL_FP64;
+    int strict_dt = 0;
+    unsigned long long seed = 0;
+    long long sample0 = 0;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    long long step = 0;
+    int poisoned = 0;
+    double dtmax = 0.0;
+    // device memory owned by the context
+    double *xi = nullptr, *nodeU = nullptr, *nodeB = nullptr, *nodeDiv = nullptr;
+    double *faceU = nullptr, *faceB = nullptr;
+    void *Q = nullptr;
+    size_t state_elem = 8;
+    double *dW = nullptr;
+    int dW_cap = 0;  // steps the Wiener scratch holds
+    double *psum = nullptr, *psq = nullptr, *mean_tmp = nullptr, *m2_tmp = nullptr;
+    int mom_chunk = 64;
+    int *err = nullptr;
+    void *faces2d = nullptr;  // 2D face-value scratch
+    // 1D launch geometry
+    int S = 1, C = 1, T = 1;
+    // kernel timing hook
+    int profiling = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+};
+
+namespace {
+
+constexpr size_t kWienerScratchBytes = size_t(64) << 20;
+
+int fail_cuda(sl_ctx *c)
+{
+    if (c) c->poisoned = 1;
+    return SL_ERR_CUDA;
+}
+
+bool valid_kind(int dim, int what, const sl_field *f)
+{
+    if (!f) return false;
+    const int k = f->kind;
+    if (what == 0)
+        return k == SL_U_CONST || (dim == 1 && k == SL_U_SIN) || (dim == 2 && k == SL_U_ROTATION);
+    if (what == 1) return k == SL_D_CONST || k == SL_D_COS || (dim == 2 && k == SL_D_SINSIN);
+    if (k == SL_PHI_NODAL) return f->nodal != nullptr;
+    if (k == SL_PHI_FOURIER) return dim == 1 && f->p[2] >= 0 && f->p[2] <= 18;
+    return k == SL_PHI_GAUSS || (dim == 1 && k == SL_PHI_SINE) || (dim == 2 && k == SL_PHI_SINSIN);
+}
+
+sl::FieldDev to_dev(const sl_field *f)
+{
+    sl::FieldDev d;
+    d.kind = f->kind;
+    std::memcpy(d.p, f->p, sizeof(d.p));
+    return d;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// Chebyshev-Gauss nodes (host copy for the time-step guard only).
+double host_min_gap(int N)
+{
+    double g = 1.0;
+    for (int i = 0; i + 1 < N; ++i) {
+        const double a = 0.5 * (1.0 - std::cos((i + 0.5) * M_PI / N));
+        const double b = 0.5 * (1.0 - std::cos((i + 1.5) * M_PI / N));
+        g = std::min(g, b - a);
+    }
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sl_strerror(int code)
+{
+    switch (code) {
+    case SL_OK: return "ok";
+    case SL_ERR_ARG: return "invalid argument";
+    case SL_ERR_DT: return "time step above the particle-gap bound";
+    case SL_ERR_OOM: return "device allocation failed";
+    case SL_ERR_CUDA: return "CUDA error";
+    case SL_ERR_SINGULAR: return "non-finite remap (coincident advected particles)";
+    case SL_ERR_TIMEOUT: return "bounded device wait expired";
+    case SL_ERR_STATE: return "context poisoned by an earlier error";
+    case SL_ERR_UNSUPPORTED: return "not supported";
+    default: return "unknown error";
+    }
+}
+
+void sl_free(sl_ctx *c)
+{
+    if (!c) return;
+    for (auto &ev : c->events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    cudaFree(c->xi);
+    cudaFree(c->nodeU);
+    cudaFree(c->nodeB);
+    cudaFree(c->nodeDiv);
+    cudaFree(c->faceU);
+    cudaFree(c->faceB);
+    cudaFree(c->Q);
+    cudaFree(c->dW);
+    cudaFree(c->psum);
+    cudaFree(c->psq);
+    cudaFree(c->mean_tmp);
+    cudaFree(c->m2_tmp);
+    cudaFree(c->err);
+    cudaFree(c->faces2d);
+    delete c;
+}
+
+int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift, const sl_field *diffusion,
+            const sl_field *phi0, const sl_options *opt)
+{
+    if (!out) return SL_ERR_ARG;
+    *out = nullptr;
+    if (!mesh || (mesh->dim != 1 && mesh->dim != 2)) return SL_ERR_ARG;
+    const int dim = mesh->dim;
+    if (N < 2 || N > sl::kMaxN || M < 1) return SL_ERR_ARG;
+    for (int d = 0; d < dim; ++d) {
+        if (mesh->K[d] < 1 || !(mesh->hi[d] > mesh->lo[d]) || !std::isfinite(mesh->hi[d] - mesh->lo[d]))
+            return SL_ERR_ARG;
+        if (!mesh->periodic[d]) return SL_ERR_UNSUPPORTED;
+    }
+    if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion) || !valid_kind(dim, 2, phi0))
+        return SL_ERR_ARG;
+    if (diffusion->kind != SL_D_CONST && std::fabs(diffusion->p[1]) > 1.0) return SL_ERR_ARG;  // D >= 0
+    if (diffusion->p[0] < 0.0) return SL_ERR_ARG;
+    const int precision = opt ? opt->precision : SL_FP64;
+    if (precision != SL_FP64 && precision != SL_MIXED && precision != SL_FP32) return SL_ERR_ARG;
+    if (dim == 1 && mesh->K[0] > sl::kMaxThreads1D * sl::kMaxCluster1D) return SL_ERR_UNSUPPORTED;
+    if (opt && (opt->sample0 < 0 || opt->sample0 + M > (1ll << 32))) return SL_ERR_ARG;
+
+    if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
+    sl_ctx *c = new (std::nothrow) sl_ctx;
+    if (!c) return SL_ERR_OOM;
+    cudaGetDevice(&c->device);
+    c->precision = precision;
+    c->seed = opt ? opt->seed : 0ull;
+    c->sample0 = opt ? opt->sample0 : 0ll;
+    c->strict_dt = opt ? opt->strict_dt : 0;
+    c->st = opt ? static_cast<cudaStream_t>(opt->stream) : nullptr;
+    c->M = M;
+    sl::Mesh &m = c->m;
+    m.dim = dim;
+    m.N = N;
+    m.n = dim == 2 ? N * N : N;
+    m.K[0] = mesh->K[0];
+    m.K[1] = dim == 2 ? mesh->K[1] : 1;
+    m.E = m.K[0] * m.K[1];
+    for (int d = 0; d < 2; ++d) {
+        m.lo[d] = d < dim ? mesh->lo[d] : 0.0;
+        m.hi[d] = d < dim ? mesh->hi[d] : 1.0;
+        m.h[d] = (m.hi[d] - m.lo[d]) / m.K[d];
+    }
+    const long long V = (long long)m.E * m.n;
+    c->state_elem = precision == SL_FP64 ? sizeof(double) : sizeof(float2);  // FP32 modes: hi + lo pair
+    const int nf = dim == 1 ? m.E : 2 * m.E * N;
+    c->mom_chunk = 64;
+    const int nc = (M + c->mom_chunk - 1) / c->mom_chunk;
+    bool ok = dalloc(&c->xi, N) == cudaSuccess && dalloc(&c->nodeU, size_t(dim) * V) == cudaSuccess &&
+              dalloc(&c->nodeB, V) == cudaSuccess && dalloc(&c->nodeDiv, V) == cudaSuccess &&
+              dalloc(&c->faceU, nf) == cudaSuccess && dalloc(&c->faceB, nf) == cudaSuccess &&
+              cudaMalloc(&c->Q, size_t(M) * V * c->state_elem) == cudaSuccess &&
+              dalloc(&c->psum, size_t(nc) * V) == cudaSuccess && dalloc(&c->psq, size_t(nc) * V) == cudaSuccess &&
+              dalloc(&c->mean_tmp, V) == cudaSuccess && dalloc(&c->m2_tmp, V) == cudaSuccess &&
+              dalloc(&c->err, 1) == cudaSuccess;
+    if (ok && dim == 2)
+        ok = cudaMalloc(&c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        sl_free(c);
+        return SL_ERR_OOM;
+    }
+    double *nodal_dev = nullptr;
+    if (phi0->kind == SL_PHI_NODAL) {
+        if (cudaMalloc(&nodal_dev, V * sizeof(double)) != cudaSuccess ||
+            cudaMemcpy(nodal_dev, phi0->nodal, V * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(nodal_dev);
+            sl_free(c);
+            return SL_ERR_OOM;
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+    if (e == cudaSuccess)
+        e = sl::launch_init_fields(m, to_dev(drift), to_dev(diffusion), to_dev(phi0), nodal_dev, c->xi, c->nodeU,
+                                   c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M, precision == SL_FP64, c->st);
+    // maxima for the time-step guard (host copy of the node coefficients)
+    std::vector<double> hu(size_t(dim) * V), hb(V);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess) e = cudaMemcpy(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(nodal_dev);
+    if (e != cudaSuccess) {
+        sl_free(c);
+        return SL_ERR_CUDA;
+    }
+    double best = INFINITY;
+    const double gap = host_min_gap(N);
+    double bmax = 0.0;
+    for (double b : hb) bmax = std::max(bmax, b);
+    for (int d = 0; d < dim; ++d) {
+        double umax = 0.0;
+        for (long long v = 0; v < V; ++v) umax = std::max(umax, std::fabs(hu[size_t(d) * V + v]));
+        const double dx = gap * m.h[d];
+        double dt;
+        if (umax == 0.0)
+            dt = bmax > 0.0 ? dx * dx / (bmax * bmax) : INFINITY;
+        else {
+            const double s = (-bmax + std::sqrt(bmax * bmax + 4.0 * umax * dx)) / (2.0 * umax);
+            dt = s * s;
+        }
+        best = std::min(best, dt);
+    }
+    c->dtmax = best;
+
+    if (dim == 1) {
+        const int K = m.K[0];
+        if (K <= sl::kMaxThreads1D) {
+            c->C = 1;
+            c->T = K;
+            c->S = std::max(1, std::min(sl::kMaxThreads1D / K, M));
+        } else {
+            c->C = (K + sl::kMaxThreads1D - 1) / sl::kMaxThreads1D;
+            c->T = (K + c->C - 1) / c->C;
+            c->S = 1;
+        }
+    }
+    *out = c;
+    return SL_OK;
+}
+
+int sl_dt_max(const sl_ctx *c, double *dt)
+{
+    if (!c || !dt) return SL_ERR_ARG;
+    *dt = c->dtmax;
+    return SL_OK;
+}
+
+int sl_step_count(const sl_ctx *c, long long *n)
+{
+    if (!c || !n) return SL_ERR_ARG;
+    *n = c->step;
+    return SL_OK;
+}
+
+int sl_set_step_count(sl_ctx *c, long long n)
+{
+    if (!c || n < 0) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    c->step = n;
+    return SL_OK;
+}
+
+int sl_step(sl_ctx *c, double dt, int steps)
+{
+    if (!c) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    if (!(dt > 0.0) || !std::isfinite(dt) || steps < 0) return SL_ERR_ARG;
+    if (c->strict_dt && dt > c->dtmax * (1.0 + 1e-12)) return SL_ERR_DT;
+    if (steps == 0) return SL_OK;
+    const sl::Mesh &m = c->m;
+    const int dim = m.dim;
+    const size_t per_step = size_t(c->M) * dim * sizeof(double);
+    const int chunk = int(std::max<size_t>(1, std::min<size_t>(size_t(steps), kWienerScratchBytes / per_step)));
+    if (chunk > c->dW_cap) {
+        cudaFree(c->dW);
+        c->dW = nullptr;
+        c->dW_cap = 0;
+        if (cudaMalloc(&c->dW, chunk * per_step) != cudaSuccess) {
+            cudaGetLastError();
+            return SL_ERR_OOM;
+        }
+        c->dW_cap = chunk;
+    }
+    const double sqrt_dt = std::sqrt(dt);
+    for (int done = 0; done < steps;) {
+        const int n = std::min(chunk, steps - done);
+        cudaError_t e = sl::launch_wiener(c->seed, c->step, c->sample0, n, c->M, dim, sqrt_dt, c->dW, c->st);
+        if (e != cudaSuccess) return fail_cuda(c);
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (c->profiling) {
+            if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess ||
+                cudaEventRecord(ev.first, c->st) != cudaSuccess)
+                return fail_cuda(c);
+            c->events.push_back(ev);
+        }
+        if (dim == 1) {
+            sl::Step1DArgs a;
+            a.K = m.K[0];
+            a.M = c->M;
+            a.S = c->S;
+            a.C = c->C;
+            a.T = c->T;
+            a.nsteps = n;
+            a.dt = dt;
+            a.h = m.h[0];
+            a.xi = c->xi;
+            a.nodeU = c->nodeU;
+            a.nodeB = c->nodeB;
+            a.nodeDiv = c->nodeDiv;
+            a.faceU = c->faceU;
+            a.faceB = c->faceB;
+            a.dW = c->dW;
+            a.Q = c->Q;
+            a.err = c->err;
+            if (c->precision == SL_FP64)
+                e = sl::launch_step1d_fp64(a, m.N, c->st);
+            else if (c->precision == SL_MIXED)
+                e = sl::launch_step1d_mixed(a, m.N, c->st);
+            else
+                e = sl::launch_step1d_fp32(a, m.N, c->st);
+        } else {
+            sl::Step2DArgs a;
+            a.Kx = m.K[0];
+            a.Ky = m.K[1];
+            a.M = c->M;
+            a.nsteps = n;
+            a.dt = dt;
+            a.hx = m.h[0];
+            a.hy = m.h[1];
+            a.xi = c->xi;
+            a.nodeU = c->nodeU;
+            a.nodeB = c->nodeB;
+            a.nodeDiv = c->nodeDiv;
+            a.faceU = c->faceU;
+            a.faceB = c->faceB;
+            a.dW = c->dW;
+            a.Q = c->Q;
+            a.faces = c->faces2d;
+            a.err = c->err;
+            e = sl::launch_step2d(a, m.N, c->precision, c->st);
+        }
+        if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return fail_cuda(c);
+        if (c->profiling && cudaEventRecord(ev.second, c->st) != cudaSuccess) return fail_cuda(c);
+        c->step += n;
+        done += n;
+    }
+    return SL_OK;
+}
+
+static int check_device_error(sl_ctx *c)
+{
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+        return fail_cuda(c);
+    if (h & 1) {
+        c->poisoned = 1;
+        return SL_ERR_SINGULAR;
+    }
+    if (h & 2) {
+        c->poisoned = 1;
+        return SL_ERR_TIMEOUT;
+    }
+    return SL_OK;
+}
+
+int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2)
+{
+    if (!c || !d_mean) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const long long V = (long long)c->m.E * c->m.n;
+    if (sl::launch_moments(c->Q, c->precision == SL_FP64, c->M, V, c->mom_chunk, c->psum, c->psq, d_mean, d_m2,
+                           c->st) != cudaSuccess)
+        return fail_cuda(c);
+    return SL_OK;
+}
+
+int sl_moments(sl_ctx *c, double *mean, double *m2)
+{
+    if (!c || !mean) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const long long V = (long long)c->m.E * c->m.n;
+    int rc = sl_moments_device(c, c->mean_tmp, m2 ? c->m2_tmp : nullptr);
+    if (rc != SL_OK) return rc;
+    if (cudaMemcpyAsync(mean, c->mean_tmp, V * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return fail_cuda(c);
+    if (m2 && cudaMemcpyAsync(m2, c->m2_tmp, V * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return fail_cuda(c);
+    return check_device_error(c);
+}
+
+int sl_get_samples(sl_ctx *c, int s0, int count, double *out)
+{
+    if (!c || !out || s0 < 0 || count < 0 || s0 + count > c->M) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const size_t V = size_t(c->m.E) * c->m.n;
+    const size_t n = V * count;
+    if (c->precision == SL_FP64) {
+        if (cudaMemcpyAsync(out, static_cast<double *>(c->Q) + V * s0, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->st) != cudaSuccess)
+            return fail_cuda(c);
+    } else {
+        std::vector<float2> tmp(n);
+        if (cudaMemcpyAsync(tmp.data(), static_cast<float2 *>(c->Q) + V * s0, n * sizeof(float2),
+                            cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess)
+            return fail_cuda(c);
+        for (size_t i = 0; i < n; ++i) out[i] = double(tmp[i].x) + double(tmp[i].y);
+    }
+    return check_device_error(c);
+}
+
+int sl_set_samples(sl_ctx *c, int s0, int count, const double *in)
+{
+    if (!c || !in || s0 < 0 || count < 0 || s0 + count > c->M) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const size_t V = size_t(c->m.E) * c->m.n;
+    const size_t n = V * count;
+    cudaError_t e;
+    if (c->precision == SL_FP64) {
+        e = cudaMemcpyAsync(static_cast<double *>(c->Q) + V * s0, in, n * sizeof(double), cudaMemcpyHostToDevice,
+                            c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    } else {
+        std::vector<float2> tmp(n);
+        for (size_t i = 0; i < n; ++i) {
+            const float hi = float(in[i]);
+            tmp[i] = make_float2(hi, float(in[i] - double(hi)));
+        }
+        e = cudaMemcpyAsync(static_cast<float2 *>(c->Q) + V * s0, tmp.data(), n * sizeof(float2),
+                            cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    }
+    return e == cudaSuccess ? SL_OK : fail_cuda(c);
+}
+
+int sl_profile(sl_ctx *c, int enable)
+{
+    if (!c) return SL_ERR_ARG;
+    c->profiling = enable ? 1 : 0;
+    return SL_OK;
+}
+
+int sl_profile_read(sl_ctx *c, double *kernel_ms, long long *launches)
+{
+    if (!c || !kernel_ms || !launches) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    double total = 0.0;
+    for (auto &ev : c->events) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(ev.second) != cudaSuccess || cudaEventElapsedTime(&ms, ev.first, ev.second) != cudaSuccess)
+            return fail_cuda(c);
+        total += ms;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    *kernel_ms = total;
+    *launches = (long long)c->events.size();
+    c->events.clear();
+    return SL_OK;
+}
+
+int sl_wiener(sl_ctx *c, long long step0, int nsteps, double dt, double *out)
+{
+    if (!c || !out || nsteps < 0 || step0 < 0 || !(dt > 0.0)) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const size_t n = size_t(nsteps) * c->M * c->m.dim;
+    if (n == 0) return SL_OK;
+    double *d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_OOM;
+    }
+    cudaError_t e = sl::launch_wiener(c->seed, step0, c->sample0, nsteps, c->M, c->m.dim, std::sqrt(dt), d, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(d);
+    return e == cudaSuccess ? SL_OK : fail_cuda(c);
+}
+
+}  // extern "C"

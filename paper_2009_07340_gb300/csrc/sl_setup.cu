@@ -1,0 +1,260 @@
+// sl_setup.cu -- device kernels around the step: reference nodes, prescribed
+// fields at the nodes and faces, the initial state (Section 5.1), the Wiener
+// increments (Section 5.2) and the sample moments (Section 5.4).
+#include <cmath>
+
+#include "sl_internal.cuh"
+#include "sl_rng.cuh"
+
+namespace sl {
+
+// Chebyshev-Gauss nodes on [0,1]: xi_i = (1 - cos((i + 1/2) pi / N)) / 2
+// (Eq. gaussquad with (i+1/2)/N, interleaved with the Lobatto nodes).
+__device__ __forceinline__ double gauss_node(int i, int N) { return 0.5 * (1.0 - cospi((i + 0.5) / N)); }
+
+// d h_m / d xi at x for the Lagrange basis on the Gauss nodes (product rule).
+__device__ double lagrange_deriv(int N, int m, double x)
+{
+    double sum = 0.0;
+    const double xm = gauss_node(m, N);
+    for (int k = 0; k < N; ++k) {
+        if (k == m) continue;
+        double v = 1.0 / (xm - gauss_node(k, N));
+        for (int l = 0; l < N; ++l)
+            if (l != m && l != k) v *= (x - gauss_node(l, N)) / (xm - gauss_node(l, N));
+        sum += v;
+    }
+    return sum;
+}
+
+__device__ void drift_at(const FieldDev &f, double x, double y, double &ux, double &uy)
+{
+    const double *p = f.p;
+    switch (f.kind) {
+    case SL_U_CONST: ux = p[0]; uy = p[1]; break;
+    case SL_U_SIN: ux = p[0] + p[1] * sin(p[2] * M_PI * x); uy = 0.0; break;
+    default: ux = -p[0] * (y - p[2]); uy = p[0] * (x - p[1]); break;  // SL_U_ROTATION
+    }
+}
+
+__device__ double diffusion_at(const FieldDev &f, double x, double y)
+{
+    const double *p = f.p;
+    switch (f.kind) {
+    case SL_D_CONST: return p[0];
+    case SL_D_COS: return p[0] * (1.0 + p[1] * cos(p[2] * M_PI * x));
+    default: return p[0] * (1.0 + p[1] * sin(p[2] * M_PI * x) * sin(p[3] * M_PI * y));  // SL_D_SINSIN
+    }
+}
+
+__device__ double phi0_at(const FieldDev &f, const Mesh &m, double x, double y)
+{
+    const double *p = f.p;
+    switch (f.kind) {
+    case SL_PHI_GAUSS: {
+        const double Lx = m.hi[0] - m.lo[0], Ly = m.hi[1] - m.lo[1];
+        const int ny = m.dim == 2 ? 1 : 0;
+        double v = 0.0;
+        for (int ix = -1; ix <= 1; ++ix)
+            for (int iy = -ny; iy <= ny; ++iy) {
+                const double dx = x - p[2] + ix * Lx;
+                double r2 = dx * dx;
+                if (m.dim == 2) {
+                    const double dy = y - p[3] + iy * Ly;
+                    r2 += dy * dy;
+                }
+                v += exp(-r2 / (2.0 * p[1] * p[1]));
+            }
+        return p[0] * v;
+    }
+    case SL_PHI_FOURIER: {
+        double v = p[0];
+        const int nk = int(p[2]);
+        for (int k = 1; k <= nk; ++k)
+            v += p[3 + 2 * (k - 1)] * cos(k * p[1] * M_PI * x) + p[4 + 2 * (k - 1)] * sin(k * p[1] * M_PI * x);
+        return v;
+    }
+    case SL_PHI_SINE: return p[0] + p[1] * sin(2.0 * M_PI * p[2] * x);
+    default: return p[0] + p[1] * sin(2.0 * M_PI * p[2] * x) * sin(2.0 * M_PI * p[2] * y);  // SL_PHI_SINSIN
+    }
+}
+
+// One thread per node (e, p): physical coordinates, drift, sqrt(2D), the
+// divergence of the drift by spectral differentiation along the element's
+// grid lines (the paper takes du/dx from the DSEM solver, Section 5.2), and
+// the initial value written to every sample.
+__device__ __forceinline__ void store_state(double *Q, long long i, double v) { Q[i] = v; }
+__device__ __forceinline__ void store_state(float2 *Q, long long i, double v)
+{
+    const float hi = float(v);
+    Q[i] = make_float2(hi, float(v - double(hi)));
+}
+__device__ __forceinline__ double load_state(const double *Q, long long i) { return Q[i]; }
+__device__ __forceinline__ double load_state(const float2 *Q, long long i)
+{
+    const float2 v = Q[i];
+    return double(v.x) + double(v.y);
+}
+
+template <typename State>
+__global__ void init_nodes_kernel(Mesh m, FieldDev fu, FieldDev fD, FieldDev fphi, const double *phi0_nodal,
+                                  double *xi, double *nodeU, double *nodeB, double *nodeDiv, State *Q, int M)
+{
+    const long long V = (long long)m.E * m.n;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < m.N && blockIdx.x == 0) xi[v] = gauss_node(int(v), m.N);
+    if (v >= V) return;
+    const int e = int(v / m.n), p = int(v % m.n);
+    const int N = m.N;
+    const int kx = e % m.K[0], ky = e / m.K[0];
+    const int i = p % N, j = p / N;
+    const double x = m.lo[0] + (kx + gauss_node(i, N)) * m.h[0];
+    const double y = m.dim == 2 ? m.lo[1] + (ky + gauss_node(j, N)) * m.h[1] : 0.0;
+    double ux, uy;
+    drift_at(fu, x, y, ux, uy);
+    nodeU[v] = ux;
+    if (m.dim == 2) nodeU[V + v] = uy;
+    nodeB[v] = sqrt(2.0 * diffusion_at(fD, x, y));
+    // divergence
+    double dx = 0.0, dy = 0.0;
+    for (int l = 0; l < N; ++l) {
+        double uxl, uyl, dummy;
+        if (m.dim == 1) {
+            drift_at(fu, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], 0.0, uxl, dummy);
+            dx += lagrange_deriv(N, l, gauss_node(i, N)) * uxl;
+        } else {
+            drift_at(fu, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], y, uxl, dummy);
+            dx += lagrange_deriv(N, l, gauss_node(i, N)) * uxl;
+            drift_at(fu, x, m.lo[1] + (ky + gauss_node(l, N)) * m.h[1], dummy, uyl);
+            dy += lagrange_deriv(N, l, gauss_node(j, N)) * uyl;
+        }
+    }
+    nodeDiv[v] = dx / m.h[0] + (m.dim == 2 ? dy / m.h[1] : 0.0);
+    const double phi = phi0_nodal ? phi0_nodal[v] : phi0_at(fphi, m, x, y);
+    for (int s = 0; s < M; ++s) store_state(Q, (long long)s * V + v, phi);
+}
+
+// Interface coefficients.  1D: interface f (left face of element f) at
+// x_f = lo + f h.  2D: for each element the N points of its low-x face
+// (normal drift u_x) and of its low-y face (u_y), at the Gauss-node positions.
+__global__ void init_faces_kernel(Mesh m, FieldDev fu, FieldDev fD, double *faceU, double *faceB)
+{
+    const int nf = m.dim == 1 ? m.E : m.E * m.N;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nf) return;
+    double ux, uy;
+    if (m.dim == 1) {
+        const double xf = m.lo[0] + v * m.h[0];
+        drift_at(fu, xf, 0.0, ux, uy);
+        faceU[v] = ux;
+        faceB[v] = sqrt(2.0 * diffusion_at(fD, xf, 0.0));
+        return;
+    }
+    const int e = v / m.N, f = v % m.N;
+    const int kx = e % m.K[0], ky = e / m.K[0];
+    const double xv = m.lo[0] + kx * m.h[0], yv = m.lo[1] + (ky + gauss_node(f, m.N)) * m.h[1];
+    drift_at(fu, xv, yv, ux, uy);
+    faceU[v] = ux;
+    faceB[v] = sqrt(2.0 * diffusion_at(fD, xv, yv));
+    const double xh = m.lo[0] + (kx + gauss_node(f, m.N)) * m.h[0], yh = m.lo[1] + ky * m.h[1];
+    drift_at(fu, xh, yh, ux, uy);
+    faceU[nf + v] = uy;
+    faceB[nf + v] = sqrt(2.0 * diffusion_at(fD, xh, yh));
+}
+
+cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
+                               const double *phi0_nodal_dev, double *xi, double *nodeU, double *nodeB,
+                               double *nodeDiv, double *faceU, double *faceB, void *Q, int M,
+                               int state_is_double, cudaStream_t st)
+{
+    const long long V = (long long)m.E * m.n;
+    const int tb = 128;
+    const unsigned nb = unsigned((V + tb - 1) / tb);
+    if (state_is_double)
+        init_nodes_kernel<double><<<nb, tb, 0, st>>>(m, u, D, phi0, phi0_nodal_dev, xi, nodeU, nodeB, nodeDiv,
+                                                     static_cast<double *>(Q), M);
+    else
+        init_nodes_kernel<float2><<<nb, tb, 0, st>>>(m, u, D, phi0, phi0_nodal_dev, xi, nodeU, nodeB, nodeDiv,
+                                                     static_cast<float2 *>(Q), M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nf = m.dim == 1 ? m.E : m.E * m.N;
+    init_faces_kernel<<<(nf + tb - 1) / tb, tb, 0, st>>>(m, u, D, faceU, faceB);
+    return cudaGetLastError();
+}
+
+// dW[t][s][d] = sqrt(dt) z_d for step counter step0 + t and sample
+// sample0 + s.
+__global__ void wiener_kernel(unsigned long long seed, long long step0, long long sample0, int nsteps, int M,
+                              int dim, double sqrt_dt, double *out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nsteps * M) return;
+    const int t = int(idx / M), s = int(idx % M);
+    const double2 z = normal_pair(seed, uint32_t(step0 + t), uint32_t(sample0 + s), 0u);
+    out[idx * dim] = __dmul_rn(sqrt_dt, z.x);
+    if (dim == 2) out[idx * dim + 1] = __dmul_rn(sqrt_dt, z.y);
+}
+
+cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sample0, int nsteps, int M,
+                          int dim, double sqrt_dt, double *out, cudaStream_t st)
+{
+    const long long n = (long long)nsteps * M;
+    if (n == 0) return cudaSuccess;
+    const int tb = 128;
+    wiener_kernel<<<unsigned((n + tb - 1) / tb), tb, 0, st>>>(seed, step0, sample0, nsteps, M, dim, sqrt_dt, out);
+    return cudaGetLastError();
+}
+
+// Moments, Eq. (averaged), in a fixed summation order: chunk c of `chunk`
+// consecutive samples is summed in ascending sample order into partials
+// [c][V]; the partials are then added in ascending c.  FP64 throughout.
+template <typename State>
+__global__ void moments_partial_kernel(const State *__restrict__ Q, int M, long long V, int chunk,
+                                       double *__restrict__ psum, double *__restrict__ psq)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int c = blockIdx.y;
+    const int s0 = c * chunk, s1 = min(M, s0 + chunk);
+    double a = 0.0, b = 0.0;
+    for (int s = s0; s < s1; ++s) {
+        const double x = load_state(Q, (long long)s * V + v);
+        a += x;
+        b = fma(x, x, b);
+    }
+    psum[(long long)c * V + v] = a;
+    psq[(long long)c * V + v] = b;
+}
+
+__global__ void moments_final_kernel(const double *__restrict__ psum, const double *__restrict__ psq, int nc,
+                                     long long V, int M, double *__restrict__ mean, double *__restrict__ m2)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        a += psum[(long long)c * V + v];
+        b += psq[(long long)c * V + v];
+    }
+    mean[v] = a / M;
+    if (m2) m2[v] = b / M;
+}
+
+cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
+                           double *psq, double *mean, double *m2, cudaStream_t st)
+{
+    const int tb = 256;
+    const int nc = (M + chunk - 1) / chunk;
+    dim3 g1(unsigned((V + tb - 1) / tb), unsigned(nc));
+    if (state_is_double)
+        moments_partial_kernel<double><<<g1, tb, 0, st>>>(static_cast<const double *>(Q), M, V, chunk, psum, psq);
+    else
+        moments_partial_kernel<float2><<<g1, tb, 0, st>>>(static_cast<const float2 *>(Q), M, V, chunk, psum, psq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, M, mean, m2);
+    return cudaGetLastError();
+}
+
+}  // namespace sl

@@ -42,6 +42,7 @@ import numpy as np
 # stated once here as plain numbers so that every consumer runs the same dt.
 DT_CFG1 = 6.510e-4  # K=8, N=6, u=1, D=0.01, edge gap: particles stay in-element at 1 sigma
 DT_CFG2 = 7.33e-7   # K=256, N=16 node gap, |u|max=1.5, Dmax=0.015 (used for every N)
+DT_CFG2_HALF = 3.665e-7  # half of it: at DT_CFG2 itself the N=16 step amplifies perturbations
 DT_CFG3 = 6.93e-5   # 64x64, N=8 node gap, |u_j|max=pi, Dmax=0.0065
 
 
@@ -83,11 +84,12 @@ def fourier_phi0(seed=2, modes=8):
     return ("fourier", p)
 
 
-def config2(N=16, M=4096, steps=1000, K=256):
+def config2(N=16, M=4096, steps=1000, K=256, dt=DT_CFG2):
     """1D non-constant drift-diffusion, periodic [0,2], K=256, N in {4,8,12,16},
     M=4096, u = 1 + 0.5 sin(pi x), D = 0.01 (1 + 0.5 cos(pi x)), random
-    8-mode Fourier phi0 (seed 2), 1000 steps at the N=16 stable dt."""
-    return problem(1, (K,), (0.0,), (2.0,), N, M, steps, DT_CFG2, 2,
+    8-mode Fourier phi0 (seed 2), 1000 steps at the N=16 particle-gap dt (or
+    the dt given)."""
+    return problem(1, (K,), (0.0,), (2.0,), N, M, steps, dt, 2,
                    ("sin", [1.0, 0.5, 1.0]), ("cos", [0.01, 0.5, 1.0]), fourier_phi0(2))
 
 

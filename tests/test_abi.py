@@ -1,0 +1,70 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU,
+exports every entry point that include/sl.h declares, and rejects invalid
+arguments before touching the device."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import sl_inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def sl():
+    from paper_2009_07340_gb300 import build
+
+    build.build()
+    import paper_2009_07340_gb300 as sl
+
+    return sl
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sl_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(sl):
+    names = _declared()
+    assert {"sl_init", "sl_step", "sl_moments", "sl_moments_device", "sl_free"} <= names
+    L = C.CDLL(os.path.join(ROOT, "paper_2009_07340_gb300", "libsl.so"))
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_strerror(sl):
+    assert sl.sl_strerror(0) == "ok"
+    assert "argument" in sl.sl_strerror(-1)
+    assert sl.sl_strerror(-999) == "unknown error"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(N=1), dict(N=17), dict(M=0), dict(K=(0,)), dict(hi=(0.0,)),
+    dict(diffusion=("cos", [0.01, 1.5, 1.0])), dict(diffusion=("const", [-1.0])),
+    dict(drift=("rotation", [1.0, 0.5, 0.5])), dict(phi0=("sinsin", [1.0, 1.0, 1.0])),
+])
+def test_invalid_arguments_rejected_before_device(sl, bad):
+    pb = I.config1()
+    pb.update(bad)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_init(pb)
+    assert e.value.code == -1
+
+
+def test_invalid_precision_and_null(sl):
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_init(I.config1(), precision=7)
+    assert e.value.code == -1
+    L = sl.lib()
+    assert L.sl_step(None, 1e-3, 1) == -1
+    assert L.sl_moments(None, None, None) == -1
+    L.sl_free(None)  # no-op

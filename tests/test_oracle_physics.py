@@ -165,3 +165,24 @@ def test_moment_bookkeeping(orc):
     # thread split changes only the summation grouping
     r4 = orc.run(pb, ns=6, nthreads=3)
     assert np.allclose(r4["sum"], r["sum"], rtol=1e-14)
+
+
+def test_amplification_at_the_bound(orc):
+    # K=256, N=16: at dt = 7.33e-7 (the Eq. (1d_timestep) node-gap bound of
+    # this order) near-edge particles leave the element at one standard
+    # deviation and a perturbation of the state grows by ~0.85 % per step;
+    # at half that dt it stays bounded.  Measured on the oracle alone: two
+    # runs from phi0 and phi0 + 1e-10 noise with the same increments.
+    def growth(frac, steps):
+        pb = I.config2(N=16, M=1, steps=steps)
+        pb["dt"] = frac * I.DT_CFG2
+        q0 = orc.init_state(pb)
+        p0 = q0 + 1e-10 * np.random.default_rng(0).normal(size=q0.shape)
+        a = orc.run(pb, ns=1, state_in=q0[None], want_states=True)["states"][0]
+        b = orc.run(pb, ns=1, state_in=p0[None], want_states=True)["states"][0]
+        return np.abs(a - b).max() / 1e-10
+
+    g_bound = growth(1.0, 400)
+    g_half = growth(0.5, 400)
+    assert g_bound > 30.0
+    assert g_half < 10.0
