@@ -163,6 +163,27 @@ int sl_wiener(sl_ctx *c, long long step0, int nsteps, double dt, double *out);
 int sl_profile(sl_ctx *c, int enable);
 int sl_profile_read(sl_ctx *c, double *kernel_ms, long long *launches);
 
+/* Allocation-free sample moments.  The paper has no counterpart: this entry  */
+/* exists for callers that cannot call cudaMalloc when they need the moments */
+/* (a serving loop whose HBM budget is fully reserved up front, code that     */
+/* must not let an allocation synchronise the device, a host framework that   */
+/* owns all device memory through its own pool).  No context is needed.     */
+/*   d_samples  device, FP64 [M][V] (sample-major), caller-owned, read only   */
+/*   d_mean     device, FP64 [V]: (1/M) sum_s samples[s][v]                   */
+/*   d_m2       device, FP64 [V] or NULL: (1/M) sum_s samples[s][v]^2         */
+/*   stream     cudaStream_t or NULL; the call is asynchronous on it          */
+/* Partial sums go to one fixed device array of 2^21 doubles (16 MiB) that    */
+/* every GPU loading the library holds until exit; hence V <= 2^20 nodes      */
+/* (larger V returns SL_ERR_ARG), and no cudaMalloc, cudaFree or allocating   */
+/* library routine is called.  The first call on a device looks up the        */
+/* array's device address (once per device); make that first call before any */
+/* stream capture.  All calls on a device share the array: calls that may    */
+/* overlap on the GPU (different streams without ordering) race and give     */
+/* wrong results.  Each call writes every partial it reads, so no clearing   */
+/* is needed between calls.                                                   */
+int sl_moments_static(const double *d_samples, int M, long long V, double *d_mean, double *d_m2,
+                      void *stream);
+
 /* Releases the context and its device memory.  NULL is a no-op. */
 void sl_free(sl_ctx *c);
 

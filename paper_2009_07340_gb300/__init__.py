@@ -21,8 +21,8 @@ from . import build as _build
 
 __all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_init", "sl_step",
            "sl_moments", "sl_moments_device", "sl_dt_max", "sl_step_count", "sl_get_samples",
-           "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_profile", "sl_profile_read", "sl_free",
-           "sl_strerror"]
+           "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_profile", "sl_profile_read",
+           "sl_moments_static", "sl_free", "sl_strerror"]
 
 SL_FP64, SL_MIXED, SL_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": SL_FP64, "mixed": SL_MIXED, "fp32": SL_FP32}
@@ -78,6 +78,7 @@ def lib():
         L.sl_wiener.argtypes = [vp, C.c_longlong, C.c_int, C.c_double, _dp]
         L.sl_profile.argtypes = [vp, C.c_int]
         L.sl_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
+        L.sl_moments_static.argtypes = [vp, C.c_int, C.c_longlong, vp, vp, vp]
         L.sl_free.argtypes = [vp]
         L.sl_free.restype = None
         L.sl_strerror.argtypes = [C.c_int]
@@ -209,6 +210,14 @@ def sl_profile_read(ctx):
     n = C.c_longlong()
     _check(lib().sl_profile_read(C.c_void_p(ctx), C.byref(ms), C.byref(n)), "sl_profile_read")
     return ms.value, n.value
+
+
+def sl_moments_static(d_samples_ptr, M, V, d_mean_ptr, d_m2_ptr=None, stream=None):
+    """Allocation-free moments of caller-owned device FP64 samples [M][V]
+    (see include/sl.h: for callers that cannot allocate device memory)."""
+    _check(lib().sl_moments_static(C.c_void_p(d_samples_ptr), int(M), int(V), C.c_void_p(d_mean_ptr),
+                                   C.c_void_p(d_m2_ptr) if d_m2_ptr else None,
+                                   C.c_void_p(stream) if stream else None), "sl_moments_static")
 
 
 def sl_free(ctx):
