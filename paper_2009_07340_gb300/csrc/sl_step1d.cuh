@@ -55,6 +55,11 @@
 
 #include "sl_internal.cuh"
 
+// CTAs per SM the FP32 modes are compiled for (register budget 256 threads x 2).
+#ifndef SL1D_FP32_MIN_BLOCKS
+#define SL1D_FP32_MIN_BLOCKS 2
+#endif
+
 namespace sl {
 
 namespace cg = cooperative_groups;
@@ -113,7 +118,7 @@ __device__ __forceinline__ void load_row(const double *src, double (&z)[NP])
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(kMaxThreads1D) sl1d_step_kernel(const Step1DArgs a)
+__global__ void __launch_bounds__(kMaxThreads1D, MODE == SL_FP64 ? 1 : SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel(const Step1DArgs a)
 {
     using R = typename Prec1D<MODE>::R;
     using State = typename Prec1D<MODE>::State;
