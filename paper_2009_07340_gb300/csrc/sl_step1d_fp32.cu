@@ -1,4 +1,5 @@
-// 1D step kernels, precision mode SL_FP32 (see sl_step1d.cuh).
+// 1D step kernels, precision mode SL_FP32 (scalar FP32 kernel of sl_step1d.cuh;
+// measured as fast as the packed form on GB300, where FFMA2 has the FFMA rate).
 #include "sl_step1d.cuh"
 
 namespace sl {
