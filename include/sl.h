@@ -113,7 +113,10 @@ typedef struct sl_ctx sl_ctx; /* opaque; owns all of its device memory */
 
 /* Creates a solver for M samples of order N (N Gauss nodes per direction,  */
 /* 2 <= N <= 16) on `mesh`, evaluates the fields at the nodes and faces and  */
-/* sets every sample to phi0 (Section 5.1).  1D: K <= 1024 elements.         */
+/* sets every sample to phi0 (Section 5.1).  1D: K <= 2048 elements.         */
+/* 2D: N <= 8 in SL_FP64, N <= 10 in the FP32 modes (SL_ERR_UNSUPPORTED       */
+/* otherwise); in 2D both FP32 modes run the FP32 Gram solve with one         */
+/* refinement step.                                                           */
 /* The step counter starts at 0.  opt may be NULL (seed 0, SL_FP64).         */
 int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift,
             const sl_field *diffusion, const sl_field *phi0, const sl_options *opt);

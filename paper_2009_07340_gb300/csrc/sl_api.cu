@@ -154,6 +154,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     const int precision = opt ? opt->precision : SL_FP64;
     if (precision != SL_FP64 && precision != SL_MIXED && precision != SL_FP32) return SL_ERR_ARG;
     if (dim == 1 && mesh->K[0] > sl::kMaxThreads1D * sl::kMaxCluster1D) return SL_ERR_UNSUPPORTED;
+    if (dim == 2 && N > (precision == SL_FP64 ? 8 : 10)) return SL_ERR_UNSUPPORTED;
     if (opt && (opt->sample0 < 0 || opt->sample0 + M > (1ll << 32))) return SL_ERR_ARG;
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
@@ -354,7 +355,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.Q = c->Q;
             a.faces = c->faces2d;
             a.err = c->err;
-            e = sl::launch_step2d(a, m.N, c->precision, c->st);
+            e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
         }
         if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;
         if (e != cudaSuccess) return fail_cuda(c);

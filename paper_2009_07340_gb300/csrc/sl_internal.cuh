@@ -69,7 +69,8 @@ cudaError_t launch_step1d_fp32(const Step1DArgs &a, int N, cudaStream_t st);
 size_t step1d_smem_bytes_fp64(int N, int S, int T);
 size_t step1d_smem_bytes_mixed(int N, int S, int T);
 size_t step1d_smem_bytes_fp32(int N, int S, int T);
-cudaError_t launch_step2d(const Step2DArgs &a, int N, int precision, cudaStream_t st);
+cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st);
+cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
                                const double *phi0_nodal_dev, double *xi, double *nodeU, double *nodeB,
                                double *nodeDiv, double *faceU, double *faceB, void *Q, int M,

@@ -1,0 +1,393 @@
+// sl_step2d.cuh -- 2D semi-Lagrangian Monte-Carlo step on tensor-product
+// elements (n = N^2 Gauss nodes per element, nodes p = j*N + i, x fastest).
+//
+// Per element-sample and step (Sections 5.2-5.3 in tensor form; the paper
+// defers the multi-dimensional remap to the authors' earlier deterministic
+// paper, so the reading is: tensor Lagrange basis on the scattered advected
+// particles, 4N face rows at the Gauss-node positions of the four faces):
+//   particle p moves from its node by (dx_p, dy_p) = (u_x dt + b dW_x,
+//   u_y dt + b dW_y) / h  (Eq. def_dx, one dW per sample and dimension);
+//   phi*_p = Q_p - dt (div u)_p Q_p                     (Eq. advection_phi);
+//   V[p][(i',j')] = h_i'(x*_p) h_j'(y*_p) (Gauss-node basis at the particles);
+//   phase 1: alpha = V^{-1} phi* (nodal values of the advected interpolant),
+//            face values B alpha at the 4N face points  (Eq. remap_bnd);
+//   phase 2: upwind face values g (Eq. bnd_update) and
+//            q = argmin |V q - phi*|^2 + |B q - g|^2     (Section 5.3).
+// The two phases are two launches per step: phase 2 of an element needs its
+// neighbours' phase-1 face values.
+//
+// Mapping: a group of n threads (rounded up to a warp multiple, its own named
+// barrier) per element-sample; thread p owns particle p.  Rows of the stacked
+// system [V; B] (B only in phase 2) are staged in shared memory; thread c
+// builds row c of the Gram matrix G = [V;B]^T [V;B] in registers and the
+// group solves G x = [V;B]^T rhs by Gauss-Jordan elimination without
+// pivoting (G is SPD), one broadcast pivot row per step.  Everything is
+// relative to the element reference value c (the middle node's state):
+// [V;B] 1 = 1 (partition of unity), so the unknown is q - c.  The FP32 mode
+// keeps the state and face values as float pairs (as in 1D) and applies one
+// step of iterative refinement of the stacked least-squares residual against
+// the original rows, replaying the stored elimination multipliers.
+#pragma once
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "sl_internal.cuh"
+
+namespace sl {
+
+constexpr int kGroupThreads2D = 256;  // threads per CTA
+
+__device__ __forceinline__ void two_sum2d(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int N, typename R>
+struct Geo2D {
+    static constexpr int n = N * N;
+    static constexpr int GS = (n + 31) / 32 * 32;               // threads per group
+    static constexpr int GPC = GS >= kGroupThreads2D ? 1 : kGroupThreads2D / GS;  // groups per CTA
+    static constexpr int LD = (n + 3) & ~3;                     // row stride (16-byte rows)
+    static constexpr int P = n + 4 * N;                         // stacked rows
+    // per-group shared memory (elements of R)
+    static constexpr int kRows = P * LD, kRhs = P, kPiv = 2 * (LD + 4), kVec = P, kRes = P;
+    static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
+    // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N]
+    static constexpr int kTables = N * N + 3 * N;
+};
+
+template <int N, typename R, int PHASE>
+__global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2DArgs a, int t)
+{
+    using G = Geo2D<N, R>;
+    constexpr int n = G::n, LD = G::LD;
+    constexpr int P = PHASE == 1 ? n : G::P;  // rows of the system solved in this phase
+    constexpr bool kPair = !std::is_same<R, double>::value;
+    using State = typename std::conditional<kPair, float2, double>::type;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *tab = reinterpret_cast<R *>(smem_raw);
+    R *sZ = tab;              // [N][N] 4 (xi_i - xi_m)
+    R *slam = sZ + N * N;     // [N] barycentric weights of the (scaled) Gauss nodes
+    R *sh0 = slam + N;        // [N] h_i(0)
+    R *sh1 = sh0 + N;         // [N] h_i(1)
+    const int grp = threadIdx.x / G::GS;
+    const int c = threadIdx.x - grp * G::GS;  // thread's node / row / column index
+    R *gbase = tab + ((G::kTables + 3) & ~3) + grp * G::kGroup;
+    R *Vs = gbase;                 // [P][LD] stacked rows
+    R *rhs = Vs + G::kRows;        // [P] right-hand side (relative to c)
+    R *piv = rhs + G::kRhs;        // [2][LD + 4] pivot rows
+    R *vec = piv + G::kPiv;        // [P] broadcast vector
+    R *res = vec + G::kVec;        // [P] residual
+
+    if (threadIdx.x < N * N) {
+        const int i = threadIdx.x / N, m = threadIdx.x % N;
+        sZ[threadIdx.x] = R(4.0 * (a.xi[i] - a.xi[m]));
+    }
+    if (threadIdx.x < N) {
+        const int j = threadIdx.x;
+        double lam = 1.0, l0 = 1.0, l1 = 1.0;
+        for (int m = 0; m < N; ++m)
+            if (m != j) {
+                lam /= 4.0 * (a.xi[j] - a.xi[m]);
+                l0 *= (0.0 - a.xi[m]) / (a.xi[j] - a.xi[m]);
+                l1 *= (1.0 - a.xi[m]) / (a.xi[j] - a.xi[m]);
+            }
+        slam[j] = R(lam);
+        sh0[j] = R(l0);
+        sh1[j] = R(l1);
+    }
+    __syncthreads();
+
+    const int E = a.Kx * a.Ky;
+    const long long gid = (long long)blockIdx.x * G::GPC + grp;
+    const bool group_active = gid < (long long)E * a.M;
+    const int s = group_active ? int(gid / E) : 0;
+    const int e = group_active ? int(gid % E) : 0;
+    const int kx = e % a.Kx, ky = e / a.Kx;
+    const bool real = group_active && c < n;
+    const int bar_id = 1 + grp;
+
+    // reference value and own state
+    State *Qg = reinterpret_cast<State *>(a.Q);
+    const long long qoff = ((long long)s * E + e) * n;
+    R ch, cl = R(0), qh = R(0), ql = R(0);
+    {
+        const State cv = Qg[qoff + n / 2];
+        if constexpr (kPair) {
+            ch = cv.x;
+            cl = cv.y;
+        } else {
+            ch = cv;
+        }
+        if (real) {
+            const State qv = Qg[qoff + c];
+            if constexpr (kPair) {
+                qh = qv.x;
+                ql = qv.y;
+            } else {
+                qh = qv;
+            }
+        }
+    }
+    const int ip = c % N, jp = c / N;
+    R hx[N], hy[N];
+    R ph = R(0);
+    if (real) {
+        const long long V = (long long)E * n;
+        const double dWx = a.dW[((long long)t * a.M + s) * 2 + 0];
+        const double dWy = a.dW[((long long)t * a.M + s) * 2 + 1];
+        const double ux = a.nodeU[(long long)e * n + c], uy = a.nodeU[V + (long long)e * n + c];
+        const double b = a.nodeB[(long long)e * n + c];
+        const R dx = R(4.0 * (ux * a.dt + b * dWx) / a.hx);
+        const R dy = R(4.0 * (uy * a.dt + b * dWy) / a.hy);
+        const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
+        R dq = qh - ch;
+        if constexpr (kPair) dq += ql - cl;
+        ph = dq - gam * qh;
+        // Gauss-node basis at the particle: h_i'(x) = lam_i' prod_{m != i'} (x - zeta_m),
+        // x - zeta_m = Z[ip][m] + dx (node difference plus displacement)
+        R pre = R(1);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            hx[m] = pre;
+            pre *= sZ[ip * N + m] + dx;
+        }
+        R suf = R(1);
+#pragma unroll
+        for (int m = N - 1; m >= 0; --m) {
+            hx[m] *= suf * slam[m];
+            suf *= sZ[ip * N + m] + dx;
+        }
+        pre = R(1);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            hy[m] = pre;
+            pre *= sZ[jp * N + m] + dy;
+        }
+        suf = R(1);
+#pragma unroll
+        for (int m = N - 1; m >= 0; --m) {
+            hy[m] *= suf * slam[m];
+            suf *= sZ[jp * N + m] + dy;
+        }
+        // row c of V and its right-hand side
+#pragma unroll
+        for (int jj = 0; jj < N; ++jj)
+#pragma unroll
+            for (int ii = 0; ii < N; ++ii) Vs[c * LD + jj * N + ii] = hx[ii] * hy[jj];
+        rhs[c] = ph;
+    }
+
+    using FaceT = typename std::conditional<kPair, float2, double>::type;
+    FaceT *faces = reinterpret_cast<FaceT *>(a.faces);
+    const long long fbase = (long long)s * E;
+    if constexpr (PHASE == 2) {
+        // face rows of B and the upwinded face values g (Eq. bnd_update)
+        if (group_active && c < 4 * N) {
+            const int side = c / N, f = c % N;
+            R *row = Vs + (n + c) * LD;
+#pragma unroll
+            for (int q = 0; q < n; ++q) row[q] = R(0);
+            const double dW = a.dW[((long long)t * a.M + s) * 2 + (side < 2 ? 0 : 1)];
+            int e_face;  // element whose low face is this interface
+            if (side == 0) e_face = e;
+            else if (side == 1) e_face = ky * a.Kx + (kx + 1) % a.Kx;
+            else if (side == 2) e_face = e;
+            else e_face = ((ky + 1) % a.Ky) * a.Kx + kx;
+            const long long fidx = (long long)(side < 2 ? 0 : 1) * E * N + (long long)e_face * N + f;
+            const double af = a.faceU[fidx] * a.dt, bf = a.faceB[fidx];
+            bool from_low;  // take the value from the element on the low side
+            if constexpr (kPair)
+                from_low = fmaf(float(bf), float(dW), float(af)) > 0.f;
+            else
+                from_low = __dadd_rn(af, __dmul_rn(bf, dW)) > 0.0;
+            int e_low, e_high;
+            if (side == 0) {
+                e_low = ky * a.Kx + (kx - 1 + a.Kx) % a.Kx;
+                e_high = e;
+            } else if (side == 1) {
+                e_low = e;
+                e_high = e_face;
+            } else if (side == 2) {
+                e_low = ((ky - 1 + a.Ky) % a.Ky) * a.Kx + kx;
+                e_high = e;
+            } else {
+                e_low = e;
+                e_high = e_face;
+            }
+            const bool xface = side < 2;
+            // low element's far face (right / top) or high element's near face (left / bottom)
+            const FaceT gv = from_low ? faces[(fbase + e_low) * 4 * N + (xface ? N : 3 * N) + f]
+                                      : faces[(fbase + e_high) * 4 * N + (xface ? 0 : 2 * N) + f];
+            R gr;
+            if constexpr (kPair)
+                gr = (gv.x - ch) + (gv.y - cl);
+            else
+                gr = gv - ch;
+            rhs[n + c] = gr;
+            if (side == 0)
+#pragma unroll
+                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = sh0[ii];
+            else if (side == 1)
+#pragma unroll
+                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = sh1[ii];
+            else if (side == 2)
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = sh0[jj];
+            else
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = sh1[jj];
+        }
+    }
+    group_sync(bar_id, G::GS);
+
+    // Gram row c: G[c][c'] = sum_p S[p][c] S[p][c'], b_c = sum_p S[p][c] rhs_p
+    R gr[n];
+#pragma unroll
+    for (int q = 0; q < n; ++q) gr[q] = R(0);
+    R bc = R(0);
+    if (real) {
+        for (int p = 0; p < P; ++p) {
+            const R vpc = Vs[p * LD + c];
+            const R *rowp = Vs + p * LD;
+#pragma unroll
+            for (int q = 0; q < n; ++q) gr[q] = fma(vpc, rowp[q], gr[q]);
+            bc = fma(vpc, rhs[p], bc);
+        }
+    }
+
+    // Gauss-Jordan elimination without pivoting (G is SPD); multipliers are
+    // kept in the eliminated positions for the refinement replay
+    R diag = R(1);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        R *pr = piv + (k & 1) * (LD + 4);
+        if (c == k) {
+#pragma unroll
+            for (int q = 0; q < n; ++q) pr[q] = gr[q];
+            pr[LD] = bc;
+            pr[LD + 1] = R(1) / gr[k];
+            diag = gr[k];
+        }
+        group_sync(bar_id, G::GS);
+        if (real && c != k) {
+            const R l = gr[k] * pr[LD + 1];
+            // columns < k hold multipliers (eliminated); only q > k change
+#pragma unroll
+            for (int q = k + 1; q < n; ++q) gr[q] = fma(-l, pr[q], gr[q]);
+            bc = fma(-l, pr[LD], bc);
+            gr[k] = l;
+        }
+    }
+    R x = real ? bc / diag : R(0);
+    bad |= real && !(diag > R(0));
+
+    if constexpr (kPair) {
+        // one step of iterative refinement of the stacked least-squares
+        // residual: r = S^T (rhs - S x), G dx = r, x += dx
+        if (c < n) vec[c] = x;  // the group may have more threads than nodes
+        group_sync(bar_id, G::GS);
+        if (real) {
+            // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
+            R vx = R(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) {
+                R t2 = R(0);
+#pragma unroll
+                for (int ii = 0; ii < N; ++ii) t2 = fma(hx[ii], vec[jj * N + ii], t2);
+                vx = fma(hy[jj], t2, vx);
+            }
+            res[c] = rhs[c] - vx;
+        }
+        if (PHASE == 2 && group_active && c < 4 * N) {
+            const R *row = Vs + (n + c) * LD;
+            R bx = R(0);
+#pragma unroll
+            for (int q = 0; q < n; ++q) bx = fma(row[q], vec[q], bx);
+            res[n + c] = rhs[n + c] - bx;
+        }
+        group_sync(bar_id, G::GS);
+        R rc = R(0);
+        if (real)
+            for (int p = 0; p < P; ++p) rc = fma(Vs[p * LD + c], res[p], rc);
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            R *pr = piv + (k & 1) * (LD + 4);
+            if (c == k) pr[0] = rc;
+            group_sync(bar_id, G::GS);
+            if (real && c != k) rc = fma(-gr[k], pr[0], rc);
+        }
+        x += real ? rc / diag : R(0);
+    }
+    bad |= real && !isfinite(x);
+
+    if constexpr (PHASE == 1) {
+        // face values of the advected interpolant (alpha - c = x) at the 4N face points
+        if (c < n) vec[c] = x;  // the group may have more threads than nodes
+        group_sync(bar_id, G::GS);
+        if (group_active && c < 4 * N) {
+            const int side = c / N, f = c % N;
+            R v = R(0);
+            if (side < 2) {
+                const R *h = side == 0 ? sh0 : sh1;
+#pragma unroll
+                for (int ii = 0; ii < N; ++ii) v = fma(h[ii], vec[f * N + ii], v);
+            } else {
+                const R *h = side == 2 ? sh0 : sh1;
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj) v = fma(h[jj], vec[jj * N + f], v);
+            }
+            FaceT out;
+            if constexpr (kPair) {
+                two_sum2d(ch, v, out.x, out.y);
+                out.y += cl;
+            } else {
+                out = ch + v;
+            }
+            faces[(fbase + e) * 4 * N + c] = out;
+        }
+    } else {
+        if (real) {
+            if constexpr (kPair) {
+                float hi, lo;
+                two_sum2d(ch, x, hi, lo);
+                Qg[qoff + c] = make_float2(hi, lo + cl);
+            } else {
+                Qg[qoff + c] = ch + x;
+            }
+        }
+    }
+    if (bad) atomicOr(a.err, 1);
+}
+
+template <int N, typename R>
+cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
+{
+    using G = Geo2D<N, R>;
+    const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
+    const long long groups = (long long)a.Kx * a.Ky * a.M;
+    const unsigned grid = unsigned((groups + G::GPC - 1) / G::GPC);
+    const unsigned block = unsigned(G::GPC * G::GS);
+    auto k1 = sl2d_step_kernel<N, R, 1>;
+    auto k2 = sl2d_step_kernel<N, R, 2>;
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    for (int t = 0; t < a.nsteps; ++t) {
+        k1<<<grid, block, smem, st>>>(a, t);
+        k2<<<grid, block, smem, st>>>(a, t);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sl

@@ -1,0 +1,106 @@
+"""GPU parity of the 2D path (tensor-product elements) against the FP64 CPU
+oracle, through the C ABI.  SL_FP64 within 1e-10 of the oracle; the FP32
+path (float-pair state, FP32 Gram solve, one refinement step) within 1e-5 of
+the FP64 path on the moments."""
+
+import numpy as np
+import pytest
+
+import sl_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sl():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_07340_gb300 import build
+
+    build.build()
+    import paper_2009_07340_gb300 as sl
+
+    return sl
+
+
+def _rel(a, b, scale=None):
+    scale = np.abs(b).max() if scale is None else scale
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / scale)
+
+
+def _rot(K=(4, 4), N=4, M=3, steps=4, frac=0.5, orc=None):
+    pb = I.problem(2, K, (0.0, 0.0), (1.0, 1.0), N, M, steps, 0.0, 31,
+                   ("rotation", [2 * np.pi, 0.5, 0.5]), ("sinsin", [0.005, 0.3, 2.0, 2.0]),
+                   ("gauss", [1.0, 0.15, 0.5, 0.65]))
+    pb["dt"] = frac * orc.dt_max(pb)
+    return pb
+
+
+def _pair(sl, orc, pb, precision="fp64", states=None):
+    states = pb["M"] if states is None else states
+    ref = orc.run(pb, want_states=True, nthreads=8, ns=pb["M"])
+    with sl.Solver(pb, precision) as s:
+        s.step()
+        mean, m2 = s.moments()
+        st = s.samples(0, states)
+    M = pb["M"]
+    rm = ref["sum"] / M
+    scale = np.abs(rm).max()
+    return _rel(mean, rm, scale), _rel(m2, ref["sumsq"] / M), _rel(st, ref["states"][:states], scale)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6, 8])
+def test_rotation_fp64(sl, orc, N):
+    pb = _rot(N=N, orc=orc)
+    e_mean, e_m2, e_st = _pair(sl, orc, pb)
+    assert e_mean <= FP64_TOL and e_m2 <= FP64_TOL and e_st <= FP64_TOL
+
+
+def test_constant_drift_nonsquare_fp64(sl, orc):
+    pb = I.problem(2, (5, 3), (0.0, -1.0), (2.0, 1.0), 5, 7, 6, 0.0, 9, ("const", [0.7, -0.4]),
+                   ("const", [0.002]), ("gauss", [1.0, 0.3, 1.0, 0.2]))
+    pb["dt"] = 0.5 * orc.dt_max(pb)
+    e_mean, e_m2, e_st = _pair(sl, orc, pb)
+    assert e_mean <= FP64_TOL and e_st <= FP64_TOL
+
+
+def test_config3_mesh_fp64_sampled(sl, orc):
+    # the full 64x64, N=8 mesh of the 2D workload at its dt, 2 samples, 2 steps
+    pb = I.config3(M=2, steps=2)
+    e_mean, _, e_st = _pair(sl, orc, pb)
+    assert e_mean <= FP64_TOL and e_st <= FP64_TOL
+
+
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_fp32_vs_fp64(sl, orc, N):
+    pb = _rot(K=(12, 12), N=N, M=64, steps=40, orc=orc)
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        m64, _ = s.moments()
+    with sl.Solver(pb, "fp32") as s:
+        s.step()
+        m32, _ = s.moments()
+    assert _rel(m32, m64) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("N", [9, 10])
+def test_fp32_high_order_vs_oracle(sl, orc, N):
+    pb = _rot(K=(3, 3), N=N, M=2, steps=3, orc=orc)
+    e_mean, _, e_st = _pair(sl, orc, pb, precision="fp32")
+    assert e_mean <= MIXED_TOL and e_st <= MIXED_TOL
+
+
+def test_order_limits(sl, orc):
+    pb = _rot(K=(2, 2), N=9, M=1, steps=1, orc=orc)
+    with pytest.raises(sl.SLError) as e:
+        sl.Solver(pb, "fp64")
+    assert e.value.code == -8
+    pb = _rot(K=(2, 2), N=11, M=1, steps=1, orc=orc)
+    with pytest.raises(sl.SLError) as e:
+        sl.Solver(pb, "fp32")
+    assert e.value.code == -8
