@@ -166,6 +166,93 @@ int sl_wiener(sl_ctx *c, long long step0, int nsteps, double dt, double *out);
 int sl_profile(sl_ctx *c, int enable);
 int sl_profile_read(sl_ctx *c, double *kernel_ms, long long *launches);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent solves of uneven size (mesh, N, M, dt, fields)  */
+/* advanced together.  Each instance is a full solver (as sl_init); a call  */
+/* of sl_batch_step advances all of them by `steps` steps of their own dt   */
+/* with one CUDA-graph launch: a Wiener kernel over all instances, one       */
+/* persistent kernel per 1D order (CTAs take (instance, sample-slot) work    */
+/* items from an atomic counter; instances with K > 256 get their own        */
+/* cluster launch), two launches per step per 2D order, and a step-counter   */
+/* update.  The graph is captured on the first call with a given `steps`    */
+/* and replayed afterwards.  Results per instance are the same as the        */
+/* instance run alone with sl_init/sl_step (bitwise in SL_FP64).             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    sl_mesh mesh;
+    int N, M;
+    sl_field drift, diffusion, phi0;
+    double dt;                /* this instance's time step                  */
+    unsigned long long seed;  /* this instance's Philox key                 */
+} sl_instance;
+
+typedef struct sl_batch sl_batch; /* opaque; owns its instances' device memory */
+
+/* opt: precision, stream, device and strict_dt apply to every instance     */
+/* (seed and sample0 are taken per instance).  A NULL stream makes the batch */
+/* create its own non-blocking stream (graphs cannot be captured on the     */
+/* legacy default stream).  Returns the first failing instance's error.    */
+int sl_batch_create(sl_batch **out, int count, const sl_instance *inst, const sl_options *opt);
+
+/* Advances every instance by `steps` steps (asynchronous on the stream).   */
+int sl_batch_step(sl_batch *b, int steps);
+
+/* Autotuner: for each 1D order, times the persistent kernel on the real    */
+/* instances for `probe_steps` steps with 1..4 CTAs per SM and keeps the     */
+/* fastest; every instance's state and step counter are restored afterwards. */
+/* best_ms (may be NULL) receives the sum of the best probe times.           */
+int sl_batch_tune(sl_batch *b, int probe_steps, double *best_ms);
+
+/* Persistent grid chosen for 1D class `cls` (order N, CTAs, instances).     */
+int sl_batch_grid(const sl_batch *b, int cls, int *N, int *grid, int *instances);
+
+/* Moments / samples of instance i (as sl_moments / sl_get_samples).         */
+int sl_batch_moments(sl_batch *b, int i, double *mean, double *m2);
+int sl_batch_samples(sl_batch *b, int i, int s0, int count, double *out);
+
+void sl_batch_free(sl_batch *b);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: solves submitted over time, run with continuous batching.  A     */
+/* scheduler thread admits queued requests in arrival order while their      */
+/* device footprint fits in `budget_bytes` beside the running ones (a        */
+/* request larger than the budget is rejected with SL_ERR_OOM), advances     */
+/* every running request by up to `slice_steps` steps per round on one of    */
+/* `streams` CUDA streams (their kernels overlap on the GPU), and completes   */
+/* finished requests (moments, memory released, latency = completion minus   */
+/* submission).  Each request's result equals the request run alone.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    size_t budget_bytes; /* device memory the running requests may hold        */
+    int slice_steps;     /* steps per request per scheduling round (>= 1)      */
+    int streams;         /* CUDA streams (1..64)                               */
+    int precision;       /* SL_FP64, SL_MIXED or SL_FP32                        */
+    int device;          /* CUDA device ordinal; -1 = current                   */
+} sl_server_config;
+
+typedef struct {
+    long long submitted, completed, rejected, failed, running, queued;
+    long long esu_completed;            /* element-sample updates of completed requests */
+    long long memory_in_use, memory_peak;
+    double p50_s, p99_s, mean_s;        /* latency of completed requests             */
+    double span_s;                      /* first submission to last completion       */
+    double esu_per_s;                   /* esu_completed / span_s                    */
+} sl_server_stats;
+
+typedef struct sl_server sl_server;
+
+int sl_server_create(sl_server **out, const sl_server_config *cfg);
+/* Queues a request of `steps` steps of spec->dt; *ticket identifies it.    */
+int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long *ticket);
+/* state: 0 queued, 1 running, 2 done, < 0 error code.  When done, copies   */
+/* the moments (host [elements][N^dim]; either may be NULL) and latency.    */
+int sl_server_poll(sl_server *s, long long ticket, int *state, double *mean, double *m2, double *latency_s);
+/* Waits until nothing is queued or running (SL_ERR_TIMEOUT after timeout_s). */
+int sl_server_wait_idle(sl_server *s, double timeout_s);
+int sl_server_stats_get(sl_server *s, sl_server_stats *out);
+/* Stops admitting, finishes the running requests, releases everything.     */
+void sl_server_free(sl_server *s);
+
 /* Allocation-free sample moments.  The paper has no counterpart: this entry  */
 /* exists for callers that cannot call cudaMalloc when they need the moments */
 /* (a serving loop whose HBM budget is fully reserved up front, code that     */

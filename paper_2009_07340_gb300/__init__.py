@@ -52,6 +52,22 @@ class sl_options(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong)]
 
 
+class sl_instance(C.Structure):
+    _fields_ = [("mesh", sl_mesh), ("N", C.c_int), ("M", C.c_int), ("drift", sl_field),
+                ("diffusion", sl_field), ("phi0", sl_field), ("dt", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class sl_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("slice_steps", C.c_int), ("streams", C.c_int),
+                ("precision", C.c_int), ("device", C.c_int)]
+
+
+class sl_server_stats(C.Structure):
+    _fields_ = [(n, C.c_longlong) for n in ("submitted", "completed", "rejected", "failed", "running", "queued",
+                                             "esu_completed", "memory_in_use", "memory_peak")] + \
+               [(n, C.c_double) for n in ("p50_s", "p99_s", "mean_s", "span_s", "esu_per_s")]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 
@@ -79,6 +95,21 @@ def lib():
         L.sl_profile.argtypes = [vp, C.c_int]
         L.sl_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
         L.sl_moments_static.argtypes = [vp, C.c_int, C.c_longlong, vp, vp, vp]
+        L.sl_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(sl_instance), C.POINTER(sl_options)]
+        L.sl_batch_step.argtypes = [vp, C.c_int]
+        L.sl_batch_tune.argtypes = [vp, C.c_int, _dp]
+        L.sl_batch_grid.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sl_batch_moments.argtypes = [vp, C.c_int, _dp, _dp]
+        L.sl_batch_samples.argtypes = [vp, C.c_int, C.c_int, C.c_int, _dp]
+        L.sl_batch_free.argtypes = [vp]
+        L.sl_batch_free.restype = None
+        L.sl_server_create.argtypes = [C.POINTER(vp), C.POINTER(sl_server_config)]
+        L.sl_server_submit.argtypes = [vp, C.POINTER(sl_instance), C.c_int, C.POINTER(C.c_longlong)]
+        L.sl_server_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), _dp, _dp, _dp]
+        L.sl_server_wait_idle.argtypes = [vp, C.c_double]
+        L.sl_server_stats_get.argtypes = [vp, C.POINTER(sl_server_stats)]
+        L.sl_server_free.argtypes = [vp]
+        L.sl_server_free.restype = None
         L.sl_free.argtypes = [vp]
         L.sl_free.restype = None
         L.sl_strerror.argtypes = [C.c_int]
@@ -223,6 +254,175 @@ def sl_moments_static(d_samples_ptr, M, V, d_mean_ptr, d_m2_ptr=None, stream=Non
 def sl_free(ctx):
     if ctx:
         lib().sl_free(C.c_void_p(ctx))
+
+
+def _instance(pb, dt=None, seed=None):
+    inst = sl_instance()
+    inst.mesh = _mesh(pb)
+    inst.N = pb["N"]
+    inst.M = pb["M"]
+    inst.drift = _field(_U, pb["drift"])
+    inst.diffusion = _field(_D, pb["diffusion"])
+    inst.phi0 = _field(_PHI, pb["phi0"])
+    inst.dt = float(pb["dt"] if dt is None else dt)
+    inst.seed = int(pb["seed"] if seed is None else seed)
+    return inst
+
+
+def sl_batch_create(problems, precision=SL_FP64, stream=None, strict_dt=False, device=-1):
+    arr = (sl_instance * len(problems))(*[_instance(pb) for pb in problems])
+    opt = sl_options()
+    opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt.strict_dt = 1 if strict_dt else 0
+    opt.stream = C.c_void_p(stream) if stream else None
+    opt.device = device
+    h = C.c_void_p()
+    _check(lib().sl_batch_create(C.byref(h), len(problems), arr, C.byref(opt)), "sl_batch_create")
+    return h.value
+
+
+def sl_batch_step(b, steps):
+    _check(lib().sl_batch_step(C.c_void_p(b), int(steps)), "sl_batch_step")
+
+
+def sl_batch_tune(b, probe_steps=2):
+    ms = C.c_double()
+    _check(lib().sl_batch_tune(C.c_void_p(b), int(probe_steps), C.byref(ms)), "sl_batch_tune")
+    return ms.value
+
+
+def sl_batch_grid(b, cls):
+    N, g, k = C.c_int(), C.c_int(), C.c_int()
+    rc = lib().sl_batch_grid(C.c_void_p(b), int(cls), C.byref(N), C.byref(g), C.byref(k))
+    return None if rc != 0 else (N.value, g.value, k.value)
+
+
+def sl_batch_moments(b, i, V):
+    mean, m2 = np.zeros(V), np.zeros(V)
+    _check(lib().sl_batch_moments(C.c_void_p(b), int(i), _f64p(mean), _f64p(m2)), "sl_batch_moments")
+    return mean, m2
+
+
+def sl_batch_samples(b, i, s0, count, V):
+    out = np.zeros((count, V))
+    _check(lib().sl_batch_samples(C.c_void_p(b), int(i), int(s0), int(count), _f64p(out)), "sl_batch_samples")
+    return out
+
+
+def sl_batch_free(b):
+    if b:
+        lib().sl_batch_free(C.c_void_p(b))
+
+
+class Batch:
+    """Many independent problems advanced together (see include/sl.h)."""
+
+    def __init__(self, problems, precision="fp64", stream=None, strict_dt=False):
+        self.problems = problems
+        self.V = [int(np.prod(pb["K"])) * pb["N"] ** pb["dim"] for pb in problems]
+        self.h = sl_batch_create(problems, precision, stream, strict_dt)
+
+    def step(self, steps):
+        sl_batch_step(self.h, steps)
+
+    def tune(self, probe_steps=2):
+        return sl_batch_tune(self.h, probe_steps)
+
+    def grids(self):
+        out, c = [], 0
+        while True:
+            g = sl_batch_grid(self.h, c)
+            if g is None:
+                return out
+            out.append(g)
+            c += 1
+
+    def moments(self, i):
+        pb = self.problems[i]
+        E, n = int(np.prod(pb["K"])), pb["N"] ** pb["dim"]
+        mean, m2 = sl_batch_moments(self.h, i, self.V[i])
+        return mean.reshape(E, n), m2.reshape(E, n)
+
+    def samples(self, i, s0=0, count=None):
+        pb = self.problems[i]
+        count = pb["M"] - s0 if count is None else count
+        return sl_batch_samples(self.h, i, s0, count, self.V[i])
+
+    def close(self):
+        if self.h:
+            sl_batch_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server of drift-diffusion solves (see include/sl.h)."""
+
+    def __init__(self, budget_bytes, slice_steps=10, streams=8, precision="fp32", device=-1):
+        cfg = sl_server_config()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.slice_steps = int(slice_steps)
+        cfg.streams = int(streams)
+        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.device = device
+        h = C.c_void_p()
+        _check(lib().sl_server_create(C.byref(h), C.byref(cfg)), "sl_server_create")
+        self.h = h.value
+        self.V = {}
+
+    def submit(self, pb, steps=None):
+        inst = _instance(pb)
+        t = C.c_longlong()
+        _check(lib().sl_server_submit(C.c_void_p(self.h), C.byref(inst), int(pb["steps"] if steps is None else steps),
+                                      C.byref(t)), "sl_server_submit")
+        self.V[t.value] = int(np.prod(pb["K"])) * pb["N"] ** pb["dim"]
+        return t.value
+
+    def poll(self, ticket, want=True):
+        st = C.c_int()
+        lat = C.c_double()
+        V = self.V[ticket]
+        mean = np.zeros(V) if want else None
+        m2 = np.zeros(V) if want else None
+        _check(lib().sl_server_poll(C.c_void_p(self.h), int(ticket), C.byref(st), _f64p(mean) if want else None,
+                                    _f64p(m2) if want else None, C.byref(lat)), "sl_server_poll")
+        return st.value, (mean, m2, lat.value) if st.value == 2 else None
+
+    def wait_idle(self, timeout_s=600.0):
+        _check(lib().sl_server_wait_idle(C.c_void_p(self.h), float(timeout_s)), "sl_server_wait_idle")
+
+    def stats(self):
+        st = sl_server_stats()
+        _check(lib().sl_server_stats_get(C.c_void_p(self.h), C.byref(st)), "sl_server_stats_get")
+        return {f: getattr(st, f) for f, _ in sl_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().sl_server_free(C.c_void_p(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience

@@ -12,35 +12,6 @@
 
 #include "sl_internal.cuh"
 
-struct sl_ctx {
-    sl::Mesh m;
-    int M = 0;
-    int precision = SL_FP64;
-    int strict_dt = 0;
-    unsigned long long seed = 0;
-    long long sample0 = 0;
-    cudaStream_t st = nullptr;
-    int device = 0;
-    long long step = 0;
-    int poisoned = 0;
-    double dtmax = 0.0;
-    // device memory owned by the context
-    double *xi = nullptr, *nodeU = nullptr, *nodeB = nullptr, *nodeDiv = nullptr;
-    double *faceU = nullptr, *faceB = nullptr;
-    void *Q = nullptr;
-    size_t state_elem = 8;
-    double *dW = nullptr;
-    int dW_cap = 0;  // steps the Wiener scratch holds
-    double *psum = nullptr, *psq = nullptr, *mean_tmp = nullptr, *m2_tmp = nullptr;
-    int mom_chunk = 64;
-    int *err = nullptr;
-    void *faces2d = nullptr;  // 2D face-value scratch
-    // 1D launch geometry
-    int S = 1, C = 1, T = 1;
-    // kernel timing hook
-    int profiling = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-};
 
 namespace {
 
@@ -48,6 +19,7 @@ constexpr size_t kWienerScratchBytes = size_t(64) << 20;
 
 int fail_cuda(sl_ctx *c)
 {
+    cudaGetLastError();  // do not leave the error for unrelated later calls
     if (c) c->poisoned = 1;
     return SL_ERR_CUDA;
 }

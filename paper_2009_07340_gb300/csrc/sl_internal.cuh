@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 #include "../../include/sl.h"
 
@@ -63,12 +65,36 @@ struct Step2DArgs {
     int *err;
 };
 
+// Persistent batched 1D launch: `ninst` instances of one order N, work
+// items (instance, sample slot) numbered by prefix[0..ninst].
+struct Batch1DLaunch {
+    const Step1DArgs *args;  // device [ninst]
+    const int *prefix;       // device [ninst + 1]
+    int ninst;
+    int *counter;            // device work counter (reset by the launcher)
+    int grid;                // persistent CTAs
+    size_t smem;             // dynamic shared memory per CTA
+};
+cudaError_t launch_step1d_batch_fp64(const Batch1DLaunch &b, int N, cudaStream_t st);
+cudaError_t launch_step1d_batch_mixed(const Batch1DLaunch &b, int N, cudaStream_t st);
+cudaError_t launch_step1d_batch_fp32(const Batch1DLaunch &b, int N, cudaStream_t st);
 cudaError_t launch_step1d_fp64(const Step1DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step1d_mixed(const Step1DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step1d_fp32(const Step1DArgs &a, int N, cudaStream_t st);
 size_t step1d_smem_bytes_fp64(int N, int S, int T);
 size_t step1d_smem_bytes_mixed(int N, int S, int T);
 size_t step1d_smem_bytes_fp32(int N, int S, int T);
+// Batched 2D launch: `ninst` instances of one order N; instance i owns the
+// element-sample groups [prefix[i], prefix[i+1]).
+struct Batch2DLaunch {
+    const Step2DArgs *args;    // device [ninst]
+    const long long *prefix;   // device [ninst + 1]
+    int ninst;
+    long long total_groups;
+    int nsteps;
+};
+cudaError_t launch_step2d_batch_fp64(const Batch2DLaunch &b, int N, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
@@ -80,4 +106,49 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk,
                            double *psum, double *psq, double *mean, double *m2, cudaStream_t st);
 
+}  // namespace sl
+
+// Solver context (opaque in the ABI).
+struct sl_ctx {
+    sl::Mesh m;
+    int M = 0;
+    int precision = SL_FP64;
+    int strict_dt = 0;
+    unsigned long long seed = 0;
+    long long sample0 = 0;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    long long step = 0;
+    int poisoned = 0;
+    double dtmax = 0.0;
+    // device memory owned by the context
+    double *xi = nullptr, *nodeU = nullptr, *nodeB = nullptr, *nodeDiv = nullptr;
+    double *faceU = nullptr, *faceB = nullptr;
+    void *Q = nullptr;
+    size_t state_elem = 8;
+    double *dW = nullptr;
+    int dW_cap = 0;  // steps the Wiener scratch holds
+    double *psum = nullptr, *psq = nullptr, *mean_tmp = nullptr, *m2_tmp = nullptr;
+    int mom_chunk = 64;
+    int *err = nullptr;
+    void *faces2d = nullptr;  // 2D face-value scratch
+    // 1D launch geometry
+    int S = 1, C = 1, T = 1;
+    // kernel timing hook
+    int profiling = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+};
+
+namespace sl {
+// Wiener increments of one instance in a batched launch.
+struct WienerJob {
+    unsigned long long seed;
+    long long sample0;
+    int M, dim;
+    double sqrt_dt;
+    double *out;  // [nsteps][M][dim]
+};
+cudaError_t launch_wiener_batch(const WienerJob *jobs, const long long *prefix, int njobs, int nsteps,
+                                const long long *steps, long long total, cudaStream_t st);
+cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_t st);
 }  // namespace sl

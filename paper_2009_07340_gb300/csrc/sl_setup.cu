@@ -206,6 +206,50 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
     return cudaGetLastError();
 }
 
+// Batched Wiener increments: job i covers [prefix[i], prefix[i+1]) =
+// nsteps x M_i entries, for the step counters steps[i] .. steps[i]+nsteps-1
+// (read on the device, so a captured graph replays with advancing counters).
+__global__ void wiener_batch_kernel(const WienerJob *__restrict__ jobs, const long long *__restrict__ prefix, int njobs,
+                                    int nsteps, const long long *__restrict__ steps, long long total)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    const WienerJob j = jobs[lo];
+    const long long local = idx - prefix[lo];
+    const int t = int(local / j.M), s = int(local % j.M);
+    const double2 z = normal_pair(j.seed, uint32_t(steps[lo] + t), uint32_t(j.sample0 + s), 0u);
+    j.out[local * j.dim] = __dmul_rn(j.sqrt_dt, z.x);
+    if (j.dim == 2) j.out[local * j.dim + 1] = __dmul_rn(j.sqrt_dt, z.y);
+}
+
+cudaError_t launch_wiener_batch(const WienerJob *jobs, const long long *prefix, int njobs, int nsteps,
+                                const long long *steps, long long total, cudaStream_t st)
+{
+    if (total == 0) return cudaSuccess;
+    const int tb = 256;
+    wiener_batch_kernel<<<unsigned((total + tb - 1) / tb), tb, 0, st>>>(jobs, prefix, njobs, nsteps, steps, total);
+    return cudaGetLastError();
+}
+
+__global__ void advance_counters_kernel(long long *steps, int n, int by)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) steps[i] += by;
+}
+
+cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    advance_counters_kernel<<<(n + 255) / 256, 256, 0, st>>>(steps, n, by);
+    return cudaGetLastError();
+}
+
 // Moments, Eq. (averaged), in a fixed summation order: chunk c of `chunk`
 // consecutive samples is summed in ascending sample order into partials
 // [c][V]; the partials are then added in ascending c.  FP64 throughout.

@@ -33,7 +33,7 @@ __device__ __forceinline__ float lane(const float2 *v)
 __device__ __forceinline__ float lane_rt(const float2 &v, int odd) { return odd ? v.y : v.x; }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel_f2(const Step1DArgs a)
+__device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int slot)
 {
     using Fac = typename Prec1D<MODE>::Fac;
     constexpr int NE = N + (N & 1);     // padded to an even count
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step
 
     const int sl = threadIdx.x / T;
     const int kl = threadIdx.x - sl * T;
-    const int s = (blockIdx.x / C) * S + sl;
+    const int s = slot * S + sl;
     const bool active = sl < S && kl < Kc && s < a.M;
 
     float2 *Qg = reinterpret_cast<float2 *>(a.Q);
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step
             }
         }
     }
-    const int sbase = sl * T;
+    const int sbase = (sl < S ? sl : 0) * T;  // threads beyond S*T read slot 0, never write
     int lnb_rank = rank, lnb_idx = kl - 1;
     int rnb_rank = rank, rnb_idx = kl + 1;
     if (kl == 0) {
@@ -221,8 +221,10 @@ __global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step
         const int buf = t & 1;
         float2 *fL = sface + (buf * 2 + 0) * S * T;
         float2 *fR = sface + (buf * 2 + 1) * S * T;
-        fL[sbase + kl] = f0;
-        fR[sbase + kl] = f1;
+        if (sl < S) {
+            fL[sbase + kl] = f0;
+            fR[sbase + kl] = f1;
+        }
         if (C > 1)
             cluster.sync();
         else
@@ -321,6 +323,41 @@ __global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step
     if (C > 1) cluster.sync();
 }
 
+// One launch: CTA (or cluster) b advances sample slot b / C.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel_f2(const Step1DArgs a)
+{
+    step1d_f2_body<N, MODE>(a, int(blockIdx.x) / a.C);
+}
+
+// Persistent batched launch over many instances of one order N (K <= 256,
+// no clusters): each CTA takes work items (instance, sample slot) from an
+// atomic counter and runs every step of the item resident on chip.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kMaxThreads1D, SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel_f2_batch(const Step1DArgs *__restrict__ args,
+                                                   const int *__restrict__ item_prefix, int ninst,
+                                                   int *__restrict__ counter)
+{
+    __shared__ int s_item;
+    const int total = item_prefix[ninst];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) return;
+        int lo = 0, hi = ninst - 1;  // last instance with item_prefix[i] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_prefix[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const Step1DArgs ai = args[lo];
+        step1d_f2_body<N, MODE>(ai, item - item_prefix[lo]);
+        __syncthreads();  // shared tables of this item are dead before the next fill
+    }
+}
+
 template <int MODE>
 size_t step1d_f2_smem_bytes(int N, int S, int T)
 {
@@ -371,6 +408,41 @@ cudaError_t launch_step1d_f2_mode(const Step1DArgs &a, int N, cudaStream_t st)
     case 14: return launch_step1d_f2_n<14, MODE>(a, st);
     case 15: return launch_step1d_f2_n<15, MODE>(a, st);
     case 16: return launch_step1d_f2_n<16, MODE>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N, int MODE>
+cudaError_t launch_sl1d_step_kernel_f2_batch_n(const Batch1DLaunch &b, cudaStream_t st)
+{
+    auto kern = sl1d_step_kernel_f2_batch<N, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b.smem));
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<b.grid, kMaxThreads1D, b.smem, st>>>(b.args, b.prefix, b.ninst, b.counter);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_sl1d_step_kernel_f2_batch_mode(const Batch1DLaunch &b, int N, cudaStream_t st)
+{
+    switch (N) {
+    case 2: return launch_sl1d_step_kernel_f2_batch_n<2, MODE>(b, st);
+    case 3: return launch_sl1d_step_kernel_f2_batch_n<3, MODE>(b, st);
+    case 4: return launch_sl1d_step_kernel_f2_batch_n<4, MODE>(b, st);
+    case 5: return launch_sl1d_step_kernel_f2_batch_n<5, MODE>(b, st);
+    case 6: return launch_sl1d_step_kernel_f2_batch_n<6, MODE>(b, st);
+    case 7: return launch_sl1d_step_kernel_f2_batch_n<7, MODE>(b, st);
+    case 8: return launch_sl1d_step_kernel_f2_batch_n<8, MODE>(b, st);
+    case 9: return launch_sl1d_step_kernel_f2_batch_n<9, MODE>(b, st);
+    case 10: return launch_sl1d_step_kernel_f2_batch_n<10, MODE>(b, st);
+    case 11: return launch_sl1d_step_kernel_f2_batch_n<11, MODE>(b, st);
+    case 12: return launch_sl1d_step_kernel_f2_batch_n<12, MODE>(b, st);
+    case 13: return launch_sl1d_step_kernel_f2_batch_n<13, MODE>(b, st);
+    case 14: return launch_sl1d_step_kernel_f2_batch_n<14, MODE>(b, st);
+    case 15: return launch_sl1d_step_kernel_f2_batch_n<15, MODE>(b, st);
+    case 16: return launch_sl1d_step_kernel_f2_batch_n<16, MODE>(b, st);
     default: return cudaErrorInvalidValue;
     }
 }

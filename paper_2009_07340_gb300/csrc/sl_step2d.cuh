@@ -64,8 +64,12 @@ struct Geo2D {
     static constexpr int kTables = N * N + 3 * N;
 };
 
-template <int N, typename R, int PHASE>
-__global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2DArgs a, int t)
+// BATCH = false: one instance (a0), group g = element-sample g.
+// BATCH = true: `ninst` instances of the same N, instance i owning groups
+// [prefix[i], prefix[i+1]) (its E*M element-samples).
+template <int N, typename R, int PHASE, bool BATCH>
+__global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
+                                                                    const long long *__restrict__ prefix, int ninst, int t)
 {
     using G = Geo2D<N, R>;
     constexpr int n = G::n, LD = G::LD;
@@ -88,18 +92,20 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
     R *vec = piv + G::kPiv;        // [P] broadcast vector
     R *res = vec + G::kVec;        // [P] residual
 
+    // node tables depend on N only (every instance of a batch class shares them)
+    const double *xi = BATCH ? args[0].xi : a0.xi;
     if (threadIdx.x < N * N) {
         const int i = threadIdx.x / N, m = threadIdx.x % N;
-        sZ[threadIdx.x] = R(4.0 * (a.xi[i] - a.xi[m]));
+        sZ[threadIdx.x] = R(4.0 * (xi[i] - xi[m]));
     }
     if (threadIdx.x < N) {
         const int j = threadIdx.x;
         double lam = 1.0, l0 = 1.0, l1 = 1.0;
         for (int m = 0; m < N; ++m)
             if (m != j) {
-                lam /= 4.0 * (a.xi[j] - a.xi[m]);
-                l0 *= (0.0 - a.xi[m]) / (a.xi[j] - a.xi[m]);
-                l1 *= (1.0 - a.xi[m]) / (a.xi[j] - a.xi[m]);
+                lam /= 4.0 * (xi[j] - xi[m]);
+                l0 *= (0.0 - xi[m]) / (xi[j] - xi[m]);
+                l1 *= (1.0 - xi[m]) / (xi[j] - xi[m]);
             }
         slam[j] = R(lam);
         sh0[j] = R(l0);
@@ -107,9 +113,21 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
     }
     __syncthreads();
 
+    const long long ggid = (long long)blockIdx.x * G::GPC + grp;
+    int inst = 0;
+    if constexpr (BATCH) {
+        int lo = 0, hi = ninst - 1;  // last instance with prefix[i] <= ggid
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= ggid) lo = mid;
+            else hi = mid - 1;
+        }
+        inst = lo;
+    }
+    const Step2DArgs a = BATCH ? args[inst] : a0;
+    const long long gid = BATCH ? ggid - prefix[inst] : ggid;
     const int E = a.Kx * a.Ky;
-    const long long gid = (long long)blockIdx.x * G::GPC + grp;
-    const bool group_active = gid < (long long)E * a.M;
+    const bool group_active = BATCH ? ggid < prefix[ninst] : gid < (long long)E * a.M;
     const int s = group_active ? int(gid / E) : 0;
     const int e = group_active ? int(gid % E) : 0;
     const int kx = e % a.Kx, ky = e / a.Kx;
@@ -378,14 +396,35 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
     const long long groups = (long long)a.Kx * a.Ky * a.M;
     const unsigned grid = unsigned((groups + G::GPC - 1) / G::GPC);
     const unsigned block = unsigned(G::GPC * G::GS);
-    auto k1 = sl2d_step_kernel<N, R, 1>;
-    auto k2 = sl2d_step_kernel<N, R, 2>;
+    auto k1 = sl2d_step_kernel<N, R, 1, false>;
+    auto k2 = sl2d_step_kernel<N, R, 2, false>;
     cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     for (int t = 0; t < a.nsteps; ++t) {
-        k1<<<grid, block, smem, st>>>(a, t);
-        k2<<<grid, block, smem, st>>>(a, t);
+        k1<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
+        k2<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
+    }
+    return cudaGetLastError();
+}
+
+// All instances of one order N, `nsteps` steps: two launches per step.
+template <int N, typename R>
+cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
+{
+    using G = Geo2D<N, R>;
+    const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
+    const unsigned grid = unsigned((b.total_groups + G::GPC - 1) / G::GPC);
+    const unsigned block = unsigned(G::GPC * G::GS);
+    auto k1 = sl2d_step_kernel<N, R, 1, true>;
+    auto k2 = sl2d_step_kernel<N, R, 2, true>;
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    Step2DArgs none = {};
+    for (int t = 0; t < b.nsteps; ++t) {
+        k1<<<grid, block, smem, st>>>(none, b.args, b.prefix, b.ninst, t);
+        k2<<<grid, block, smem, st>>>(none, b.args, b.prefix, b.ninst, t);
     }
     return cudaGetLastError();
 }

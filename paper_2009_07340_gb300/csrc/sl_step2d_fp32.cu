@@ -2,22 +2,57 @@
 // (see sl_step2d.cuh); N <= 10 (a Gram row of up to 100 floats per thread).
 // Both FP32 modes (SL_MIXED, SL_FP32) run this kernel in 2D: an FP64 Gram
 // factor would cost ~n^3/2 FP64 operations per element-sample, at 1/64 of the
-// FP32 rate on GB300.
-#include "sl_step2d.cuh"
+// FP32 rate on GB300.  The orders are compiled in sl_step2d_fp32_nNN.cu.
+#include "sl_internal.cuh"
 
 namespace sl {
+cudaError_t launch_step2d_fp32_n2(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n2(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n3(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n3(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n4(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n4(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n5(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n5(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n6(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n6(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n7(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n7(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n8(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n8(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n9(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n9(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n10(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n10(const Batch2DLaunch &b, cudaStream_t st);
+
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
 {
     switch (N) {
-    case 2: return launch_step2d_n<2, float>(a, st);
-    case 3: return launch_step2d_n<3, float>(a, st);
-    case 4: return launch_step2d_n<4, float>(a, st);
-    case 5: return launch_step2d_n<5, float>(a, st);
-    case 6: return launch_step2d_n<6, float>(a, st);
-    case 7: return launch_step2d_n<7, float>(a, st);
-    case 8: return launch_step2d_n<8, float>(a, st);
-    case 9: return launch_step2d_n<9, float>(a, st);
-    case 10: return launch_step2d_n<10, float>(a, st);
+    case 2: return launch_step2d_fp32_n2(a, st);
+    case 3: return launch_step2d_fp32_n3(a, st);
+    case 4: return launch_step2d_fp32_n4(a, st);
+    case 5: return launch_step2d_fp32_n5(a, st);
+    case 6: return launch_step2d_fp32_n6(a, st);
+    case 7: return launch_step2d_fp32_n7(a, st);
+    case 8: return launch_step2d_fp32_n8(a, st);
+    case 9: return launch_step2d_fp32_n9(a, st);
+    case 10: return launch_step2d_fp32_n10(a, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t st)
+{
+    switch (N) {
+    case 2: return launch_step2d_batch_fp32_n2(b, st);
+    case 3: return launch_step2d_batch_fp32_n3(b, st);
+    case 4: return launch_step2d_batch_fp32_n4(b, st);
+    case 5: return launch_step2d_batch_fp32_n5(b, st);
+    case 6: return launch_step2d_batch_fp32_n6(b, st);
+    case 7: return launch_step2d_batch_fp32_n7(b, st);
+    case 8: return launch_step2d_batch_fp32_n8(b, st);
+    case 9: return launch_step2d_batch_fp32_n9(b, st);
+    case 10: return launch_step2d_batch_fp32_n10(b, st);
     default: return cudaErrorNotSupported;
     }
 }

@@ -16,4 +16,17 @@ cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st)
     default: return cudaErrorNotSupported;
     }
 }
+cudaError_t launch_step2d_batch_fp64(const Batch2DLaunch &b, int N, cudaStream_t st)
+{
+    switch (N) {
+    case 2: return launch_step2d_batch_n<2, double>(b, st);
+    case 3: return launch_step2d_batch_n<3, double>(b, st);
+    case 4: return launch_step2d_batch_n<4, double>(b, st);
+    case 5: return launch_step2d_batch_n<5, double>(b, st);
+    case 6: return launch_step2d_batch_n<6, double>(b, st);
+    case 7: return launch_step2d_batch_n<7, double>(b, st);
+    case 8: return launch_step2d_batch_n<8, double>(b, st);
+    default: return cudaErrorNotSupported;
+    }
+}
 }  // namespace sl
