@@ -133,6 +133,142 @@ def _cpu_baseline(seconds=15.0):
                       f"FP64 C oracle, samples split over {cores} threads)"}
 
 
+def flops_per_esu_2d(N):
+    """Algorithmic flops of one 2D element-sample update (FMA = 2): phase 1
+    Gram n^3 + Gauss-Jordan n^3/2, phase 2 Gram n^2 P (P = n + 4N stacked
+    rows) + Gauss-Jordan n^3/2; the O(n^2) terms are left out."""
+    n = N * N
+    return 2 * (2 * n ** 3 + n * n * (n + 4 * N))
+
+
+def _timed(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def leg_2d(sl, stream):
+    """Config 3 mesh (64x64 elements, N=8): FP32 at M=1024, FP64 at M=64."""
+    out = {"workload": "2D periodic [0,1]^2, 64x64 elements, N=8, rotation drift, "
+                       "D=0.005(1+0.3 sin 2pi x sin 2pi y), dt=1.618e-6 (edge-distance bound; at the "
+                       "node-gap dt 6.93e-5 the 2D interpolation matrix reaches cond ~3e3 at one sigma)"}
+    means = {}
+    for mode, M, steps in (("fp32", 1024, 3), ("fp64", 64, 2)):
+        pb = I.config3(M=M, steps=steps, dt=I.DT_CFG3_EDGE)
+        s = sl.Solver(pb, mode, stream=stream.cuda_stream)
+        s.step(pb["dt"], 1)
+        s.profile(True)
+        s.step(pb["dt"], steps)
+        ms, _ = s.profile_read()
+        s.close()
+        esu = 64 * 64 * M * steps
+        out[mode] = {"value": esu / (ms * 1e-3), "unit": "ESU/s", "M": M, "steps": steps}
+    ach = out["fp32"]["value"] * flops_per_esu_2d(8) / 1e12
+    out["roofline_fp32"] = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / PEAK_FP32_TFLOPS, "flops_per_esu": flops_per_esu_2d(8)}
+    for mode in ("fp64", "fp32"):
+        pb = I.config3(M=32, steps=20, dt=I.DT_CFG3_EDGE)
+        with sl.Solver(pb, mode, stream=stream.cuda_stream) as s:
+            s.step()
+            means[mode] = s.moments()[0]
+    out["error_fp32_vs_fp64"] = float(np.abs(means["fp32"] - means["fp64"]).max() / np.abs(means["fp64"]).max())
+    out["error_what"] = "max rel. difference of the mean, M=32, 20 steps, same seeds"
+    return out
+
+
+def leg_batch(sl, stream):
+    """Batched uneven instances (one graph launch per call) vs the same
+    instances stepped one by one."""
+    import torch
+
+    out = {}
+    two_d = [pb for pb in I.batch_instances(512) if pb["N"] <= 8][:12]
+    one_d = []
+    rng = np.random.default_rng(45)
+    for i in range(32):
+        pb = I.config2(N=int(rng.integers(4, 17)), M=int(rng.integers(256, 2049)), K=int(rng.integers(64, 1025)))
+        pb["seed"] = 7000 + i
+        one_d.append(pb)
+    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config5_1d_mix", one_d, 20)):
+        for pb in pbs:  # half of each instance's particle bound (2D: edge distance)
+            pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
+        esu = sum(int(np.prod(pb["K"])) * pb["M"] for pb in pbs) * steps
+        with sl.Batch(pbs, "fp32") as b:
+            tune_ms = b.tune(2)
+            grids = b.grids()
+            b.step(steps)  # capture
+            t_batch = _timed(lambda: b.step(steps))
+        solvers = [sl.Solver(pb, "fp32", stream=stream.cuda_stream) for pb in pbs]
+        dts = [0.5 * (s.dt_edge if pb["dim"] == 2 else s.dt_max) for s, pb in zip(solvers, pbs)]
+        for s, d in zip(solvers, dts):
+            s.step(d, 1)
+
+        def seq():
+            for s, d in zip(solvers, dts):
+                s.step(d, steps)
+
+        t_seq = _timed(seq)
+        for s in solvers:
+            s.close()
+        torch.cuda.synchronize()
+        out[name] = {"instances": len(pbs), "steps": steps, "esu": esu,
+                     "batched": {"value": esu / t_batch, "unit": "ESU/s"},
+                     "one_by_one": {"value": esu / t_seq, "unit": "ESU/s"},
+                     "speedup": t_seq / t_batch, "tuned_grids": grids, "tune_ms": tune_ms}
+    out["note"] = ("config 4 as drawn (512 instances, N up to 12, 100 steps, ~8.8e10 ESU) is not run: 2D N>10 is "
+                   "not supported and the 2D path runs at ~1e7 ESU/s at N=8; the first 12 draws with N<=8 are "
+                   "timed for one step")
+    return out
+
+
+def leg_serving(sl, duration=5.0, drain=10.0):
+    """Poisson arrivals (200/s) drawn like config 5, served with continuous
+    batching; p50/p99 latency of the completed requests."""
+    reqs = I.serving_requests(rate=200.0, duration=duration, seed=5, steps=20)
+    for _, pb in reqs:
+        pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
+    srv = sl.Server(budget_bytes=64 << 30, slice_steps=5, heavy_slots=2, precision="fp32")
+    t0 = time.perf_counter()
+    tickets = []
+    for ta, pb in reqs:
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append((srv.submit(pb), pb["dim"]))
+    deadline = t0 + duration + drain
+    while time.perf_counter() < deadline:
+        st = srv.stats()
+        if st["queued"] == 0 and st["running"] == 0:
+            break
+        time.sleep(0.05)
+    st = srv.stats()
+    by_dim = {1: [], 2: []}
+    for t, dim in tickets:
+        state, res = srv.poll(t, want=False)
+        if state == 2:
+            by_dim[dim].append(res[2])
+    srv.close()
+    n2d = sum(1 for _, pb in reqs if pb["dim"] == 2)
+    per_dim = {}
+    for dim, lat in by_dim.items():
+        lat = np.sort(np.array(lat))
+        per_dim[f"{dim}d"] = {"completed": int(len(lat)),
+                              "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                              "p99_s": float(np.percentile(lat, 99)) if len(lat) else None}
+    return {"offered_rate_per_s": len(reqs) / duration, "arrival_window_s": duration, "drain_s": drain,
+            "requests": len(reqs), "requests_2d": n2d, "completed": st["completed"], "failed": st["failed"],
+            "rejected": st["rejected"], "pending_at_deadline": st["queued"] + st["running"],
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+            "served_rate_per_s": st["completed"] / max(st["span_s"], 1e-9),
+            "esu_per_s": st["esu_per_s"], "memory_peak_bytes": st["memory_peak"],
+            "by_dim": per_dim, "note": "2D requests with N>10 fail (unsupported); the 2D path dominates the load",
+            "config": "budget 64 GiB, slice 5 steps, 2 heavy slots, FP32 (pair state), 20 steps per request"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores, each step a
     bounded sample of the workload."""
@@ -341,6 +477,11 @@ def run_native(args):
                        "what": "sl_init (phi0 from pinned host memory) + sl_step + sl_moments (to host) + "
                                "sl_free per order, wall clock"}
 
+    if rank == 0 and not args.no_extra:
+        line["config3_2d"] = leg_2d(sl, stream)
+        line["batch"] = leg_batch(sl, stream)
+        line["serving"] = leg_serving(sl, args.serve_seconds)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
 
@@ -363,6 +504,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the 2D, batch and serving legs")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3 and not args.quick:
         args.warmup = 3

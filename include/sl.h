@@ -142,6 +142,15 @@ int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2);
 /* direction (Eq. 1d_timestep), dx_min = smallest node gap times h.          */
 int sl_dt_max(const sl_ctx *c, double *dt);
 
+/* The same bound with dx_min = the first Gauss node's distance to the       */
+/* element face: at this dt a particle moved by u dt + one standard           */
+/* deviation of the diffusion stays inside its element, the paper's reason  */
+/* for restricting dt (Section 5.2: the interpolation matrix stays well      */
+/* conditioned).  In 2D the remap solves with that matrix, so 2D workloads    */
+/* use this bound: at the node-gap bound its condition number reaches ~3e3   */
+/* at one standard deviation and ~5e7 at three (N = 8).                       */
+int sl_dt_edge(const sl_ctx *c, double *dt);
+
 /* Step counter (number of SL steps taken so far). */
 int sl_step_count(const sl_ctx *c, long long *n);
 
@@ -182,7 +191,9 @@ typedef struct {
     sl_mesh mesh;
     int N, M;
     sl_field drift, diffusion, phi0;
-    double dt;                /* this instance's time step                  */
+    double dt;                /* dt_rule 0: the time step; 1: fraction of     */
+                              /* sl_dt_max; 2: fraction of sl_dt_edge       */
+    int dt_rule;
     unsigned long long seed;  /* this instance's Philox key                 */
 } sl_instance;
 
@@ -214,18 +225,23 @@ void sl_batch_free(sl_batch *b);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: solves submitted over time, run with continuous batching.  A     */
-/* scheduler thread admits queued requests in arrival order while their      */
-/* device footprint fits in `budget_bytes` beside the running ones (a        */
-/* request larger than the budget is rejected with SL_ERR_OOM), advances     */
-/* every running request by up to `slice_steps` steps per round on one of    */
-/* `streams` CUDA streams (their kernels overlap on the GPU), and completes   */
-/* finished requests (moments, memory released, latency = completion minus   */
-/* submission).  Each request's result equals the request run alone.        */
+/* scheduler thread admits queued requests in arrival order, backfilling,    */
+/* while their device footprint fits in `budget_bytes` beside the running    */
+/* ones (a request larger than the budget is rejected with SL_ERR_OOM);      */
+/* each running request advances by slices of up to `slice_steps` steps on   */
+/* its own stream as soon as its previous slice is done (requests' kernels   */
+/* overlap on the GPU); requests with more than ~2e9 operations per step run */
+/* one step per slice on a low-priority stream, lighter ones on a high-     */
+/* priority stream; finished requests complete (moments, memory released    */
+/* through the stream-ordered allocator, latency = completion minus         */
+/* submission).  Each result equals the request run alone.                  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     size_t budget_bytes; /* device memory the running requests may hold        */
     int slice_steps;     /* steps per request per scheduling round (>= 1)      */
-    int streams;         /* CUDA streams (1..64)                               */
+    int heavy_slots;     /* heavy requests (estimated >= ~1 ms of GPU work per  */
+                         /* step) running at once; 0 = no limit.  Light ones    */
+                         /* are limited by the budget alone                    */
     int precision;       /* SL_FP64, SL_MIXED or SL_FP32                        */
     int device;          /* CUDA device ordinal; -1 = current                   */
 } sl_server_config;
@@ -250,7 +266,8 @@ int sl_server_poll(sl_server *s, long long ticket, int *state, double *mean, dou
 /* Waits until nothing is queued or running (SL_ERR_TIMEOUT after timeout_s). */
 int sl_server_wait_idle(sl_server *s, double timeout_s);
 int sl_server_stats_get(sl_server *s, sl_server_stats *out);
-/* Stops admitting, finishes the running requests, releases everything.     */
+/* Stops: slices in flight complete, queued and running requests are        */
+/* abandoned, everything is released.                                        */
 void sl_server_free(sl_server *s);
 
 /* Allocation-free sample moments.  The paper has no counterpart: this entry  */

@@ -84,6 +84,8 @@ def lib():
                                   dp, dp, dp, dp]
             L.orc_dt_max.restype = C.c_double
             L.orc_dt_max.argtypes = [C.POINTER(_Problem)]
+            L.orc_dt_edge.restype = C.c_double
+            L.orc_dt_edge.argtypes = [C.POINTER(_Problem)]
             _lib = L
     return _lib
 
@@ -304,6 +306,11 @@ def coeffs(pb, dt=None):
 def dt_max(pb):
     p = _problem(pb, dt=0.0)
     return lib().orc_dt_max(C.byref(p))
+
+
+def dt_edge(pb):
+    p = _problem(pb, dt=0.0)
+    return lib().orc_dt_edge(C.byref(p))
 
 
 def run(pb, nsteps=None, step0=0, s0=0, ns=None, nthreads=1, state_in=None,

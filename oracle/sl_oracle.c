@@ -992,7 +992,7 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
 /* Largest dt with |u|max dt + sqrt(2 Dmax dt) <= dx_min in every direction */
 /* (Eq. 1d_timestep; Eq. 1d_difftimestep when u = 0), dx_min being the       */
 /* smallest node-to-node gap times h, maxima over the nodes.                 */
-double orc_dt_max(const orc_problem *pb)
+static double orc_dt_bound(const orc_problem *pb, int edge)
 {
     orc_problem q = *pb;
     q.dt = 1.0;
@@ -1001,6 +1001,7 @@ double orc_dt_max(const orc_problem *pb)
     double gap = 1.0;
     for (int i = 0; i + 1 < cf.N; ++i)
         if (cf.xi[i + 1] - cf.xi[i] < gap) gap = cf.xi[i + 1] - cf.xi[i];
+    if (edge) gap = cf.xi[0]; /* distance of the first node to the element face */
     double best = INFINITY;
     for (int d = 0; d < cf.dim; ++d) {
         double umax = 0.0, bmax = 0.0;
@@ -1023,3 +1024,11 @@ double orc_dt_max(const orc_problem *pb)
     orc_coeffs_free(&cf);
     return best;
 }
+
+double orc_dt_max(const orc_problem *pb) { return orc_dt_bound(pb, 0); }
+
+/* The same bound with dx_min = the first node's distance to the element     */
+/* face: a particle moved by u dt plus one standard deviation of the        */
+/* diffusion stays inside its element (the paper restricts dt so that      */
+/* particles do not leave the subdomain, Section 5.2).                       */
+double orc_dt_edge(const orc_problem *pb) { return orc_dt_bound(pb, 1); }

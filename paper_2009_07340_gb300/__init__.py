@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_init", "sl_step",
            "sl_moments", "sl_moments_device", "sl_dt_max", "sl_step_count", "sl_get_samples",
-           "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_profile", "sl_profile_read",
+           "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_dt_edge", "sl_profile", "sl_profile_read",
            "sl_moments_static", "sl_free", "sl_strerror"]
 
 SL_FP64, SL_MIXED, SL_FP32 = 0, 1, 2
@@ -54,11 +54,12 @@ class sl_options(C.Structure):
 
 class sl_instance(C.Structure):
     _fields_ = [("mesh", sl_mesh), ("N", C.c_int), ("M", C.c_int), ("drift", sl_field),
-                ("diffusion", sl_field), ("phi0", sl_field), ("dt", C.c_double), ("seed", C.c_ulonglong)]
+                ("diffusion", sl_field), ("phi0", sl_field), ("dt", C.c_double), ("dt_rule", C.c_int),
+                ("seed", C.c_ulonglong)]
 
 
 class sl_server_config(C.Structure):
-    _fields_ = [("budget_bytes", C.c_size_t), ("slice_steps", C.c_int), ("streams", C.c_int),
+    _fields_ = [("budget_bytes", C.c_size_t), ("slice_steps", C.c_int), ("heavy_slots", C.c_int),
                 ("precision", C.c_int), ("device", C.c_int)]
 
 
@@ -87,6 +88,7 @@ def lib():
         L.sl_moments.argtypes = [vp, _dp, _dp]
         L.sl_moments_device.argtypes = [vp, vp, vp]
         L.sl_dt_max.argtypes = [vp, _dp]
+        L.sl_dt_edge.argtypes = [vp, _dp]
         L.sl_step_count.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.sl_set_step_count.argtypes = [vp, C.c_longlong]
         L.sl_get_samples.argtypes = [vp, C.c_int, C.c_int, _dp]
@@ -205,6 +207,12 @@ def sl_dt_max(ctx):
     return v.value
 
 
+def sl_dt_edge(ctx):
+    v = C.c_double()
+    _check(lib().sl_dt_edge(C.c_void_p(ctx), C.byref(v)), "sl_dt_edge")
+    return v.value
+
+
 def sl_step_count(ctx):
     v = C.c_longlong()
     _check(lib().sl_step_count(C.c_void_p(ctx), C.byref(v)), "sl_step_count")
@@ -264,7 +272,14 @@ def _instance(pb, dt=None, seed=None):
     inst.drift = _field(_U, pb["drift"])
     inst.diffusion = _field(_D, pb["diffusion"])
     inst.phi0 = _field(_PHI, pb["phi0"])
-    inst.dt = float(pb["dt"] if dt is None else dt)
+    d = pb["dt"] if dt is None else dt
+    # a problem's dt may be ("node", f) / ("edge", f): f times sl_dt_max / sl_dt_edge
+    if isinstance(d, (tuple, list)):
+        inst.dt_rule = {"node": 1, "edge": 2}[d[0]]
+        inst.dt = float(d[1])
+    else:
+        inst.dt_rule = 0
+        inst.dt = float(d)
     inst.seed = int(pb["seed"] if seed is None else seed)
     return inst
 
@@ -369,11 +384,11 @@ class Batch:
 class Server:
     """Continuous-batching server of drift-diffusion solves (see include/sl.h)."""
 
-    def __init__(self, budget_bytes, slice_steps=10, streams=8, precision="fp32", device=-1):
+    def __init__(self, budget_bytes, slice_steps=10, heavy_slots=2, precision="fp32", device=-1):
         cfg = sl_server_config()
         cfg.budget_bytes = int(budget_bytes)
         cfg.slice_steps = int(slice_steps)
-        cfg.streams = int(streams)
+        cfg.heavy_slots = int(heavy_slots)
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.device = device
         h = C.c_void_p()
@@ -469,6 +484,10 @@ class Solver:
     @property
     def dt_max(self):
         return sl_dt_max(self.ctx)
+
+    @property
+    def dt_edge(self):
+        return sl_dt_edge(self.ctx)
 
     @property
     def step_count(self):

@@ -45,12 +45,12 @@ sl::FieldDev to_dev(const sl_field *f)
 }
 
 template <typename T>
-cudaError_t dalloc(T **p, size_t count)
+cudaError_t dalloc(const sl_ctx *c, T **p, size_t count)
 {
-    return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+    return sl::ctx_alloc(c, reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
 
-// Chebyshev-Gauss nodes (host copy for the time-step guard only).
+// Chebyshev-Gauss nodes (host copy for the time-step guards only).
 double host_min_gap(int N)
 {
     double g = 1.0;
@@ -60,6 +60,16 @@ double host_min_gap(int N)
         g = std::min(g, b - a);
     }
     return g;
+}
+
+double host_edge_gap(int N) { return 0.5 * (1.0 - std::cos(0.5 * M_PI / N)); }
+
+// Largest dt with |u|max dt + sqrt(2 Dmax dt) <= dx in direction d (Eq. 1d_timestep).
+double step_bound(double umax, double bmax, double dx)
+{
+    if (umax == 0.0) return bmax > 0.0 ? dx * dx / (bmax * bmax) : INFINITY;
+    const double s = (-bmax + std::sqrt(bmax * bmax + 4.0 * umax * dx)) / (2.0 * umax);
+    return s * s;
 }
 
 }  // namespace
@@ -89,20 +99,20 @@ void sl_free(sl_ctx *c)
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
-    cudaFree(c->xi);
-    cudaFree(c->nodeU);
-    cudaFree(c->nodeB);
-    cudaFree(c->nodeDiv);
-    cudaFree(c->faceU);
-    cudaFree(c->faceB);
-    cudaFree(c->Q);
-    cudaFree(c->dW);
-    cudaFree(c->psum);
-    cudaFree(c->psq);
-    cudaFree(c->mean_tmp);
-    cudaFree(c->m2_tmp);
-    cudaFree(c->err);
-    cudaFree(c->faces2d);
+    sl::ctx_free(c, c->xi);
+    sl::ctx_free(c, c->nodeU);
+    sl::ctx_free(c, c->nodeB);
+    sl::ctx_free(c, c->nodeDiv);
+    sl::ctx_free(c, c->faceU);
+    sl::ctx_free(c, c->faceB);
+    sl::ctx_free(c, c->Q);
+    sl::ctx_free(c, c->dW);
+    sl::ctx_free(c, c->psum);
+    sl::ctx_free(c, c->psq);
+    sl::ctx_free(c, c->mean_tmp);
+    sl::ctx_free(c, c->m2_tmp);
+    sl::ctx_free(c, c->err);
+    sl::ctx_free(c, c->faces2d);
     delete c;
 }
 
@@ -156,15 +166,15 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     const int nf = dim == 1 ? m.E : 2 * m.E * N;
     c->mom_chunk = 64;
     const int nc = (M + c->mom_chunk - 1) / c->mom_chunk;
-    bool ok = dalloc(&c->xi, N) == cudaSuccess && dalloc(&c->nodeU, size_t(dim) * V) == cudaSuccess &&
-              dalloc(&c->nodeB, V) == cudaSuccess && dalloc(&c->nodeDiv, V) == cudaSuccess &&
-              dalloc(&c->faceU, nf) == cudaSuccess && dalloc(&c->faceB, nf) == cudaSuccess &&
-              cudaMalloc(&c->Q, size_t(M) * V * c->state_elem) == cudaSuccess &&
-              dalloc(&c->psum, size_t(nc) * V) == cudaSuccess && dalloc(&c->psq, size_t(nc) * V) == cudaSuccess &&
-              dalloc(&c->mean_tmp, V) == cudaSuccess && dalloc(&c->m2_tmp, V) == cudaSuccess &&
-              dalloc(&c->err, 1) == cudaSuccess;
+    bool ok = dalloc(c, &c->xi, N) == cudaSuccess && dalloc(c, &c->nodeU, size_t(dim) * V) == cudaSuccess &&
+              dalloc(c, &c->nodeB, V) == cudaSuccess && dalloc(c, &c->nodeDiv, V) == cudaSuccess &&
+              dalloc(c, &c->faceU, nf) == cudaSuccess && dalloc(c, &c->faceB, nf) == cudaSuccess &&
+              sl::ctx_alloc(c, &c->Q, size_t(M) * V * c->state_elem) == cudaSuccess &&
+              dalloc(c, &c->psum, size_t(nc) * V) == cudaSuccess && dalloc(c, &c->psq, size_t(nc) * V) == cudaSuccess &&
+              dalloc(c, &c->mean_tmp, V) == cudaSuccess && dalloc(c, &c->m2_tmp, V) == cudaSuccess &&
+              dalloc(c, &c->err, 1) == cudaSuccess;
     if (ok && dim == 2)
-        ok = cudaMalloc(&c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
+        ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         sl_free(c);
@@ -172,9 +182,9 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     }
     double *nodal_dev = nullptr;
     if (phi0->kind == SL_PHI_NODAL) {
-        if (cudaMalloc(&nodal_dev, V * sizeof(double)) != cudaSuccess ||
-            cudaMemcpy(nodal_dev, phi0->nodal, V * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaFree(nodal_dev);
+        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&nodal_dev), V * sizeof(double)) != cudaSuccess ||
+            cudaMemcpyAsync(nodal_dev, phi0->nodal, V * sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
+            sl::ctx_free(c, nodal_dev);
             sl_free(c);
             return SL_ERR_OOM;
         }
@@ -188,29 +198,23 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e == cudaSuccess) e = cudaMemcpy(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    cudaFree(nodal_dev);
+    sl::ctx_free(c, nodal_dev);
     if (e != cudaSuccess) {
         sl_free(c);
         return SL_ERR_CUDA;
     }
-    double best = INFINITY;
-    const double gap = host_min_gap(N);
+    double best = INFINITY, best_edge = INFINITY;
+    const double gap = host_min_gap(N), edge = host_edge_gap(N);
     double bmax = 0.0;
     for (double b : hb) bmax = std::max(bmax, b);
     for (int d = 0; d < dim; ++d) {
         double umax = 0.0;
         for (long long v = 0; v < V; ++v) umax = std::max(umax, std::fabs(hu[size_t(d) * V + v]));
-        const double dx = gap * m.h[d];
-        double dt;
-        if (umax == 0.0)
-            dt = bmax > 0.0 ? dx * dx / (bmax * bmax) : INFINITY;
-        else {
-            const double s = (-bmax + std::sqrt(bmax * bmax + 4.0 * umax * dx)) / (2.0 * umax);
-            dt = s * s;
-        }
-        best = std::min(best, dt);
+        best = std::min(best, step_bound(umax, bmax, gap * m.h[d]));
+        best_edge = std::min(best_edge, step_bound(umax, bmax, edge * m.h[d]));
     }
     c->dtmax = best;
+    c->dtedge = best_edge;
 
     if (dim == 1) {
         const int K = m.K[0];
@@ -232,6 +236,13 @@ int sl_dt_max(const sl_ctx *c, double *dt)
 {
     if (!c || !dt) return SL_ERR_ARG;
     *dt = c->dtmax;
+    return SL_OK;
+}
+
+int sl_dt_edge(const sl_ctx *c, double *dt)
+{
+    if (!c || !dt) return SL_ERR_ARG;
+    *dt = c->dtedge;
     return SL_OK;
 }
 
@@ -262,10 +273,10 @@ int sl_step(sl_ctx *c, double dt, int steps)
     const size_t per_step = size_t(c->M) * dim * sizeof(double);
     const int chunk = int(std::max<size_t>(1, std::min<size_t>(size_t(steps), kWienerScratchBytes / per_step)));
     if (chunk > c->dW_cap) {
-        cudaFree(c->dW);
+        sl::ctx_free(c, c->dW);
         c->dW = nullptr;
         c->dW_cap = 0;
-        if (cudaMalloc(&c->dW, chunk * per_step) != cudaSuccess) {
+        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&c->dW), chunk * per_step) != cudaSuccess) {
             cudaGetLastError();
             return SL_ERR_OOM;
         }
@@ -458,14 +469,14 @@ int sl_wiener(sl_ctx *c, long long step0, int nsteps, double dt, double *out)
     const size_t n = size_t(nsteps) * c->M * c->m.dim;
     if (n == 0) return SL_OK;
     double *d = nullptr;
-    if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) {
+    if (sl::ctx_alloc(c, reinterpret_cast<void **>(&d), n * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return SL_ERR_OOM;
     }
     cudaError_t e = sl::launch_wiener(c->seed, step0, c->sample0, nsteps, c->M, c->m.dim, std::sqrt(dt), d, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    cudaFree(d);
+    sl::ctx_free(c, d);
     return e == cudaSuccess ? SL_OK : fail_cuda(c);
 }
 

@@ -90,16 +90,18 @@ int ensure_capacity(sl_batch *b, int steps)
     if (steps <= b->cap_steps) return SL_OK;
     drop_graphs(b);
     for (sl_ctx *c : b->inst) {
-        cudaFree(c->dW);
+        sl::ctx_free(c, c->dW);
         c->dW = nullptr;
         c->dW_cap = 0;
-        if (cudaMalloc(&c->dW, size_t(steps) * c->M * c->m.dim * sizeof(double)) != cudaSuccess) {
+        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&c->dW), size_t(steps) * c->M * c->m.dim * sizeof(double)) !=
+            cudaSuccess) {
             cudaGetLastError();
             return SL_ERR_OOM;
         }
         c->dW_cap = steps;
     }
     b->cap_steps = steps;
+    if (cudaStreamSynchronize(b->st) != cudaSuccess) return SL_ERR_CUDA;  // new buffers ready before use by the graph
     std::vector<sl::WienerJob> jobs(b->inst.size());
     for (size_t i = 0; i < b->inst.size(); ++i) {
         const sl_ctx *c = b->inst[i];
@@ -305,7 +307,7 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
     }
     for (int i = 0; i < count; ++i) {
         const sl_instance &s = specs[i];
-        if (!(s.dt > 0.0) || !std::isfinite(s.dt)) {
+        if (!(s.dt > 0.0) || !std::isfinite(s.dt) || s.dt_rule < 0 || s.dt_rule > 2 || (s.dt_rule > 0 && s.dt > 1.0)) {
             sl_batch_free(b);
             return SL_ERR_ARG;
         }
@@ -318,13 +320,14 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
             sl_batch_free(b);
             return rc;
         }
-        if (o.strict_dt && s.dt > c->dtmax * (1.0 + 1e-12)) {
+        const double dt = s.dt_rule == 0 ? s.dt : s.dt * (s.dt_rule == 1 ? c->dtmax : c->dtedge);
+        if (o.strict_dt && dt > c->dtmax * (1.0 + 1e-12)) {
             sl_free(c);
             sl_batch_free(b);
             return SL_ERR_DT;
         }
         b->inst.push_back(c);
-        b->dt.push_back(s.dt);
+        b->dt.push_back(dt);
     }
     int dev = 0;
     cudaGetDevice(&dev);

@@ -120,7 +120,8 @@ struct sl_ctx {
     int device = 0;
     long long step = 0;
     int poisoned = 0;
-    double dtmax = 0.0;
+    double dtmax = 0.0;   // Eq. (1d_timestep) with the smallest node gap
+    double dtedge = 0.0;  // the same with the first node's distance to the element face
     // device memory owned by the context
     double *xi = nullptr, *nodeU = nullptr, *nodeB = nullptr, *nodeDiv = nullptr;
     double *faceU = nullptr, *faceB = nullptr;
@@ -151,4 +152,19 @@ struct WienerJob {
 cudaError_t launch_wiener_batch(const WienerJob *jobs, const long long *prefix, int njobs, int nsteps,
                                 const long long *steps, long long total, cudaStream_t st);
 cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_t st);
+}  // namespace sl
+
+namespace sl {
+// Context memory comes from the stream-ordered allocator on the context's
+// stream: allocating and releasing it never synchronises the device, so
+// contexts created and freed while other work runs (the server) do not wait
+// for that work.
+inline cudaError_t ctx_alloc(const sl_ctx *c, void **p, size_t bytes)
+{
+    return cudaMallocAsync(p, bytes > 0 ? bytes : 1, c->st);
+}
+inline void ctx_free(const sl_ctx *c, void *p)
+{
+    if (p) cudaFreeAsync(p, c->st);
+}
 }  // namespace sl

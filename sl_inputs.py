@@ -44,6 +44,7 @@ DT_CFG1 = 6.510e-4  # K=8, N=6, u=1, D=0.01, edge gap: particles stay in-element
 DT_CFG2 = 7.33e-7   # K=256, N=16 node gap, |u|max=1.5, Dmax=0.015 (used for every N)
 DT_CFG2_HALF = 3.665e-7  # half of it: at DT_CFG2 itself the N=16 step amplifies perturbations
 DT_CFG3 = 6.93e-5   # 64x64, N=8 node gap, |u_j|max=pi, Dmax=0.0065
+DT_CFG3_EDGE = 1.618e-6  # the same with the first node's distance to the face (particles stay inside)
 
 
 def problem(dim, K, lo, hi, N, M, steps, dt, seed, drift, diffusion, phi0):
@@ -93,11 +94,12 @@ def config2(N=16, M=4096, steps=1000, K=256, dt=DT_CFG2):
                    ("sin", [1.0, 0.5, 1.0]), ("cos", [0.01, 0.5, 1.0]), fourier_phi0(2))
 
 
-def config3(M=1024, steps=500, K=64, N=8):
+def config3(M=1024, steps=500, K=64, N=8, dt=DT_CFG3):
     """2D periodic [0,1]^2, 64x64 elements, N=8, M=1024, solid-body rotation
     (omega = 2 pi) about (0.5, 0.5), D = 0.005 (1 + 0.3 sin 2 pi x sin 2 pi y),
-    Gaussian blob (0.5, 0.75), sigma 0.05, 500 steps."""
-    return problem(2, (K, K), (0.0, 0.0), (1.0, 1.0), N, M, steps, DT_CFG3, 3,
+    Gaussian blob (0.5, 0.75), sigma 0.05, 500 steps (node-gap dt, or the
+    dt given)."""
+    return problem(2, (K, K), (0.0, 0.0), (1.0, 1.0), N, M, steps, dt, 3,
                    ("rotation", [2.0 * np.pi, 0.5, 0.5]), ("sinsin", [0.005, 0.3, 2.0, 2.0]),
                    ("gauss", [1.0, 0.05, 0.5, 0.75]))
 

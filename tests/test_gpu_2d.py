@@ -88,6 +88,25 @@ def test_fp32_vs_fp64(sl, orc, N):
     assert _rel(m32, m64) <= MIXED_TOL
 
 
+def test_config3_mesh_fp32_vs_fp64_edge_dt(sl, orc):
+    # the 64x64, N=8 mesh at the edge-distance dt, 32 samples, 20 steps
+    pb = I.config3(M=32, steps=20, dt=I.DT_CFG3_EDGE)
+    with sl.Solver(pb, "fp64") as s:
+        assert s.dt_edge == pytest.approx(orc.dt_edge(pb), rel=1e-12)
+        assert s.dt_max == pytest.approx(orc.dt_max(pb), rel=1e-12)
+        s.step()
+        m64, _ = s.moments()
+        s0 = s.samples(0, 1)[0]
+    with sl.Solver(pb, "fp32") as s:
+        s.step()
+        m32, _ = s.moments()
+    assert _rel(m32, m64) <= MIXED_TOL
+    ref = orc.run(I.with_(pb, steps=3), ns=1, want_states=True)["states"][0]
+    with sl.Solver(pb, "fp64") as s:
+        s.step(steps=3)
+        assert _rel(s.samples(0, 1)[0], ref) <= FP64_TOL
+
+
 @pytest.mark.parametrize("N", [9, 10])
 def test_fp32_high_order_vs_oracle(sl, orc, N):
     pb = _rot(K=(3, 3), N=N, M=2, steps=3, orc=orc)

@@ -35,7 +35,8 @@ def _requests(orc):
         pb["seed"] = 500 + i
         pb["dt"] = 0.5 * orc.dt_max(pb)
         reqs.append(pb)
-    for i, (K, N, M) in enumerate([((5, 5), 4, 6), ((8, 4), 3, 10)]):
+    # the last two are heavy (E M n^3 > 2e9 per step): one heavy slot serves them in turn
+    for i, (K, N, M) in enumerate([((5, 5), 4, 6), ((8, 4), 3, 10), ((8, 8), 8, 600), ((8, 8), 7, 900)]):
         pb = I.problem(2, K, (0.0, 0.0), (1.0, 1.0), N, M, 9, 0.0, 600 + i,
                        ("rotation", [2 * np.pi, 0.5, 0.5]), ("const", [0.003]), ("gauss", [1.0, 0.2, 0.5, 0.5]))
         pb["dt"] = 0.5 * orc.dt_max(pb)
@@ -46,7 +47,7 @@ def _requests(orc):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_mix_equals_alone(sl, orc, precision):
     reqs = _requests(orc)
-    with sl.Server(budget_bytes=2 << 30, slice_steps=2, streams=4, precision=precision) as srv:
+    with sl.Server(budget_bytes=2 << 30, slice_steps=2, heavy_slots=1, precision=precision) as srv:
         tickets = [srv.submit(pb) for pb in reqs[:3]]
         time.sleep(0.02)  # the rest arrive while the first ones run
         tickets += [srv.submit(pb) for pb in reqs[3:]]
@@ -70,7 +71,7 @@ def test_budget_admission_and_rejection(sl, orc):
     big = I.config2(N=16, M=4096, steps=5, K=256)  # ~140 MB of state
     big["dt"] = I.DT_CFG2_HALF
     budget = 40 << 20
-    with sl.Server(budget_bytes=budget, slice_steps=3, streams=2, precision="fp64") as srv:
+    with sl.Server(budget_bytes=budget, slice_steps=3, heavy_slots=0, precision="fp64") as srv:
         tickets = [srv.submit(pb) for pb in reqs]
         tb = srv.submit(big)
         srv.wait_idle(300)

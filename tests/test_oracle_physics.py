@@ -148,6 +148,9 @@ def test_time_step_condition(orc):
     xi = orc.nodes(8)
     dx = np.min(np.diff(xi)) * 0.25
     assert orc.dt_max(pb) == pytest.approx(dx * dx / 2.0, rel=1e-12)
+    # the edge bound uses the first node's distance to the face
+    assert orc.dt_edge(pb) == pytest.approx((xi[0] * 0.25) ** 2 / 2.0, rel=1e-12)
+    assert orc.dt_edge(I.config3()) == pytest.approx(I.DT_CFG3_EDGE, rel=1e-3)
 
 
 def test_moment_bookkeeping(orc):
