@@ -111,6 +111,16 @@ typedef struct {
 
 typedef struct sl_ctx sl_ctx; /* opaque; owns all of its device memory */
 
+/* Prepares every kernel of the library on `device` (-1 = current device),  */
+/* once per process: loads it and sets its shared-memory limit, and creates */
+/* the library's memory pool for the device.  Under CUDA's lazy module      */
+/* loading a kernel is loaded at its first launch, and a load may wait for  */
+/* all work on the device; a solver created while other solvers' long       */
+/* kernels run would then stall.  sl_init, sl_batch_create and              */
+/* sl_server_create call it; calling it earlier moves the cost (tens of     */
+/* milliseconds) to a time of the caller's choosing.  SL_OK or SL_ERR_CUDA. */
+int sl_preload(int device);
+
 /* Creates a solver for M samples of order N (N Gauss nodes per direction,  */
 /* 2 <= N <= 16) on `mesh`, evaluates the fields at the nodes and faces and  */
 /* sets every sample to phi0 (Section 5.1).  1D: K <= 2048 elements.         */

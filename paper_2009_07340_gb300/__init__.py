@@ -85,6 +85,7 @@ def lib():
         L.sl_init.argtypes = [C.POINTER(vp), C.POINTER(sl_mesh), C.c_int, C.c_int, C.POINTER(sl_field),
                               C.POINTER(sl_field), C.POINTER(sl_field), C.POINTER(sl_options)]
         L.sl_step.argtypes = [vp, C.c_double, C.c_int]
+        L.sl_preload.argtypes = [C.c_int]
         L.sl_moments.argtypes = [vp, _dp, _dp]
         L.sl_moments_device.argtypes = [vp, vp, vp]
         L.sl_dt_max.argtypes = [vp, _dp]
@@ -183,6 +184,11 @@ def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, devi
     _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
                          C.byref(opt)), "sl_init")
     return h.value
+
+
+def sl_preload(device=-1):
+    """Prepares every kernel of the library on `device` (once per process)."""
+    _check(lib().sl_preload(int(device)), "sl_preload")
 
 
 def sl_step(ctx, dt, steps):

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -74,7 +75,74 @@ double step_bound(double umax, double bmax, double dx)
 
 }  // namespace
 
+namespace sl {
+
+namespace {
+std::mutex g_load_mu;
+unsigned long long g_loaded = 0;  // bit d: device d's kernels are prepared and its pool exists
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaMemPool_t device_pool(int device)
+{
+    return device >= 0 && device < 64 ? g_pool[device] : nullptr;
+}
+
+cudaError_t ensure_loaded()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    const unsigned long long bit = 1ull << dev;
+    std::lock_guard<std::mutex> lk(g_load_mu);
+    if (g_loaded & bit) return cudaSuccess;
+    e = preload_setup();
+    if (e == cudaSuccess) e = preload_step1d_fp64();
+    if (e == cudaSuccess) e = preload_step1d_mixed();
+    if (e == cudaSuccess) e = preload_step1d_fp32();
+    if (e == cudaSuccess) e = preload_step2d_fp64();
+    if (e == cudaSuccess) e = preload_step2d_fp32();
+    if (e == cudaSuccess && !g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&g_pool[dev], &props);
+        if (e == cudaSuccess) {
+            unsigned long long keep = ~0ull;  // no release at synchronisation points
+            e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        if (e == cudaSuccess) {
+            // A block freed on one stream but not yet reached there is never
+            // handed to another stream: that reuse would make the allocating
+            // stream wait for the freeing one (a light solver created while a
+            // heavy one's queue is long).  Blocks whose free has executed are
+            // still reused across streams.
+            int no = 0;
+            e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolReuseAllowInternalDependencies, &no);
+        }
+    }
+    if (e == cudaSuccess) g_loaded |= bit;
+    return e;
+}
+
+}  // namespace sl
+
 extern "C" {
+
+int sl_preload(int device)
+{
+    if (device >= 0 && cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_CUDA;
+    }
+    if (sl::ensure_loaded() != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_CUDA;
+    }
+    return SL_OK;
+}
 
 const char *sl_strerror(int code)
 {
@@ -140,6 +208,10 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (opt && (opt->sample0 < 0 || opt->sample0 + M > (1ll << 32))) return SL_ERR_ARG;
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
+    if (sl::ensure_loaded() != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_CUDA;
+    }
     sl_ctx *c = new (std::nothrow) sl_ctx;
     if (!c) return SL_ERR_OOM;
     cudaGetDevice(&c->device);
@@ -195,9 +267,11 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
                                    c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M, precision == SL_FP64, c->st);
     // maxima for the time-step guard (host copy of the node coefficients)
     std::vector<double> hu(size_t(dim) * V), hb(V);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    if (e == cudaSuccess) e = cudaMemcpy(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost);
     sl::ctx_free(c, nodal_dev);
     if (e != cudaSuccess) {
         sl_free(c);

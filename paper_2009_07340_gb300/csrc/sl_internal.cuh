@@ -106,6 +106,36 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk,
                            double *psum, double *psq, double *mean, double *m2, cudaStream_t st);
 
+// Module loading.  With lazy loading (the default), the first launch of a
+// kernel loads it, and a load may synchronise the whole device: a request
+// whose kernel is first launched while another request's long kernels run
+// would wait for them.  Each unit's preload function prepares every kernel
+// it holds (prepare_kernel: load, shared-memory limit); ensure_loaded() runs
+// them all once per device, before any launch.
+template <typename F>
+cudaError_t prepare_kernel(F f)
+{
+    // Loads kernel f and lets its launches use the device's whole opt-in
+    // shared memory.  The limit is set here once: changing a kernel's
+    // attribute while an instance of it runs can wait for that instance,
+    // which would stall a launch from one request behind another's kernel.
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    int dev = 0, optin = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+    return e;
+}
+cudaError_t preload_step1d_fp64();
+cudaError_t preload_step1d_mixed();
+cudaError_t preload_step1d_fp32();
+cudaError_t preload_step2d_fp64();
+cudaError_t preload_step2d_fp32();
+cudaError_t preload_setup();
+cudaError_t ensure_loaded();
+
 }  // namespace sl
 
 // Solver context (opaque in the ABI).
@@ -155,13 +185,16 @@ cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_
 }  // namespace sl
 
 namespace sl {
-// Context memory comes from the stream-ordered allocator on the context's
-// stream: allocating and releasing it never synchronises the device, so
-// contexts created and freed while other work runs (the server) do not wait
-// for that work.
+// Context memory comes from the library's stream-ordered memory pool of the
+// context's device (created by ensure_loaded): allocating and releasing it
+// never synchronises the device, so contexts created and freed while other
+// work runs (the server) do not wait for that work.  The pool keeps freed
+// memory mapped for reuse (cudaMemPoolTrimTo releases it) and reuses a block
+// on another stream only once its free has executed.
+cudaMemPool_t device_pool(int device);
 inline cudaError_t ctx_alloc(const sl_ctx *c, void **p, size_t bytes)
 {
-    return cudaMallocAsync(p, bytes > 0 ? bytes : 1, c->st);
+    return cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, device_pool(c->device), c->st);
 }
 inline void ctx_free(const sl_ctx *c, void *p)
 {

@@ -301,4 +301,18 @@ cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long 
     return cudaGetLastError();
 }
 
+cudaError_t preload_setup()
+{
+    cudaError_t e = prepare_kernel(init_nodes_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(init_nodes_kernel<float2>);
+    if (e == cudaSuccess) e = prepare_kernel(init_faces_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(wiener_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(wiener_batch_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(advance_counters_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
+    return e;
+}
+
 }  // namespace sl

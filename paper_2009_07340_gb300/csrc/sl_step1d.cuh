@@ -469,8 +469,6 @@ cudaError_t launch_step1d_n(const Step1DArgs &a, cudaStream_t st)
 {
     const size_t smem = step1d_smem_bytes_t<MODE>(N, a.S, a.T);
     auto kern = sl1d_step_kernel<N, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     const int slots = (a.M + a.S - 1) / a.S;
     cfg.gridDim = dim3(unsigned(slots * a.C));
@@ -514,9 +512,7 @@ template <int N, int MODE>
 cudaError_t launch_sl1d_step_kernel_batch_n(const Batch1DLaunch &b, cudaStream_t st)
 {
     auto kern = sl1d_step_kernel_batch<N, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b.smem));
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     kern<<<b.grid, kMaxThreads1D, b.smem, st>>>(b.args, b.prefix, b.ninst, b.counter);
     return cudaGetLastError();
@@ -543,6 +539,25 @@ cudaError_t launch_sl1d_step_kernel_batch_mode(const Batch1DLaunch &b, int N, cu
     case 16: return launch_sl1d_step_kernel_batch_n<16, MODE>(b, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Prepares the step kernels of one mode for every order.
+template <int MODE, int... I>
+cudaError_t preload_step1d_seq(std::integer_sequence<int, I...>)
+{
+    cudaError_t e = cudaSuccess;
+    auto one = [&](auto f) {
+        if (e == cudaSuccess) e = prepare_kernel(f);
+    };
+    (one(sl1d_step_kernel<I + 2, MODE>), ...);
+    (one(sl1d_step_kernel_batch<I + 2, MODE>), ...);
+    return e;
+}
+
+template <int MODE>
+cudaError_t preload_step1d_mode()
+{
+    return preload_step1d_seq<MODE>(std::make_integer_sequence<int, kMaxN - 1>{});
 }
 
 }  // namespace sl

@@ -398,14 +398,22 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
     const unsigned block = unsigned(G::GPC * G::GS);
     auto k1 = sl2d_step_kernel<N, R, 1, false>;
     auto k2 = sl2d_step_kernel<N, R, 2, false>;
-    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     for (int t = 0; t < a.nsteps; ++t) {
         k1<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
         k2<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
     }
     return cudaGetLastError();
+}
+
+// Prepares the four kernels of one order (two phases, single and batched).
+template <int N, typename R>
+cudaError_t preload_step2d_n()
+{
+    cudaError_t e = prepare_kernel(sl2d_step_kernel<N, R, 1, false>);
+    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, false>);
+    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 1, true>);
+    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, true>);
+    return e;
 }
 
 // All instances of one order N, `nsteps` steps: two launches per step.
@@ -418,9 +426,6 @@ cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
     const unsigned block = unsigned(G::GPC * G::GS);
     auto k1 = sl2d_step_kernel<N, R, 1, true>;
     auto k2 = sl2d_step_kernel<N, R, 2, true>;
-    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     Step2DArgs none = {};
     for (int t = 0; t < b.nsteps; ++t) {
         k1<<<grid, block, smem, st>>>(none, b.args, b.prefix, b.ninst, t);

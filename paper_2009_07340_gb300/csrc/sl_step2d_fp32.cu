@@ -25,6 +25,16 @@ cudaError_t launch_step2d_batch_fp32_n9(const Batch2DLaunch &b, cudaStream_t st)
 cudaError_t launch_step2d_fp32_n10(const Step2DArgs &a, cudaStream_t st);
 cudaError_t launch_step2d_batch_fp32_n10(const Batch2DLaunch &b, cudaStream_t st);
 
+cudaError_t preload_step2d_fp32_n2();
+cudaError_t preload_step2d_fp32_n3();
+cudaError_t preload_step2d_fp32_n4();
+cudaError_t preload_step2d_fp32_n5();
+cudaError_t preload_step2d_fp32_n6();
+cudaError_t preload_step2d_fp32_n7();
+cudaError_t preload_step2d_fp32_n8();
+cudaError_t preload_step2d_fp32_n9();
+cudaError_t preload_step2d_fp32_n10();
+
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
 {
     switch (N) {
@@ -39,6 +49,14 @@ cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
     case 10: return launch_step2d_fp32_n10(a, st);
     default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t preload_step2d_fp32()
+{
+    cudaError_t e = cudaSuccess;
+    for (auto f : {preload_step2d_fp32_n2, preload_step2d_fp32_n3, preload_step2d_fp32_n4, preload_step2d_fp32_n5, preload_step2d_fp32_n6, preload_step2d_fp32_n7, preload_step2d_fp32_n8, preload_step2d_fp32_n9, preload_step2d_fp32_n10})
+        if (e == cudaSuccess) e = f();
+    return e;
 }
 
 cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t st)

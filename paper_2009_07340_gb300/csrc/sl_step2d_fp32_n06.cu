@@ -5,4 +5,5 @@
 namespace sl {
 cudaError_t launch_step2d_fp32_n6(const Step2DArgs &a, cudaStream_t st) { return launch_step2d_n<6, float>(a, st); }
 cudaError_t launch_step2d_batch_fp32_n6(const Batch2DLaunch &b, cudaStream_t st) { return launch_step2d_batch_n<6, float>(b, st); }
+cudaError_t preload_step2d_fp32_n6() { return preload_step2d_n<6, float>(); }
 }  // namespace sl

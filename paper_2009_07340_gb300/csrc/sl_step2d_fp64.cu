@@ -16,6 +16,17 @@ cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st)
     default: return cudaErrorNotSupported;
     }
 }
+cudaError_t preload_step2d_fp64()
+{
+    cudaError_t e = preload_step2d_n<2, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<3, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<4, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<5, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<6, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<7, double>();
+    if (e == cudaSuccess) e = preload_step2d_n<8, double>();
+    return e;
+}
 cudaError_t launch_step2d_batch_fp64(const Batch2DLaunch &b, int N, cudaStream_t st)
 {
     switch (N) {

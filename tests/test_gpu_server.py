@@ -81,3 +81,8 @@ def test_budget_admission_and_rejection(sl, orc):
         assert srv.poll(tb, want=False)[0] == -3  # SL_ERR_OOM
         for t in tickets:
             assert srv.poll(t, want=False)[0] == 2
+
+
+def test_preload(sl):
+    sl.sl_preload()  # idempotent: every kernel is already prepared by the solvers above
+    sl.sl_preload(0)
