@@ -107,6 +107,13 @@ typedef struct {
     long long sample0;       /* global index of sample 0 (Philox counter word 1): a run */
                              /* split over GPUs gives each a disjoint sample range;    */
                              /* sample0 + M <= 2^32                                     */
+    long long launch_chunk;  /* 2D: at most this many element-sample pairs per kernel  */
+                             /* launch (0 = one launch per phase; results unchanged). */
+                             /* Bounds how long one launch holds the GPU, so that     */
+                             /* other streams' kernels start between launches.  When */
+                             /* set, sl_step keeps at most 2 launches queued on the  */
+                             /* stream, waiting on the host for earlier ones, and so */
+                             /* returns only when the last launches are queued       */
 } sl_options;
 
 typedef struct sl_ctx sl_ctx; /* opaque; owns all of its device memory */

@@ -49,7 +49,8 @@ class sl_mesh(C.Structure):
 
 class sl_options(C.Structure):
     _fields_ = [("seed", C.c_ulonglong), ("precision", C.c_int), ("strict_dt", C.c_int),
-                ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong)]
+                ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong),
+                ("launch_chunk", C.c_longlong)]
 
 
 class sl_instance(C.Structure):
@@ -159,7 +160,7 @@ def _f64p(a):
 
 # ------------------------------------------------------------------ C-named wrappers
 def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, device=-1, phi0_nodal=None,
-            sample0=0):
+            sample0=0, launch_chunk=0):
     """Returns an opaque context handle (int).  `stream` is a cudaStream_t
     handle (int) or None."""
     mesh = _mesh(pb)
@@ -180,6 +181,7 @@ def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, devi
     opt.stream = C.c_void_p(stream) if stream else None
     opt.device = device
     opt.sample0 = int(sample0)
+    opt.launch_chunk = int(launch_chunk)
     h = C.c_void_p()
     _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
                          C.byref(opt)), "sl_init")
@@ -451,14 +453,15 @@ class Solver:
     """One solver context for a problem dict (see ``sl_inputs``)."""
 
     def __init__(self, pb, precision="fp64", seed=None, stream=None, strict_dt=False, phi0_nodal=None,
-                 sample0=0):
+                 sample0=0, launch_chunk=0):
         self.pb = pb
         self.E = int(np.prod(pb["K"]))
         self.n = pb["N"] ** pb["dim"]
         self.V = self.E * self.n
         self.M = pb["M"]
         self.dim = pb["dim"]
-        self.ctx = sl_init(pb, precision, seed, stream, strict_dt, phi0_nodal=phi0_nodal, sample0=sample0)
+        self.ctx = sl_init(pb, precision, seed, stream, strict_dt, phi0_nodal=phi0_nodal, sample0=sample0,
+                           launch_chunk=launch_chunk)
 
     def step(self, dt=None, steps=None):
         sl_step(self.ctx, self.pb["dt"] if dt is None else dt, self.pb["steps"] if steps is None else steps)

@@ -167,6 +167,8 @@ void sl_free(sl_ctx *c)
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
+    for (cudaEvent_t ev : c->throttle.ev)
+        if (ev) cudaEventDestroy(ev);
     sl::ctx_free(c, c->xi);
     sl::ctx_free(c, c->nodeU);
     sl::ctx_free(c, c->nodeB);
@@ -219,6 +221,14 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     c->seed = opt ? opt->seed : 0ull;
     c->sample0 = opt ? opt->sample0 : 0ll;
     c->strict_dt = opt ? opt->strict_dt : 0;
+    c->launch_chunk = opt && opt->launch_chunk > 0 ? opt->launch_chunk : 0;
+    if (c->launch_chunk > 0)
+        for (cudaEvent_t &ev : c->throttle.ev)
+            if (cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                sl_free(c);
+                return SL_ERR_CUDA;
+            }
     c->st = opt ? static_cast<cudaStream_t>(opt->stream) : nullptr;
     c->M = M;
     sl::Mesh &m = c->m;
@@ -412,6 +422,9 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.Q = c->Q;
             a.faces = c->faces2d;
             a.err = c->err;
+            a.chunk = c->launch_chunk;
+            a.g0 = a.g1 = 0;
+            a.throttle = c->launch_chunk > 0 ? &c->throttle : nullptr;
             e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
         }
         if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;

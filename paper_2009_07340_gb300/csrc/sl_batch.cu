@@ -155,6 +155,9 @@ sl::Step2DArgs args2d(const sl_ctx *c, double dt, int steps)
     a.Q = c->Q;
     a.faces = c->faces2d;
     a.err = c->err;
+    a.chunk = 0;  // the batched launch covers all instances' groups
+    a.g0 = a.g1 = 0;
+    a.throttle = nullptr;
     return a;
 }
 

@@ -49,6 +49,24 @@ struct Step1DArgs {
 };
 
 // Kernel arguments of the 2D step.
+// Bounded queue depth for chunked launches: before launch number i, the host
+// waits (blocking-sync event) until launch i - kDepth has completed, so a
+// stream never holds more than kDepth queued launches.  CUDA multiplexes
+// streams onto a few in-order hardware queues; a stream with a deep queue of
+// dependent launches would block every other stream that shares its queue.
+struct LaunchThrottle {
+    static constexpr int kDepth = 2;
+    cudaEvent_t ev[kDepth] = {};
+    long long n = 0;  // launches recorded
+    cudaError_t before() const { return n >= kDepth ? cudaEventSynchronize(ev[n % kDepth]) : cudaSuccess; }
+    cudaError_t after(cudaStream_t st)
+    {
+        const cudaError_t e = cudaEventRecord(ev[n % kDepth], st);
+        ++n;
+        return e;
+    }
+};
+
 struct Step2DArgs {
     int Kx, Ky, M;
     int nsteps;
@@ -63,6 +81,9 @@ struct Step2DArgs {
     void *Q;               // [M][E][n]
     void *faces;           // scratch [M][E][4N] face values of the advected interpolant
     int *err;
+    long long chunk;       // element-sample groups per launch (0: all in one launch)
+    long long g0, g1;      // groups [g0, g1) of this launch (set by the launcher)
+    LaunchThrottle *throttle;  // host object; with chunk > 0: bounded queue depth (may be null)
 };
 
 // Persistent batched 1D launch: `ninst` instances of one order N, work
@@ -163,6 +184,8 @@ struct sl_ctx {
     int mom_chunk = 64;
     int *err = nullptr;
     void *faces2d = nullptr;  // 2D face-value scratch
+    long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
+    sl::LaunchThrottle throttle;  // events created when launch_chunk > 0
     // 1D launch geometry
     int S = 1, C = 1, T = 1;
     // kernel timing hook

@@ -30,6 +30,8 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "sl_internal.cuh"
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
     }
     __syncthreads();
 
-    const long long ggid = (long long)blockIdx.x * G::GPC + grp;
+    const long long ggid = (BATCH ? 0 : a0.g0) + (long long)blockIdx.x * G::GPC + grp;
     int inst = 0;
     if constexpr (BATCH) {
         int lo = 0, hi = ninst - 1;  // last instance with prefix[i] <= ggid
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
     const Step2DArgs a = BATCH ? args[inst] : a0;
     const long long gid = BATCH ? ggid - prefix[inst] : ggid;
     const int E = a.Kx * a.Ky;
-    const bool group_active = BATCH ? ggid < prefix[ninst] : gid < (long long)E * a.M;
+    const bool group_active = BATCH ? ggid < prefix[ninst] : gid < a.g1;
     const int s = group_active ? int(gid / E) : 0;
     const int e = group_active ? int(gid % E) : 0;
     const int kx = e % a.Kx, ky = e / a.Kx;
@@ -394,13 +396,31 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
     using G = Geo2D<N, R>;
     const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
     const long long groups = (long long)a.Kx * a.Ky * a.M;
-    const unsigned grid = unsigned((groups + G::GPC - 1) / G::GPC);
+    // a launch covers at most `chunk` groups (a multiple of the groups per CTA)
+    const long long chunk =
+        a.chunk > 0 ? std::min(groups, (a.chunk + G::GPC - 1) / G::GPC * G::GPC) : groups;
     const unsigned block = unsigned(G::GPC * G::GS);
     auto k1 = sl2d_step_kernel<N, R, 1, false>;
     auto k2 = sl2d_step_kernel<N, R, 2, false>;
+    Step2DArgs b = a;
+    LaunchThrottle *th = a.chunk > 0 ? a.throttle : nullptr;
     for (int t = 0; t < a.nsteps; ++t) {
-        k1<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
-        k2<<<grid, block, smem, st>>>(a, nullptr, nullptr, 0, t);
+        for (int phase = 1; phase <= 2; ++phase)  // every group's faces before any remap
+            for (long long g0 = 0; g0 < groups; g0 += chunk) {
+                if (th) {
+                    const cudaError_t e = th->before();
+                    if (e != cudaSuccess) return e;
+                }
+                b.g0 = g0;
+                b.g1 = std::min(groups, g0 + chunk);
+                const unsigned grid = unsigned((b.g1 - g0 + G::GPC - 1) / G::GPC);
+                if (phase == 1) k1<<<grid, block, smem, st>>>(b, nullptr, nullptr, 0, t);
+                else k2<<<grid, block, smem, st>>>(b, nullptr, nullptr, 0, t);
+                if (th) {
+                    const cudaError_t e = th->after(st);
+                    if (e != cudaSuccess) return e;
+                }
+            }
     }
     return cudaGetLastError();
 }

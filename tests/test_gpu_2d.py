@@ -123,3 +123,18 @@ def test_order_limits(sl, orc):
     with pytest.raises(sl.SLError) as e:
         sl.Solver(pb, "fp32")
     assert e.value.code == -8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_launch_chunk_is_bitwise_neutral(sl, orc, precision):
+    # a step split into launches of 7 element-sample groups (ragged: 4*4*5 = 80
+    # groups, at most 2 launches queued) equals the step in one launch per
+    # phase, bit for bit
+    pb = _rot(K=(4, 4), N=5, M=5, steps=6, orc=orc)
+    with sl.Solver(pb, precision) as s:
+        s.step()
+        whole = s.samples()
+    for chunk in (7, 80, 1000):
+        with sl.Solver(pb, precision, launch_chunk=chunk) as s:
+            s.step()
+            assert np.array_equal(s.samples(), whole), chunk
