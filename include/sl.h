@@ -244,23 +244,31 @@ void sl_batch_free(sl_batch *b);
 /* Serving: solves submitted over time, run with continuous batching.  A     */
 /* scheduler thread admits queued requests in arrival order, backfilling,    */
 /* while their device footprint fits in `budget_bytes` beside the running    */
-/* ones (a request larger than the budget is rejected with SL_ERR_OOM);      */
-/* each running request advances by slices of up to `slice_steps` steps on   */
-/* its own stream as soon as its previous slice is done (requests' kernels   */
-/* overlap on the GPU); requests with more than ~2e9 operations per step run */
-/* one step per slice on a low-priority stream, lighter ones on a high-     */
-/* priority stream; finished requests complete (moments, memory released    */
-/* through the stream-ordered allocator, latency = completion minus         */
-/* submission).  Each result equals the request run alone.                  */
+/* ones (a request larger than the budget is rejected with SL_ERR_OOM).     */
+/* Light requests (up to ~2e9 operations per step) run on high-priority     */
+/* streams by slices of up to `slice_steps` steps; a host callback at the    */
+/* end of each slice hands the request back to the scheduler for the next   */
+/* one, so requests' kernels overlap on the GPU.  A heavy request runs on a  */
+/* low-priority stream, driven by a worker thread of its own one step at a  */
+/* time in short launches with a bounded queue (sl_options.launch_chunk),   */
+/* so that it never holds the GPU or a hardware queue for long.  Solvers    */
+/* are created and completed (moments, memory released, latency =          */
+/* completion minus submission) on worker threads.  Each result equals the  */
+/* request run alone.                                                       */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    size_t budget_bytes; /* device memory the running requests may hold        */
+    size_t budget_bytes; /* device memory the running requests may hold;      */
+                         /* reserved when the server is created (SL_ERR_OOM  */
+                         /* if the device cannot hold it)                    */
     int slice_steps;     /* steps per request per scheduling round (>= 1)      */
     int heavy_slots;     /* heavy requests (estimated >= ~1 ms of GPU work per  */
-                         /* step) running at once; 0 = no limit.  Light ones    */
-                         /* are limited by the budget alone                    */
+                         /* step) running at once, each driven by a worker     */
+                         /* thread of its own; 0 = admitted by the budget      */
+                         /* alone and served by 2 threads in arrival order     */
     int precision;       /* SL_FP64, SL_MIXED or SL_FP32                        */
     int device;          /* CUDA device ordinal; -1 = current                   */
+    int max_active;      /* requests admitted and not finished at once; 0 = no  */
+                         /* limit (the budget and heavy_slots alone)            */
 } sl_server_config;
 
 typedef struct {
@@ -270,6 +278,9 @@ typedef struct {
     double p50_s, p99_s, mean_s;        /* latency of completed requests             */
     double span_s;                      /* first submission to last completion       */
     double esu_per_s;                   /* esu_completed / span_s                    */
+    long long slices;                   /* light-request slices launched              */
+    double sched_busy_s;                /* scheduler thread time spent working        */
+    double launch_s, launch_max_s;      /* time in slice launches: total, longest     */
 } sl_server_stats;
 
 typedef struct sl_server sl_server;
@@ -280,6 +291,18 @@ int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long
 /* state: 0 queued, 1 running, 2 done, < 0 error code.  When done, copies   */
 /* the moments (host [elements][N^dim]; either may be NULL) and latency.    */
 int sl_server_poll(sl_server *s, long long ticket, int *state, double *mean, double *m2, double *latency_s);
+/* Phases of a completed request, in seconds (out[9]):                     */
+/*   out[0] queued: submission to admission (budget, slots)                */
+/*   out[1] admission to the start of solver creation (worker wait)       */
+/*   out[2] solver creation (stream, sl_init)                              */
+/*   out[3] running: solver ready to its last slice seen complete          */
+/*   out[4] last slice seen complete to the start of completion (wait)    */
+/*   out[5] moments (computed and copied to the host)                      */
+/*   out[6] release (solver, stream)                                       */
+/*   out[7] total latency (the sum of out[0..6])                           */
+/*   out[8] the longest slice turnaround (launch to completion seen)       */
+/* SL_ERR_STATE if the request is not done.                                */
+int sl_server_timing(sl_server *s, long long ticket, double *out);
 /* Waits until nothing is queued or running (SL_ERR_TIMEOUT after timeout_s). */
 int sl_server_wait_idle(sl_server *s, double timeout_s);
 int sl_server_stats_get(sl_server *s, sl_server_stats *out);

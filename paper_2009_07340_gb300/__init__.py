@@ -61,13 +61,14 @@ class sl_instance(C.Structure):
 
 class sl_server_config(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("slice_steps", C.c_int), ("heavy_slots", C.c_int),
-                ("precision", C.c_int), ("device", C.c_int)]
+                ("precision", C.c_int), ("device", C.c_int), ("max_active", C.c_int)]
 
 
 class sl_server_stats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in ("submitted", "completed", "rejected", "failed", "running", "queued",
                                              "esu_completed", "memory_in_use", "memory_peak")] + \
-               [(n, C.c_double) for n in ("p50_s", "p99_s", "mean_s", "span_s", "esu_per_s")]
+               [(n, C.c_double) for n in ("p50_s", "p99_s", "mean_s", "span_s", "esu_per_s")] + \
+               [("slices", C.c_longlong)] + [(n, C.c_double) for n in ("sched_busy_s", "launch_s", "launch_max_s")]
 
 
 _lib = None
@@ -111,6 +112,7 @@ def lib():
         L.sl_server_submit.argtypes = [vp, C.POINTER(sl_instance), C.c_int, C.POINTER(C.c_longlong)]
         L.sl_server_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), _dp, _dp, _dp]
         L.sl_server_wait_idle.argtypes = [vp, C.c_double]
+        L.sl_server_timing.argtypes = [vp, C.c_longlong, _dp]
         L.sl_server_stats_get.argtypes = [vp, C.POINTER(sl_server_stats)]
         L.sl_server_free.argtypes = [vp]
         L.sl_server_free.restype = None
@@ -392,11 +394,12 @@ class Batch:
 class Server:
     """Continuous-batching server of drift-diffusion solves (see include/sl.h)."""
 
-    def __init__(self, budget_bytes, slice_steps=10, heavy_slots=2, precision="fp32", device=-1):
+    def __init__(self, budget_bytes, slice_steps=10, heavy_slots=2, precision="fp32", device=-1, max_active=0):
         cfg = sl_server_config()
         cfg.budget_bytes = int(budget_bytes)
         cfg.slice_steps = int(slice_steps)
         cfg.heavy_slots = int(heavy_slots)
+        cfg.max_active = int(max_active)
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.device = device
         h = C.c_void_p()
@@ -421,6 +424,14 @@ class Server:
         _check(lib().sl_server_poll(C.c_void_p(self.h), int(ticket), C.byref(st), _f64p(mean) if want else None,
                                     _f64p(m2) if want else None, C.byref(lat)), "sl_server_poll")
         return st.value, (mean, m2, lat.value) if st.value == 2 else None
+
+    def timing(self, ticket):
+        """Phases of a completed request in seconds: (queued, creation wait,
+        creation, running, completion wait, moments, release, total, longest
+        slice)."""
+        out = np.zeros(9)
+        _check(lib().sl_server_timing(C.c_void_p(self.h), int(ticket), _f64p(out)), "sl_server_timing")
+        return tuple(float(v) for v in out)
 
     def wait_idle(self, timeout_s=600.0):
         _check(lib().sl_server_wait_idle(C.c_void_p(self.h), float(timeout_s)), "sl_server_wait_idle")

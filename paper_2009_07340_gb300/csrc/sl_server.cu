@@ -1,28 +1,37 @@
 // sl_server.cu -- a serving loop for drift-diffusion solves that arrive over
 // time (host runtime around the solver; no kernels of its own).
 //
-// Requests (an sl_instance plus a step count) are queued on submission.  A
-// scheduler thread runs rounds:
-//   1. admission: queued requests are admitted in arrival order while their
-//      device footprint (state, face buffer, Wiener scratch, moment
-//      partials, node tables) fits in the memory budget next to the running
-//      ones; a request larger than the whole budget is rejected;
-//      (backfilling: a request that does not fit yet does not block later,
-//      smaller ones); at most `heavy_slots` heavy requests run at once, so
-//      that heavy work is served nearly in order instead of being shared
-//      among many requests that would then all finish late;
-//   2. a running request whose previous slice has completed (CUDA event)
-//      gets its next slice on its stream, so requests' kernels overlap on the
-//      GPU and a slow request never holds back the others.  Requests are
-//      light or heavy by their estimated work per step; light ones run on
-//      high-priority streams (the CTA scheduler serves them first when SMs
-//      free up), heavy ones on low-priority streams with one step per slice;
-//   3. a request that has taken all its steps computes its moments, releases
-//      its memory and records its latency (completion minus submission);
-//      new arrivals are admitted between slices (continuous batching).
-// Creating a request's solver and completing it (moments, release) can wait
-// on the GPU, so they run on a small worker pool; the scheduler thread only
-// admits, polls events and launches slices, none of which blocks.
+// Requests (an sl_instance plus a step count) are queued on submission and
+// go through these phases:
+//   1. admission (scheduler thread): queued requests are admitted in arrival
+//      order while their device footprint (state, face buffer, Wiener
+//      scratch, moment partials, node tables) fits in the memory budget next
+//      to the running ones; a request larger than the whole budget is
+//      rejected.  Backfilling: a request that does not fit yet does not block
+//      later, smaller ones.  At most `heavy_slots` heavy requests run at once,
+//      so that heavy work is served nearly in order instead of being shared
+//      among many requests that would then all finish late, and at most
+//      `max_active` requests are admitted and unfinished at once;
+//   2. creation (worker thread): the request's stream and solver (sl_init);
+//   3. steps.  Requests are light or heavy by their estimated work per step.
+//      A light request runs on a high-priority stream (the CTA scheduler
+//      serves it first when SMs free up) in slices of `slice_steps` steps
+//      launched by the scheduler thread; each slice ends with a host callback
+//      that hands the request back to the scheduler, which sleeps until a
+//      callback, an arrival, a created solver or a completion wakes it (no
+//      polling).  A heavy request runs on a low-priority stream and is driven
+//      from creation to completion by one heavy worker thread, one step at a
+//      time, its 2D kernels split into launches of bounded length with at
+//      most two queued (sl_options.launch_chunk): CUDA multiplexes streams
+//      onto a few in-order hardware queues, and a long or deeply queued heavy
+//      stream would block every light stream sharing its queue;
+//   4. completion (worker thread): moments, release of the solver, latency.
+// New arrivals are admitted while others run (continuous batching).
+// Creation and completion wait on the GPU, so they run on worker threads;
+// light and heavy requests have separate workers, so that no thread that
+// light requests depend on ever waits on heavy work.  The budget is reserved
+// in the library's memory pool when the server is created, so requests'
+// allocations never take new memory from the driver.
 // Each request is an independent solver context, so its result is the same
 // as that of the request run alone (bitwise in SL_FP64).
 #include <cuda_runtime.h>
@@ -47,6 +56,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
     long long ticket = 0;
+    sl_server *owner = nullptr;
     sl_instance spec;
     int steps = 0, done_steps = 0;
     double dt = 0.0;  // resolved time step
@@ -56,14 +66,17 @@ struct Request {
     bool heavy = false;
     sl_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;  // the request's own stream
-    cudaEvent_t ev = nullptr;  // completion of the slice in flight
-    int inflight = 0;          // steps of the slice in flight
-    Clock::time_point t_submit, t_done;
+    int inflight = 0;           // steps of the slice in flight
+    // submitted, admitted, creation started, solver created, last slice seen
+    // complete, completion started, moments copied, done
+    Clock::time_point t_submit, t_admit, t_create, t_ready, t_ran, t_finish, t_moments, t_done;
+    Clock::time_point t_launch;  // launch of the slice in flight
+    double slice_max = 0.0;      // longest slice turnaround (launch to completion seen)
     std::vector<double> mean, m2;
     long long esu = 0;
 };
 
-size_t footprint_of(const sl_instance &s, int slice, int precision)
+size_t footprint_of(const sl_instance &s, int slice)
 {
     const int dim = s.mesh.dim;
     const long long E = (long long)s.mesh.K[0] * (dim == 2 ? s.mesh.K[1] : 1);
@@ -75,7 +88,6 @@ size_t footprint_of(const sl_instance &s, int slice, int precision)
     b += size_t(std::max(slice, 1)) * s.M * dim * sizeof(double);       // Wiener scratch
     b += size_t((s.M + 63) / 64) * V * 2 * sizeof(double);             // moment partials
     b += size_t(V) * (dim + 4) * sizeof(double) + size_t(2 * E * s.N) * 2 * sizeof(double);  // tables
-    (void)precision;
     return b + (1u << 20);
 }
 
@@ -88,40 +100,65 @@ double work_of(const sl_instance &s)
     return E * s.M * (s.mesh.dim == 2 ? n * n * n : n * n);
 }
 
-constexpr double kHeavyWork = 2e9;  // about a millisecond of GPU time per step
+constexpr double kHeavyWork = 2e9;    // about a millisecond of GPU time per step
+constexpr double kLaunchWork = 2e10;  // arithmetic per heavy 2D launch: a few milliseconds
+constexpr int kLightWorkers = 8;
+
+// Element-sample groups per launch for a heavy request (2D: n^3 per group).
+long long launch_chunk_of(const sl_instance &s)
+{
+    if (s.mesh.dim != 2) return 0;
+    const double n = double(s.N) * s.N;
+    return std::max<long long>(4096, (long long)(kLaunchWork / (n * n * n)));
+}
 
 }  // namespace
 
 struct sl_server {
     sl_server_config cfg;
     int prio_light = 0, prio_heavy = 0;  // stream priorities
-    std::mutex mu;
-    std::condition_variable cv;
-    std::deque<long long> queue;
+    int device = 0;
+    std::mutex mu;               // guards everything below
+    std::condition_variable cv;  // wakes the scheduler
+    bool wake = false;           // something for the scheduler to do
+    bool admit_changed = false;  // an arrival or a release: run admission
+    std::deque<long long> queue;  // submitted, not admitted
     std::map<long long, Request> req;
-    std::vector<long long> running;
-    int heavy_running = 0;  // heavy requests admitted and not yet finished
+    std::vector<long long> ready;   // light solvers created, first slice not launched
+    std::vector<long long> landed;  // light slices completed (host callbacks)
+    long long active = 0;           // admitted and not finished
+    int heavy_running = 0;          // heavy requests among them
     size_t used = 0, peak = 0;
     long long next_ticket = 1;
     bool stop = false;
-    std::thread worker;
     std::vector<double> latencies;
     long long esu_done = 0, submitted = 0, completed = 0, rejected = 0, failed = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
-    int device = 0;
-    // worker pool for solver creation and completion
+    // workers for creation, heavy requests and completion: lane 0 light, lane 1 heavy
     std::vector<std::thread> pool;
-    std::deque<std::function<void()>> tasks;
-    std::condition_variable task_cv;
-    std::vector<long long> ready;  // created solvers waiting to join the running set
-    int outstanding = 0;           // tasks queued or running
+    std::deque<std::function<void()>> tasks[2];
+    std::condition_variable task_cv[2];
+    int outstanding = 0;  // tasks queued or running
+    std::thread scheduler;
+    // scheduler accounting
+    long long slices = 0;
+    double busy_s = 0.0, launch_s = 0.0, launch_max_s = 0.0;
 };
 
 namespace {
 
+void wake_scheduler(sl_server *s, bool admit)  // caller holds s->mu
+{
+    s->wake = true;
+    if (admit) s->admit_changed = true;
+    s->cv.notify_one();
+}
+
+// Completion: moments to the host, release, bookkeeping (a worker thread).
 void finish(sl_server *s, Request &r, int rc)
 {
+    r.t_finish = Clock::now();
     if (r.ctx) {
         if (rc == SL_OK) {
             const size_t V = size_t(r.ctx->m.E) * r.ctx->m.n;
@@ -129,12 +166,11 @@ void finish(sl_server *s, Request &r, int rc)
             r.m2.resize(V);
             rc = sl_moments(r.ctx, r.mean.data(), r.m2.data());
         }
+        r.t_moments = Clock::now();
         sl_free(r.ctx);
         r.ctx = nullptr;
-    }
-    if (r.ev) {
-        cudaEventDestroy(r.ev);
-        r.ev = nullptr;
+    } else {
+        r.t_moments = r.t_finish;
     }
     if (r.st) {
         cudaStreamDestroy(r.st);  // pending frees on it still complete
@@ -143,6 +179,7 @@ void finish(sl_server *s, Request &r, int rc)
     r.t_done = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     s->used -= r.footprint;
+    s->active--;
     if (r.heavy) s->heavy_running--;
     if (rc == SL_OK) {
         r.state = 2;
@@ -154,42 +191,43 @@ void finish(sl_server *s, Request &r, int rc)
         r.state = rc;
         s->failed++;
     }
+    wake_scheduler(s, true);
 }
 
-void post(sl_server *s, std::function<void()> f)
+void post(sl_server *s, bool heavy, std::function<void()> f)
 {
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->tasks.push_back(std::move(f));
+        s->tasks[heavy].push_back(std::move(f));
         s->outstanding++;
     }
-    s->task_cv.notify_one();
+    s->task_cv[heavy].notify_one();
 }
 
-void pool_worker(sl_server *s)
+void pool_worker(sl_server *s, int lane)
 {
     cudaSetDevice(s->device);
     for (;;) {
         std::function<void()> f;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->task_cv.wait(lk, [&] { return s->stop || !s->tasks.empty(); });
-            if (s->tasks.empty()) return;
-            f = std::move(s->tasks.front());
-            s->tasks.pop_front();
+            s->task_cv[lane].wait(lk, [&] { return s->stop || !s->tasks[lane].empty(); });
+            if (s->tasks[lane].empty()) return;
+            f = std::move(s->tasks[lane].front());
+            s->tasks[lane].pop_front();
         }
         f();
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->outstanding--;
-        }
-        s->cv.notify_one();
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->outstanding--;
     }
 }
 
-// Creates the request's stream and solver (on a pool thread).
+// Creation: the request's stream and solver (a worker thread).  A light
+// request then joins the scheduler's ready list; a heavy one returns to
+// run_heavy.
 void create_request(sl_server *s, Request *r)
 {
+    r->t_create = Clock::now();
     int rc = SL_OK;
     if (cudaStreamCreateWithPriority(&r->st, cudaStreamNonBlocking, r->heavy ? s->prio_heavy : s->prio_light) !=
         cudaSuccess) {
@@ -203,12 +241,14 @@ void create_request(sl_server *s, Request *r)
         o.precision = s->cfg.precision;
         o.device = -1;
         o.stream = r->st;
+        o.launch_chunk = r->heavy ? launch_chunk_of(r->spec) : 0;
         rc = sl_init(&r->ctx, &r->spec.mesh, r->spec.N, r->spec.M, &r->spec.drift, &r->spec.diffusion, &r->spec.phi0,
                      &o);
         if (rc != SL_OK) r->ctx = nullptr;
     }
-    if (rc == SL_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) rc = SL_ERR_CUDA;
+    r->t_ready = Clock::now();
     if (rc != SL_OK) {
+        r->t_ran = r->t_ready;
         finish(s, *r, rc);
         return;
     }
@@ -216,95 +256,140 @@ void create_request(sl_server *s, Request *r)
     r->esu = (long long)r->ctx->m.E * r->spec.M * r->steps;
     std::lock_guard<std::mutex> lk(s->mu);
     r->state = 1;
+    if (r->heavy) return;
     s->ready.push_back(r->ticket);
+    wake_scheduler(s, false);
+}
+
+// A heavy request from creation to completion (a heavy worker thread): one
+// step at a time, waiting on a blocking-sync event between steps.
+void run_heavy(sl_server *s, Request *r)
+{
+    create_request(s, r);
+    if (!r->ctx) return;  // creation failed and completed the request
+    int rc = SL_OK;
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        rc = SL_ERR_CUDA;
+    }
+    while (rc == SL_OK && r->done_steps < r->steps) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->stop) break;
+        }
+        r->t_launch = Clock::now();
+        rc = sl_step(r->ctx, r->dt, 1);
+        if (rc == SL_OK && (cudaEventRecord(ev, r->st) != cudaSuccess || cudaEventSynchronize(ev) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = SL_ERR_CUDA;
+        }
+        r->t_ran = Clock::now();
+        r->slice_max = std::max(r->slice_max, std::chrono::duration<double>(r->t_ran - r->t_launch).count());
+        if (rc == SL_OK) r->done_steps++;
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (r->done_steps == r->steps || rc != SL_OK) finish(s, *r, rc);  // else stopping: sl_server_free releases it
+}
+
+// Host callback at the end of a light slice: hands the request back to the
+// scheduler.  Runs on a CUDA runtime thread and makes no CUDA call.
+void CUDART_CB slice_landed(void *p)
+{
+    Request *r = static_cast<Request *>(p);
+    sl_server *s = r->owner;
+    const Clock::time_point now = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->t_ran = now;
+    s->landed.push_back(r->ticket);
+    wake_scheduler(s, false);
+}
+
+// Launches a light request's next slice, or hands it to completion (scheduler).
+void next_slice(sl_server *s, Request *r)
+{
+    int rc = SL_OK;
+    if (r->done_steps < r->steps) {
+        const int n = std::min(s->cfg.slice_steps, r->steps - r->done_steps);
+        r->t_launch = Clock::now();
+        rc = sl_step(r->ctx, r->dt, n);
+        if (rc == SL_OK && cudaLaunchHostFunc(r->st, slice_landed, r) != cudaSuccess) {
+            cudaGetLastError();
+            rc = SL_ERR_CUDA;
+        }
+        const double took = std::chrono::duration<double>(Clock::now() - r->t_launch).count();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->slices++;
+            s->launch_s += took;
+            s->launch_max_s = std::max(s->launch_max_s, took);
+        }
+        if (rc == SL_OK) {
+            r->inflight = n;
+            return;
+        }
+        r->t_ran = Clock::now();
+    }
+    post(s, false, [s, r, rc] { finish(s, *r, rc); });
 }
 
 void scheduler(sl_server *s)
 {
     cudaSetDevice(s->device);
     for (;;) {
-        std::vector<long long> admit;
+        std::vector<Request *> admit, start, landed;
+        Clock::time_point t_busy;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->running.empty() || !s->ready.empty() ||
-                                        s->outstanding > 0; });
+            s->cv.wait(lk, [&] { return s->stop || s->wake; });
             if (s->stop) return;  // sl_server_free drains and releases
-            // admission in arrival order with backfilling
-            for (auto it = s->queue.begin(); it != s->queue.end();) {
-                Request &r = s->req[*it];
-                if (r.footprint > s->cfg.budget_bytes) {
-                    r.state = SL_ERR_OOM;
-                    s->rejected++;
+            s->wake = false;
+            t_busy = Clock::now();
+            if (s->admit_changed) {
+                s->admit_changed = false;
+                // admission in arrival order with backfilling
+                for (auto it = s->queue.begin(); it != s->queue.end();) {
+                    if (s->cfg.max_active > 0 && s->active >= s->cfg.max_active) break;
+                    Request &r = s->req[*it];
+                    if (r.footprint > s->cfg.budget_bytes) {
+                        r.state = SL_ERR_OOM;
+                        s->rejected++;
+                        it = s->queue.erase(it);
+                        continue;
+                    }
+                    if (s->used + r.footprint > s->cfg.budget_bytes ||
+                        (r.heavy && s->cfg.heavy_slots > 0 && s->heavy_running >= s->cfg.heavy_slots)) {
+                        ++it;
+                        continue;
+                    }
+                    s->used += r.footprint;
+                    s->peak = std::max(s->peak, s->used);
+                    s->active++;
+                    if (r.heavy) s->heavy_running++;
+                    r.t_admit = Clock::now();
+                    admit.push_back(&r);
                     it = s->queue.erase(it);
-                    continue;
                 }
-                if (s->used + r.footprint > s->cfg.budget_bytes ||
-                    (r.heavy && s->cfg.heavy_slots > 0 && s->heavy_running >= s->cfg.heavy_slots)) {
-                    ++it;
-                    continue;
-                }
-                s->used += r.footprint;
-                if (r.heavy) s->heavy_running++;
-                s->peak = std::max(s->peak, s->used);
-                admit.push_back(r.ticket);
-                it = s->queue.erase(it);
             }
-        }
-        // admission: solvers are created on the pool
-        for (long long t : admit) {
-            Request *r;
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                r = &s->req[t];
-            }
-            post(s, [s, r] { create_request(s, r); });
-        }
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (long long t : s->ready) s->running.push_back(t);
+            for (long long t : s->ready) start.push_back(&s->req[t]);
             s->ready.clear();
+            for (long long t : s->landed) landed.push_back(&s->req[t]);
+            s->landed.clear();
         }
-        // slices: every running request whose previous slice has completed
-        std::vector<Request *> run;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (long long t : s->running) run.push_back(&s->req[t]);
+        for (Request *r : admit) {
+            if (r->heavy) post(s, true, [s, r] { run_heavy(s, r); });
+            else post(s, false, [s, r] { create_request(s, r); });
         }
-        bool progressed = !admit.empty();
-        std::vector<long long> still;
-        for (Request *r : run) {
-            int rc = SL_OK;
-            if (r->inflight) {
-                const cudaError_t q = cudaEventQuery(r->ev);
-                if (q == cudaErrorNotReady) {
-                    still.push_back(r->ticket);
-                    continue;
-                }
-                if (q != cudaSuccess) rc = SL_ERR_CUDA;
-                r->done_steps += r->inflight;
-                r->inflight = 0;
-                progressed = true;
-            }
-            if (rc == SL_OK && r->done_steps < r->steps) {
-                const int n = std::min(r->heavy ? 1 : s->cfg.slice_steps, r->steps - r->done_steps);
-                rc = sl_step(r->ctx, r->dt, n);
-                if (rc == SL_OK && cudaEventRecord(r->ev, r->st) != cudaSuccess)
-                    rc = SL_ERR_CUDA;
-                if (rc == SL_OK) {
-                    r->inflight = n;
-                    progressed = true;
-                    still.push_back(r->ticket);
-                    continue;
-                }
-            }
-            post(s, [s, r, rc] { finish(s, *r, rc); });
-            progressed = true;
+        for (Request *r : start) next_slice(s, r);
+        for (Request *r : landed) {
+            r->done_steps += r->inflight;
+            r->inflight = 0;
+            r->slice_max = std::max(r->slice_max, std::chrono::duration<double>(r->t_ran - r->t_launch).count());
+            next_slice(s, r);
         }
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->running.swap(still);
-        }
-        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
+        const double busy = std::chrono::duration<double>(Clock::now() - t_busy).count();
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->busy_s += busy;
     }
 }
 
@@ -314,24 +399,47 @@ extern "C" {
 
 int sl_server_create(sl_server **out, const sl_server_config *cfg)
 {
-    if (!out || !cfg || cfg->slice_steps < 1 || cfg->budget_bytes == 0 || cfg->heavy_slots < 0)
+    if (!out || !cfg || cfg->slice_steps < 1 || cfg->budget_bytes == 0 || cfg->heavy_slots < 0 || cfg->max_active < 0)
         return SL_ERR_ARG;
     if (cfg->precision != SL_FP64 && cfg->precision != SL_MIXED && cfg->precision != SL_FP32) return SL_ERR_ARG;
     *out = nullptr;
+    if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_CUDA;
+    }
+    if (sl::ensure_loaded() != cudaSuccess) {  // no module load while requests run
+        cudaGetLastError();
+        return SL_ERR_CUDA;
+    }
+    int device = 0;
+    cudaGetDevice(&device);
+    {
+        // reserve the budget: allocate it from the pool once and free it; the
+        // pool keeps the memory mapped for the requests
+        cudaStream_t st = nullptr;
+        void *p = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, cfg->budget_bytes, sl::device_pool(device), st);
+        if (e == cudaSuccess) e = cudaFreeAsync(p, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (st) cudaStreamDestroy(st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? SL_ERR_OOM : SL_ERR_CUDA;
+        }
+    }
     sl_server *s = new (std::nothrow) sl_server;
     if (!s) return SL_ERR_OOM;
     s->cfg = *cfg;
-    if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) {
-        delete s;
-        return SL_ERR_CUDA;
-    }
-    cudaGetDevice(&s->device);
+    s->device = device;
     int prio_least = 0, prio_greatest = 0;
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     s->prio_light = prio_greatest;
     s->prio_heavy = prio_least;
-    s->worker = std::thread(scheduler, s);
-    for (int i = 0; i < 4; ++i) s->pool.emplace_back(pool_worker, s);
+    s->scheduler = std::thread(scheduler, s);
+    const int heavy_workers = cfg->heavy_slots > 0 ? cfg->heavy_slots : 2;
+    for (int i = 0; i < kLightWorkers + heavy_workers; ++i)
+        s->pool.emplace_back(pool_worker, s, int(i >= kLightWorkers));
     *out = s;
     return SL_OK;
 }
@@ -342,25 +450,24 @@ int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long
         (spec->dt_rule > 0 && spec->dt > 1.0))
         return SL_ERR_ARG;
     Request r;
+    r.owner = s;
     r.spec = *spec;
     r.steps = steps;
-    r.footprint = footprint_of(*spec, s->cfg.slice_steps, s->cfg.precision);
+    r.footprint = footprint_of(*spec, s->cfg.slice_steps);
     r.work = work_of(*spec);
     r.heavy = r.work > kHeavyWork;
     r.t_submit = Clock::now();
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        r.ticket = s->next_ticket++;
-        if (!s->any) {
-            s->t_first = r.t_submit;
-            s->any = true;
-        }
-        s->submitted++;
-        s->queue.push_back(r.ticket);
-        if (ticket) *ticket = r.ticket;
-        s->req.emplace(r.ticket, std::move(r));
+    std::lock_guard<std::mutex> lk(s->mu);
+    r.ticket = s->next_ticket++;
+    if (!s->any) {
+        s->t_first = r.t_submit;
+        s->any = true;
     }
-    s->cv.notify_one();
+    s->submitted++;
+    s->queue.push_back(r.ticket);
+    if (ticket) *ticket = r.ticket;
+    s->req.emplace(r.ticket, std::move(r));
+    wake_scheduler(s, true);
     return SL_OK;
 }
 
@@ -380,6 +487,27 @@ int sl_server_poll(sl_server *s, long long ticket, int *state, double *mean, dou
     return SL_OK;
 }
 
+int sl_server_timing(sl_server *s, long long ticket, double *out)
+{
+    if (!s || !out) return SL_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->req.find(ticket);
+    if (it == s->req.end()) return SL_ERR_ARG;
+    const Request &r = it->second;
+    if (r.state != 2) return SL_ERR_STATE;
+    auto sec = [](Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+    out[0] = sec(r.t_submit, r.t_admit);
+    out[1] = sec(r.t_admit, r.t_create);
+    out[2] = sec(r.t_create, r.t_ready);
+    out[3] = sec(r.t_ready, r.t_ran);
+    out[4] = sec(r.t_ran, r.t_finish);
+    out[5] = sec(r.t_finish, r.t_moments);
+    out[6] = sec(r.t_moments, r.t_done);
+    out[7] = sec(r.t_submit, r.t_done);
+    out[8] = r.slice_max;
+    return SL_OK;
+}
+
 int sl_server_wait_idle(sl_server *s, double timeout_s)
 {
     if (!s) return SL_ERR_ARG;
@@ -387,7 +515,7 @@ int sl_server_wait_idle(sl_server *s, double timeout_s)
     for (;;) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            if (s->queue.empty() && s->running.empty() && s->ready.empty() && s->outstanding == 0) return SL_OK;
+            if (s->queue.empty() && s->active == 0 && s->outstanding == 0) return SL_OK;
         }
         if (Clock::now() > deadline) return SL_ERR_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::milliseconds(1));
@@ -403,11 +531,15 @@ int sl_server_stats_get(sl_server *s, sl_server_stats *out)
     out->completed = s->completed;
     out->rejected = s->rejected;
     out->failed = s->failed;
-    out->running = (long long)(s->running.size() + s->ready.size()) + s->outstanding;
+    out->running = s->active;
     out->queued = (long long)s->queue.size();
     out->esu_completed = s->esu_done;
     out->memory_in_use = (long long)s->used;
     out->memory_peak = (long long)s->peak;
+    out->slices = s->slices;
+    out->sched_busy_s = s->busy_s;
+    out->launch_s = s->launch_s;
+    out->launch_max_s = s->launch_max_s;
     std::vector<double> l = s->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -436,19 +568,21 @@ void sl_server_free(sl_server *s)
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         s->queue.clear();
-        s->tasks.clear();  // queued creations and completions are dropped
+        s->tasks[0].clear();  // queued creations, heavy runs and completions are dropped
+        s->tasks[1].clear();
     }
     s->cv.notify_all();
-    s->task_cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    s->task_cv[0].notify_all();
+    s->task_cv[1].notify_all();
+    if (s->scheduler.joinable()) s->scheduler.join();
     for (std::thread &t : s->pool) t.join();  // a task already running finishes
-    // slices in flight complete; the requests they belong to are abandoned
+    // slices in flight (and their host callbacks) complete; their requests are abandoned
     for (auto &kv : s->req) {
         if (kv.second.st) cudaStreamSynchronize(kv.second.st);
         if (kv.second.ctx) sl_free(kv.second.ctx);
-        if (kv.second.ev) cudaEventDestroy(kv.second.ev);
         if (kv.second.st) cudaStreamDestroy(kv.second.st);
     }
+    if (cudaMemPool_t pool = sl::device_pool(s->device)) cudaMemPoolTrimTo(pool, 0);  // give back what is unused
     delete s;
 }
 

@@ -60,6 +60,10 @@ def test_mix_equals_alone(sl, orc, precision):
             assert state == 2
             mean, m2, lat = res
             assert lat > 0
+            ph = srv.timing(t)  # queued, creation wait, creation, running, completion wait, moments, release
+            assert min(ph[:7]) >= 0 and ph[7] == pytest.approx(lat, rel=1e-12)
+            assert sum(ph[:7]) == pytest.approx(ph[7], rel=1e-9)
+            assert 0 < ph[8] <= ph[3]  # the longest slice lies within the running phase
             with sl.Solver(pb, precision) as s:
                 s.step()
                 am, aq = s.moments()
@@ -81,6 +85,25 @@ def test_budget_admission_and_rejection(sl, orc):
         assert srv.poll(tb, want=False)[0] == -3  # SL_ERR_OOM
         for t in tickets:
             assert srv.poll(t, want=False)[0] == 2
+
+
+def test_max_active_one_at_a_time(sl, orc):
+    reqs = _requests(orc)[:4]
+    with sl.Server(budget_bytes=1 << 30, slice_steps=4, max_active=1, precision="fp64") as srv:
+        tickets = [srv.submit(pb) for pb in reqs]
+        srv.wait_idle(300)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["slices"] >= len(reqs)
+        assert st["launch_s"] <= st["sched_busy_s"] and st["launch_max_s"] > 0
+        for t, pb in zip(tickets, reqs):
+            state, (mean, _, _) = srv.poll(t)
+            assert state == 2
+            with sl.Solver(pb, "fp64") as s:
+                s.step()
+                am, _ = s.moments()
+            assert np.array_equal(mean, am.ravel())
+        # one request at a time: every later request waited in the queue
+        assert all(srv.timing(t)[0] > 0 for t in tickets[1:])
 
 
 def test_preload(sl):
