@@ -167,12 +167,17 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
         const double dWy = a.dW[((long long)t * a.M + s) * 2 + 1];
         const double ux = a.nodeU[(long long)e * n + c], uy = a.nodeU[V + (long long)e * n + c];
         const double b = a.nodeB[(long long)e * n + c];
-        const R dx = R(4.0 * (ux * a.dt + b * dWx) / a.hx);
-        const R dy = R(4.0 * (uy * a.dt + b * dWy) / a.hy);
+        // explicit unfused products: the compiler may not contract these
+        // differently in the batched and single kernels
+        const R dx = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx))) / a.hx);
+        const R dy = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy))) / a.hy);
         const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
         R dq = qh - ch;
         if constexpr (kPair) dq += ql - cl;
-        ph = dq - gam * qh;
+        if constexpr (kPair)
+            ph = dq - __fmul_rn(gam, qh);
+        else
+            ph = dq - __dmul_rn(gam, qh);
         // Gauss-node basis at the particle: h_i'(x) = lam_i' prod_{m != i'} (x - zeta_m),
         // x - zeta_m = Z[ip][m] + dx (node difference plus displacement)
         R pre = R(1);
