@@ -103,14 +103,37 @@ def _clock_summary(proc, device_index):
     return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist():
+def _dist(backend="nccl"):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws
     return None, 0, 1
+
+
+def shard_sample0(rank, per_rank):
+    """Rank r owns the global samples [r * per_rank, (r + 1) * per_rank): the
+    Philox counter is keyed on the global sample index, so the ranks together
+    draw exactly the increments of one run over all samples."""
+    return rank * per_rank
+
+
+def max_over_ranks(x, dist, device="cpu"):
+    """The largest of every rank's x (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank / seconds
 
 
 def _cpu_baseline(seconds=15.0):
@@ -332,7 +355,7 @@ def run_native(args):
 
     build.build()
     stream = torch.cuda.Stream()
-    sample0 = rank * M_SAMPLES
+    sample0 = shard_sample0(rank, M_SAMPLES)
     prec = args.precision
     orders = ORDERS if not args.quick else (16,)
     sl_steps = SL_STEPS if not args.quick else 50
@@ -386,13 +409,9 @@ def run_native(args):
         kern_ms += ms_
         kern_launches += n_
         flops += flops_per_esu_1d(N) * K_ELEM * M_SAMPLES * sl_steps * args.steps
-    total_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), dist, device="cuda")
     esu_step = len(orders) * K_ELEM * M_SAMPLES * sl_steps
-    value = world * esu_step * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(esu_step * args.steps, world, total_ms * 1e-3)
     # launches per step: per order one Wiener kernel, one step kernel, two moment kernels
     gpu_launches = 4 * len(orders) * args.steps
     for s in solvers.values():
