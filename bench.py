@@ -40,6 +40,13 @@ sys.path.insert(0, ROOT)
 
 import sl_inputs as I  # noqa: E402
 
+# DRAM bytes (read + write) per launch of the FP32 step kernel at config 2,
+# one launch of 1000 steps per order, from one ncu capture of this kernel
+# version (dram__bytes_read.sum + dram__bytes_write.sum); the command and the
+# per-order figures are in profiles/sl1d_step_kernel_config2.md.  Only valid
+# while that kernel is unchanged: set to None when it changes.
+NCU_TRAFFIC_FP32 = {4: 67557120, 8: 111402752, 12: 180743936, 16: 248969728}
+
 METRIC = "element-sample SL updates/sec at stated error vs FP64 oracle; p50/p99 solve latency"
 ORDERS = (4, 8, 12, 16)
 SL_STEPS = 1000
@@ -423,7 +430,10 @@ def run_native(args):
         peak = PEAK_FP32_TFLOPS if fp32_like else PEAK_FP64_TFLOPS
         achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": (float(np.mean([NCU_TRAFFIC_FP32[N] for N in orders]))
+                                if prec == "fp32" and NCU_TRAFFIC_FP32 else None),
+                    "traffic_unit": "bytes per launch (ncu, mean over the orders' launches)",
                     "kernel": "sl1d_step_kernel<N,%s>" % prec,
                     "peak_source": "derived: 152 SM x %s x 2 flop x 2070 MHz" % ("128 FP32 lanes" if fp32_like
                                                                                  else "2 FP64 FMA units"),
