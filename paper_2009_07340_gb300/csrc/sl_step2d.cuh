@@ -52,6 +52,25 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// 16-byte vectors of R for shared-memory rows (every row and sub-array of a
+// group starts on a 16-byte boundary; rows are LD >= n (rounded to 4) long).
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+    static constexpr int W = 4;
+    __device__ static float at(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+    __device__ static float4 make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    static constexpr int W = 2;
+    __device__ static double at(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+    __device__ static double2 make(double a, double b, double, double) { return make_double2(a, b); }
+};
+
 template <int N, typename R>
 struct Geo2D {
     static constexpr int n = N * N;
@@ -60,22 +79,28 @@ struct Geo2D {
     static constexpr int LD = (n + 3) & ~3;                     // row stride (16-byte rows)
     static constexpr int P = n + 4 * N;                         // stacked rows
     // per-group shared memory (elements of R)
-    static constexpr int kRows = P * LD, kRhs = P, kPiv = 2 * (LD + 4), kVec = P, kRes = P;
+    static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
+    static constexpr int kRows = P * LD, kRhs = P4, kPiv = 2 * (LD + 4), kVec = P4, kRes = P4;
     static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
     // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N]
     static constexpr int kTables = N * N + 3 * N;
 };
 
+// FP32 kernels up to N = 8 are held to two CTAs per SM (their shared memory
+// allows it; 128 registers per thread), the rest to one.
 // BATCH = false: one instance (a0), group g = element-sample g.
 // BATCH = true: `ninst` instances of the same N, instance i owning groups
 // [prefix[i], prefix[i+1]) (its E*M element-samples).
 template <int N, typename R, int PHASE, bool BATCH>
-__global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
+__global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::value && N <= 8) ? 2 : 1) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
                                                                     const long long *__restrict__ prefix, int ninst, int t)
 {
     using G = Geo2D<N, R>;
     constexpr int n = G::n, LD = G::LD;
     constexpr int P = PHASE == 1 ? n : G::P;  // rows of the system solved in this phase
+    using VV = Vec16<R>;
+    using VT = typename VV::T;
+    constexpr int VW = VV::W;
     constexpr bool kPair = !std::is_same<R, double>::value;
     using State = typename std::conditional<kPair, float2, double>::type;
 
@@ -205,10 +230,15 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
             suf *= sZ[jp * N + m] + dy;
         }
         // row c of V and its right-hand side
+        // (row c of V: entry q = jj N + ii is hx[ii] hy[jj]; 16-byte stores,
+        // the padding past n is never read)
 #pragma unroll
-        for (int jj = 0; jj < N; ++jj)
+        for (int q = 0; q < n; q += VW) {
+            R v4[4];
 #pragma unroll
-            for (int ii = 0; ii < N; ++ii) Vs[c * LD + jj * N + ii] = hx[ii] * hy[jj];
+            for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? hx[(q + i) % N] * hy[(q + i) / N] : R(0);
+            *reinterpret_cast<VT *>(Vs + c * LD + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+        }
         rhs[c] = ph;
     }
 
@@ -221,7 +251,7 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
             const int side = c / N, f = c % N;
             R *row = Vs + (n + c) * LD;
 #pragma unroll
-            for (int q = 0; q < n; ++q) row[q] = R(0);
+            for (int q = 0; q < n; q += VW) *reinterpret_cast<VT *>(row + q) = VV::make(R(0), R(0), R(0), R(0));
             const double dW = a.dW[((long long)t * a.M + s) * 2 + (side < 2 ? 0 : 1)];
             int e_face;  // element whose low face is this interface
             if (side == 0) e_face = e;
@@ -285,7 +315,12 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
             const R vpc = Vs[p * LD + c];
             const R *rowp = Vs + p * LD;
 #pragma unroll
-            for (int q = 0; q < n; ++q) gr[q] = fma(vpc, rowp[q], gr[q]);
+            for (int q = 0; q < n; q += VW) {
+                const VT v = *reinterpret_cast<const VT *>(rowp + q);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (q + i < n) gr[q + i] = fma(vpc, VV::at(v, i), gr[q + i]);
+            }
             bc = fma(vpc, rhs[p], bc);
         }
     }
@@ -299,7 +334,12 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
         R *pr = piv + (k & 1) * (LD + 4);
         if (c == k) {
 #pragma unroll
-            for (int q = 0; q < n; ++q) pr[q] = gr[q];
+            for (int q = 0; q < n; q += VW) {
+                R v4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
+                *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+            }
             pr[LD] = bc;
             pr[LD + 1] = R(1) / gr[k];
             diag = gr[k];
@@ -309,7 +349,13 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
             const R l = gr[k] * pr[LD + 1];
             // columns < k hold multipliers (eliminated); only q > k change
 #pragma unroll
-            for (int q = k + 1; q < n; ++q) gr[q] = fma(-l, pr[q], gr[q]);
+            for (int q = 0; q < n; q += VW) {
+                if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
+                const VT v = *reinterpret_cast<const VT *>(pr + q);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+            }
             bc = fma(-l, pr[LD], bc);
             gr[k] = l;
         }
@@ -324,27 +370,43 @@ __global__ void __launch_bounds__(kGroupThreads2D) sl2d_step_kernel(const Step2D
         group_sync(bar_id, G::GS);
         if (real) {
             // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
+            R t2[N];
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+            for (int q = 0; q < n; q += VW) {
+                const VT v = *reinterpret_cast<const VT *>(vec + q);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+            }
             R vx = R(0);
 #pragma unroll
-            for (int jj = 0; jj < N; ++jj) {
-                R t2 = R(0);
-#pragma unroll
-                for (int ii = 0; ii < N; ++ii) t2 = fma(hx[ii], vec[jj * N + ii], t2);
-                vx = fma(hy[jj], t2, vx);
-            }
+            for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
             res[c] = rhs[c] - vx;
         }
         if (PHASE == 2 && group_active && c < 4 * N) {
             const R *row = Vs + (n + c) * LD;
             R bx = R(0);
 #pragma unroll
-            for (int q = 0; q < n; ++q) bx = fma(row[q], vec[q], bx);
+            for (int q = 0; q < n; q += VW) {
+                const VT rv = *reinterpret_cast<const VT *>(row + q);
+                const VT xv = *reinterpret_cast<const VT *>(vec + q);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (q + i < n) bx = fma(VV::at(rv, i), VV::at(xv, i), bx);
+            }
             res[n + c] = rhs[n + c] - bx;
         }
         group_sync(bar_id, G::GS);
         R rc = R(0);
         if (real)
-            for (int p = 0; p < P; ++p) rc = fma(Vs[p * LD + c], res[p], rc);
+            for (int p = 0; p < P; p += VW) {
+                const VT rv = *reinterpret_cast<const VT *>(res + p);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (p + i < P) rc = fma(Vs[(p + i) * LD + c], VV::at(rv, i), rc);
+            }
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             R *pr = piv + (k & 1) * (LD + 4);
