@@ -68,3 +68,34 @@ def test_invalid_precision_and_null(sl):
     assert L.sl_step(None, 1e-3, 1) == -1
     assert L.sl_moments(None, None, None) == -1
     L.sl_free(None)  # no-op
+
+
+@pytest.mark.parametrize("bad,precision,code", [
+    (dict(K=(2049,)), "fp64", -8),                          # 1D beyond the largest cluster (8 x 256 elements)
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=9, drift=("const", [0.1, 0.2]),
+          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp64", -8),   # 2D FP64 N > 8
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=11, drift=("const", [0.1, 0.2]),
+          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp32", -8),   # 2D FP32 N > 10
+])
+def test_unsupported_sizes_rejected_before_device(sl, bad, precision, code):
+    pb = I.config1()
+    pb.update(bad)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_init(pb, precision)
+    assert e.value.code == code
+
+
+def test_sample_range_and_batch_server_arguments(sl):
+    with pytest.raises(sl.SLError) as e:  # sample0 + M beyond the 2^32 Philox sample counter
+        sl.sl_init(I.config1(), sample0=(1 << 32) - 10)
+    assert e.value.code == -1
+    L = sl.lib()
+    h = C.c_void_p()
+    assert L.sl_batch_create(C.byref(h), 0, None, None) == -1
+    cfg = sl.sl_server_config()
+    cfg.budget_bytes, cfg.slice_steps, cfg.precision, cfg.device = 1 << 20, 0, 0, -1
+    assert L.sl_server_create(C.byref(h), C.byref(cfg)) == -1  # slice_steps < 1
+    cfg.slice_steps, cfg.max_active = 1, -1
+    assert L.sl_server_create(C.byref(h), C.byref(cfg)) == -1  # negative cap
+    cfg.max_active, cfg.budget_bytes = 0, 0
+    assert L.sl_server_create(C.byref(h), C.byref(cfg)) == -1  # no budget
