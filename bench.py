@@ -228,7 +228,9 @@ def leg_batch(sl, stream):
         pb = I.config2(N=int(rng.integers(4, 17)), M=int(rng.integers(256, 2049)), K=int(rng.integers(64, 1025)))
         pb["seed"] = 7000 + i
         one_d.append(pb)
-    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config5_1d_mix", one_d, 20)):
+    small = I.small_instances_1d()
+    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config5_1d_mix", one_d, 20),
+                             ("small_1d_uneven", small, 20)):
         for pb in pbs:  # half of each instance's particle bound (2D: edge distance)
             pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
         esu = sum(int(np.prod(pb["K"])) * pb["M"] for pb in pbs) * steps
@@ -254,6 +256,8 @@ def leg_batch(sl, stream):
                      "batched": {"value": esu / t_batch, "unit": "ESU/s"},
                      "one_by_one": {"value": esu / t_seq, "unit": "ESU/s"},
                      "speedup": t_seq / t_batch, "tuned_grids": grids, "tune_ms": tune_ms}
+    out["small_1d_uneven"]["what"] = ("256 instances, K ~ U{8..64}, N ~ U{4..8}, M ~ U{16..128}: each alone is "
+                                      "far from filling the GPU, so one-by-one stepping is launch-bound")
     out["note"] = ("config 4 as drawn (512 instances, N up to 12, 100 steps, ~8.8e10 ESU) is not run: 2D N>10 is "
                    "not supported and the 2D path runs at ~1e7 ESU/s at N=8; the first 12 draws with N<=8 are "
                    "timed for one step")

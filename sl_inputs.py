@@ -136,6 +136,21 @@ def batch_instances(count=512, seed=4, steps=100):
     return out
 
 
+def small_instances_1d(count=256, seed=46, steps=20):
+    """Many small uneven 1D instances (the case batching is for): K ~ U{8..64},
+    N ~ U{4..8}, M ~ U{16..128}, the fields of config 2, each its own seed.
+    dt is left as None."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        pb = config2(N=int(rng.integers(4, 9)), M=int(rng.integers(16, 129)), steps=steps,
+                     K=int(rng.integers(8, 65)))
+        pb["seed"] = 9000 + i
+        pb["dt"] = None
+        out.append(pb)
+    return out
+
+
 def serving_requests(rate=200.0, duration=60.0, seed=5, steps=20):
     """Poisson arrivals (mean `rate` per second) over `duration` seconds.  Each
     request is, with probability 1/2, a 2D instance drawn like
