@@ -43,7 +43,7 @@ class _Problem(C.Structure):
                 ("hi", C.c_double * 2), ("N", C.c_int), ("drift_kind", C.c_int),
                 ("drift_p", C.c_double * 8), ("diff_kind", C.c_int), ("diff_p", C.c_double * 8),
                 ("phi0_kind", C.c_int), ("phi0_p", C.c_double * 40), ("seed", C.c_ulonglong),
-                ("dt", C.c_double)]
+                ("dt", C.c_double), ("omega", C.c_double)]
 
 
 def lib():
@@ -75,8 +75,10 @@ def lib():
             L.orc_lagrange_split.argtypes = [C.c_int, dp, dp, C.c_int, C.c_double, C.c_double]
             L.orc_faces_1d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp]
             L.orc_remap_1d_split.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_double, dp]
+            L.orc_remap_1d_split_w.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
             L.orc_faces_2d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp]
             L.orc_remap_2d_split.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
+            L.orc_remap_2d_split_w.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_double, dp]
             L.orc_remap_2d.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_init_state.argtypes = [C.POINTER(_Problem), dp]
             L.orc_get_coeffs.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
@@ -120,6 +122,7 @@ def _problem(pb, dt=None):
         p.phi0_p[i] = v
     p.seed = pb["seed"]
     p.dt = float(dt if dt is not None else (pb["dt"] or 0.0))
+    p.omega = float(pb.get("bc_weight", 1.0) or 1.0)
     return p
 
 
@@ -253,12 +256,16 @@ def faces_1d_split(d, phs):
     return e0.value, e1.value
 
 
-def remap_1d_split(d, phs, gL, gR):
+def remap_1d_split(d, phs, gL, gR, w=None):
+    """1D remap; w weights the boundary rows (None: the unweighted form,
+    inf: hard constraints)."""
     d, phs = _f64(d), _f64(phs)
     N = len(d)
     xi = nodes(N)
     q = np.zeros(N)
-    if lib().orc_remap_1d_split(N, _dp(xi), _dp(d), _dp(phs), gL, gR, _dp(q)) != 0:
+    rc = (lib().orc_remap_1d_split(N, _dp(xi), _dp(d), _dp(phs), gL, gR, _dp(q)) if w is None else
+          lib().orc_remap_1d_split_w(N, _dp(xi), _dp(d), _dp(phs), gL, gR, float(w), _dp(q)))
+    if rc != 0:
         raise np.linalg.LinAlgError("remap failed")
     return q
 
@@ -273,12 +280,14 @@ def faces_2d_split(dx, dy, phs):
     return f
 
 
-def remap_2d_split(dx, dy, phs, g):
+def remap_2d_split(dx, dy, phs, g, w=None):
     dx, dy, phs, g = _f64(dx), _f64(dy), _f64(phs), _f64(g)
     N = int(round(np.sqrt(len(dx))))
     xi = nodes(N)
     q = np.zeros(N * N)
-    if lib().orc_remap_2d_split(N, _dp(xi), _dp(dx), _dp(dy), _dp(phs), _dp(g), _dp(q)) != 0:
+    rc = (lib().orc_remap_2d_split(N, _dp(xi), _dp(dx), _dp(dy), _dp(phs), _dp(g), _dp(q)) if w is None else
+          lib().orc_remap_2d_split_w(N, _dp(xi), _dp(dx), _dp(dy), _dp(phs), _dp(g), float(w), _dp(q)))
+    if rc != 0:
         raise np.linalg.LinAlgError("remap failed")
     return q
 

@@ -369,11 +369,15 @@ void orc_faces_1d_split(int N, const double *xi, const double *d, const double *
     *e1 = b;
 }
 
-/* 1D remap: q = argmin |V q - phi*|^2 + |B q - g|^2 where V[p][i] =         */
+/* 1D remap: q = argmin |V q - phi*|^2 + w^2 |B q - g|^2 where V[p][i] =     */
 /* h_i(xi_p + d_p) (Gauss-node basis at the advected particles) and B holds  */
-/* the rows h_i(0), h_i(1) with the upwinded face values g = (gL, gR).       */
-int orc_remap_1d_split(int N, const double *xi, const double *d, const double *phs, double gL,
-                       double gR, double *q)
+/* the rows h_i(0), h_i(1) with the upwinded face values g = (gL, gR)        */
+/* (Section 5.3 with the boundary rows weighted by w).  w = INFINITY is the  */
+/* hard-constrained problem min |V q - phi*|^2 subject to B q = g, solved    */
+/* through its Lagrange (KKT) conditions V^T V q + B^T lambda = V^T phi*,    */
+/* B q = g, by LU.                                                           */
+int orc_remap_1d_split_w(int N, const double *xi, const double *d, const double *phs, double gL,
+                         double gR, double w, double *q)
 {
     int m = N + 2;
     double *A = (double *)malloc(sizeof(double) * m * N);
@@ -388,10 +392,50 @@ int orc_remap_1d_split(int N, const double *xi, const double *d, const double *p
     }
     rhs[N] = gL;
     rhs[N + 1] = gR;
-    int rc = orc_lstsq(m, N, A, rhs, q);
+    int rc;
+    if (isinf(w)) {
+        int k = N + 2;
+        double *KKT = (double *)calloc((size_t)k * k, sizeof(double));
+        double *b = (double *)calloc((size_t)k, sizeof(double));
+        double *sol = (double *)malloc(sizeof(double) * k);
+        for (int i = 0; i < N; ++i) {
+            for (int j = 0; j < N; ++j) {
+                double s = 0.0;
+                for (int p = 0; p < N; ++p) s += A[p * N + i] * A[p * N + j];
+                KKT[i * k + j] = s;
+            }
+            double s = 0.0;
+            for (int p = 0; p < N; ++p) s += A[p * N + i] * phs[p];
+            b[i] = s;
+            KKT[i * k + N] = A[N * N + i];
+            KKT[i * k + N + 1] = A[(N + 1) * N + i];
+            KKT[N * k + i] = A[N * N + i];
+            KKT[(N + 1) * k + i] = A[(N + 1) * N + i];
+        }
+        b[N] = gL;
+        b[N + 1] = gR;
+        rc = orc_lu_solve(k, KKT, b, sol);
+        for (int i = 0; i < N; ++i) q[i] = sol[i];
+        free(KKT);
+        free(b);
+        free(sol);
+    } else {
+        for (int r = N; r < m; ++r) {
+            for (int i = 0; i < N; ++i) A[r * N + i] *= w;
+            rhs[r] *= w;
+        }
+        rc = orc_lstsq(m, N, A, rhs, q);
+    }
     free(A);
     free(rhs);
     return rc;
+}
+
+/* The unweighted remap (w = 1).                                             */
+int orc_remap_1d_split(int N, const double *xi, const double *d, const double *phs, double gL,
+                       double gR, double *q)
+{
+    return orc_remap_1d_split_w(N, xi, d, phs, gL, gR, 1.0, q);
 }
 
 /* The same with the advected particles given as absolute positions xs.      */
@@ -475,11 +519,12 @@ static int orc_faces_2d_core(int N, const double *xi, const double *bx, const do
     return rc;
 }
 
-/* 2D remap: min |V q - phi*|^2 + |B q - g|^2, B = the 4N face rows at the   */
-/* Gauss-node positions along each face, g ordered as in the face values.    */
+/* 2D remap: min |V q - phi*|^2 + w^2 |B q - g|^2, B = the 4N face rows at  */
+/* the Gauss-node positions along each face, g ordered as in the face values */
+/* (w finite).                                                               */
 static int orc_remap_2d_core(int N, const double *xi, const double *bx, const double *ox,
                              const double *by, const double *oy, const double *phs, const double *g,
-                             double *q)
+                             double w, double *q)
 {
     int n = N * N, m = n + 4 * N;
     double *A = (double *)calloc((size_t)m * n, sizeof(double));
@@ -497,6 +542,10 @@ static int orc_remap_2d_core(int N, const double *xi, const double *bx, const do
             A[(n + 3 * N + i) * n + jj * N + i] = orc_lagrange(N, xi, jj, 1.0);
         }
     for (int f = 0; f < 4 * N; ++f) rhs[n + f] = g[f];
+    for (int r = n; r < m; ++r) {
+        for (int i = 0; i < n; ++i) A[r * n + i] *= w;
+        rhs[r] *= w;
+    }
     int rc = orc_lstsq(m, n, A, rhs, q);
     free(A);
     free(rhs);
@@ -513,7 +562,7 @@ int orc_faces_2d(int N, const double *xi, const double *xs, const double *ys, co
 int orc_remap_2d(int N, const double *xi, const double *xs, const double *ys, const double *phs,
                  const double *g, double *q)
 {
-    return orc_remap_2d_core(N, xi, xs, ORC_ZEROS, ys, ORC_ZEROS, phs, g, q);
+    return orc_remap_2d_core(N, xi, xs, ORC_ZEROS, ys, ORC_ZEROS, phs, g, 1.0, q);
 }
 
 /* Particles at the Gauss nodes plus displacements dx, dy (element units). */
@@ -532,8 +581,8 @@ int orc_faces_2d_split(int N, const double *xi, const double *dx, const double *
     return rc;
 }
 
-int orc_remap_2d_split(int N, const double *xi, const double *dx, const double *dy,
-                       const double *phs, const double *g, double *q)
+int orc_remap_2d_split_w(int N, const double *xi, const double *dx, const double *dy,
+                         const double *phs, const double *g, double w, double *q)
 {
     int n = N * N;
     double *bx = (double *)malloc(sizeof(double) * n), *by = (double *)malloc(sizeof(double) * n);
@@ -541,10 +590,16 @@ int orc_remap_2d_split(int N, const double *xi, const double *dx, const double *
         bx[p] = xi[p % N];
         by[p] = xi[p / N];
     }
-    int rc = orc_remap_2d_core(N, xi, bx, dx, by, dy, phs, g, q);
+    int rc = orc_remap_2d_core(N, xi, bx, dx, by, dy, phs, g, w, q);
     free(bx);
     free(by);
     return rc;
+}
+
+int orc_remap_2d_split(int N, const double *xi, const double *dx, const double *dy,
+                       const double *phs, const double *g, double *q)
+{
+    return orc_remap_2d_split_w(N, xi, dx, dy, phs, g, 1.0, q);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -567,6 +622,7 @@ typedef struct {
     double phi0_p[40];
     unsigned long long seed;
     double dt;
+    double omega; /* weight of the boundary rows of the remap; <= 0 means 1; INFINITY: hard (1D) */
 } orc_problem;
 
 /* Drift u(x) (1D: u[0]; 2D: u[0], u[1]).                                    */
@@ -648,6 +704,7 @@ typedef struct {
     double *div;         /* [E][n] du_j/dx_j at the nodes                     */
     double *afx, *bfx;   /* [Ky][Kx][N(2D) or 1] vertical faces: u_x dt, sqrt(2D) */
     double *afy, *bfy;   /* [Ky][Kx][N] horizontal faces (2D)                 */
+    double omega;        /* boundary-row weight of the remap                  */
 } orc_coeffs;
 
 static void orc_coeffs_free(orc_coeffs *cf)
@@ -690,6 +747,7 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
     cf->E = cf->Kx * cf->Ky;
     cf->hx = (pb->hi[0] - pb->lo[0]) / cf->Kx;
     cf->hy = d == 2 ? (pb->hi[1] - pb->lo[1]) / cf->Ky : 1.0;
+    cf->omega = pb->omega > 0.0 ? pb->omega : 1.0;
     int E = cf->E, n = cf->n;
     cf->xi = (double *)malloc(sizeof(double) * N);
     orc_nodes(N, cf->xi);
@@ -815,7 +873,8 @@ static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, double *Q)
         g[f] = sigma > 0.0 ? e1[(f - 1 + K) % K] : e0[f];
     }
     for (int k = 0; k < K && rc == 0; ++k)
-        rc = orc_remap_1d_split(N, cf->xi, d + k * N, phs + k * N, g[k], g[(k + 1) % K], Q + k * N);
+        rc = orc_remap_1d_split_w(N, cf->xi, d + k * N, phs + k * N, g[k], g[(k + 1) % K], cf->omega,
+                                  Q + k * N);
     free(d);
     free(phs);
     free(e0);
@@ -867,7 +926,7 @@ static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], doub
                 g[2 * N + f] = gh[e * N + f];
                 g[3 * N + f] = gh[eT * N + f];
             }
-            rc = orc_remap_2d_split(N, cf->xi, dx + e * n, dy + e * n, phs + e * n, g, Q + e * n);
+            rc = orc_remap_2d_split_w(N, cf->xi, dx + e * n, dy + e * n, phs + e * n, g, cf->omega, Q + e * n);
         }
     free(dx);
     free(dy);
@@ -934,6 +993,7 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
             const double *state_in, double *state_out, double *sum, double *sumsq)
 {
     if (pb->dim < 1 || pb->dim > 2 || pb->N < 2 || ns < 0 || nsteps < 0 || pb->dt < 0.0) return -1;
+    if (pb->dim == 2 && isinf(pb->omega)) return -1; /* hard constraints: 1D only */
     orc_coeffs cf;
     if (orc_build_coeffs(pb, &cf) != 0) return -1;
     size_t sz = (size_t)cf.E * cf.n;

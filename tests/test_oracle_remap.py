@@ -6,6 +6,8 @@ algebraically equivalent reduced (Woodbury) form of the 1D remap."""
 import numpy as np
 import pytest
 
+import sl_inputs as I
+
 
 def _basis_np(nodes, x):
     """Lagrange basis on `nodes` at points x, [len(x)][len(nodes)], from a
@@ -193,3 +195,80 @@ def test_small_displacement_keeps_precision(orc):
     assert abs(e0 - want0) < 1e-13 and abs(e1 - want1) < 1e-13
     # and the shift itself is resolved to 1e-7 relative
     assert abs((e0 - poly(0.0)) / (-1e-6 * dpoly(0.0)) - 1) < 1e-6
+
+
+# ---------------------------------------------------------------- boundary-row weight w
+# (Section 5.3's least squares with the face rows weighted by w; w = inf is the
+# hard-constrained problem, min |V q - phi*| subject to B q = g)
+
+@pytest.mark.parametrize("N", [3, 6, 9])
+@pytest.mark.parametrize("w", [0.5, 3.0])
+def test_1d_weighted_remap_brute_force(orc, N, w):
+    rng = np.random.default_rng(60 + N)
+    for _ in range(5):
+        xi, xs = _advected(orc, N, rng, 0.4)
+        phs = rng.normal(size=N)
+        gL, gR = rng.normal(size=2)
+        A = np.vstack([_basis_np(xi, xs), w * _basis_np(xi, [0.0, 1.0])])
+        ref = np.linalg.lstsq(A, np.concatenate([phs, [w * gL, w * gR]]), rcond=None)[0]
+        q = orc.remap_1d_split(xs - xi, phs, gL, gR, w=w)
+        assert np.allclose(q, ref, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("N", [3, 6, 9, 12])
+def test_1d_hard_constraints(orc, N):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(70 + N)
+    for _ in range(5):
+        xi, xs = _advected(orc, N, rng, 0.4)
+        phs = rng.normal(size=N)
+        g = rng.normal(size=2)
+        V, B = _basis_np(xi, xs), _basis_np(xi, [0.0, 1.0])
+        q = orc.remap_1d_split(xs - xi, phs, g[0], g[1], w=np.inf)
+        # the constraints hold exactly (to rounding)
+        assert np.allclose(B @ q, g, rtol=0, atol=1e-11)
+        # null-space solution of the equality-constrained least squares
+        qp = np.linalg.lstsq(B, g, rcond=None)[0]
+        Z = scipy_linalg.null_space(B)
+        y = np.linalg.lstsq(V @ Z, phs - V @ qp, rcond=None)[0]
+        assert np.allclose(q, qp + Z @ y, rtol=1e-9, atol=1e-9)
+        # and it is the limit of large weights
+        q_big = orc.remap_1d_split(xs - xi, phs, g[0], g[1], w=1e5)
+        assert np.abs(q_big - q).max() <= 1e-7 * max(1.0, np.abs(q).max())
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+@pytest.mark.parametrize("w", [0.5, 2.0, np.inf])
+def test_1d_reduced_form_with_weight(orc, N, w):
+    # q = H*(phi* - E^T mu), mu = (I / w^2 + E E^T)^{-1}(E phi* - g) (zero
+    # diagonal for w = inf) equals the weighted / constrained remap
+    rng = np.random.default_rng(80 + N)
+    xi, xs = _advected(orc, N, rng, 0.4)
+    phs = 1.0 + 0.1 * rng.normal(size=N)
+    g = np.array(orc.faces_1d(xs, phs)) + 1e-3 * rng.normal(size=2)
+    Hs, E = _basis_np(xs, xi), _basis_np(xs, [0.0, 1.0])
+    mu = np.linalg.solve(np.eye(2) / w ** 2 + E @ E.T, E @ phs - g)
+    q = orc.remap_1d_split(xs - xi, phs, g[0], g[1], w=w)
+    assert np.allclose(q, Hs @ (phs - E.T @ mu), rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+def test_2d_weighted_remap_brute_force(orc, N):
+    rng = np.random.default_rng(90 + N)
+    w = 2.5
+    xi, xs, ys = _advected_2d(orc, N, rng)
+    X, Y = np.meshgrid(xi, xi)
+    phs = rng.normal(size=N * N)
+    g = rng.normal(size=4 * N)
+    A = np.vstack([_V2(xi, xs, ys), w * _B2(xi)])
+    ref = np.linalg.lstsq(A, np.concatenate([phs, w * g]), rcond=None)[0]
+    q = orc.remap_2d_split(xs - X.ravel(), ys - Y.ravel(), phs, g, w=w)
+    assert np.allclose(q, ref, rtol=1e-9, atol=1e-9)
+
+
+def test_hard_constraints_are_1d_only(orc):
+    pb = I.problem(2, (2, 2), (0.0, 0.0), (1.0, 1.0), 3, 2, 1, 1e-4, 1, ("const", [0.1, 0.2]),
+                   ("const", [0.01]), ("gauss", [1.0, 0.2, 0.5, 0.5]))
+    pb["bc_weight"] = np.inf
+    with pytest.raises(Exception):
+        orc.run(pb, ns=2)
