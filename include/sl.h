@@ -107,6 +107,11 @@ typedef struct {
     long long sample0;       /* global index of sample 0 (Philox counter word 1): a run */
                              /* split over GPUs gives each a disjoint sample range;    */
                              /* sample0 + M <= 2^32                                     */
+    double bc_weight;        /* weight w of the boundary rows of the remap,           */
+                             /* min |V q - phi*|^2 + w^2 |B q - g|^2 (Section 5.3);   */
+                             /* <= 0 means 1; INFINITY: the face values are hard     */
+                             /* constraints, B q = g (1D only; SL_ERR_UNSUPPORTED in */
+                             /* 2D); NaN: SL_ERR_ARG                                 */
     long long launch_chunk;  /* 2D: at most this many element-sample pairs per kernel  */
                              /* launch (0 = one launch per phase; results unchanged). */
                              /* Bounds how long one launch holds the GPU, so that     */
@@ -212,6 +217,7 @@ typedef struct {
                               /* sl_dt_max; 2: fraction of sl_dt_edge       */
     int dt_rule;
     unsigned long long seed;  /* this instance's Philox key                 */
+    double bc_weight;         /* as sl_options.bc_weight                     */
 } sl_instance;
 
 typedef struct sl_batch sl_batch; /* opaque; owns its instances' device memory */

@@ -50,13 +50,13 @@ class sl_mesh(C.Structure):
 class sl_options(C.Structure):
     _fields_ = [("seed", C.c_ulonglong), ("precision", C.c_int), ("strict_dt", C.c_int),
                 ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong),
-                ("launch_chunk", C.c_longlong)]
+                ("bc_weight", C.c_double), ("launch_chunk", C.c_longlong)]
 
 
 class sl_instance(C.Structure):
     _fields_ = [("mesh", sl_mesh), ("N", C.c_int), ("M", C.c_int), ("drift", sl_field),
                 ("diffusion", sl_field), ("phi0", sl_field), ("dt", C.c_double), ("dt_rule", C.c_int),
-                ("seed", C.c_ulonglong)]
+                ("seed", C.c_ulonglong), ("bc_weight", C.c_double)]
 
 
 class sl_server_config(C.Structure):
@@ -184,6 +184,7 @@ def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, devi
     opt.device = device
     opt.sample0 = int(sample0)
     opt.launch_chunk = int(launch_chunk)
+    opt.bc_weight = float(pb.get("bc_weight", 0.0) or 0.0)
     h = C.c_void_p()
     _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
                          C.byref(opt)), "sl_init")
@@ -291,6 +292,7 @@ def _instance(pb, dt=None, seed=None):
         inst.dt_rule = 0
         inst.dt = float(d)
     inst.seed = int(pb["seed"] if seed is None else seed)
+    inst.bc_weight = float(pb.get("bc_weight", 0.0) or 0.0)
     return inst
 
 

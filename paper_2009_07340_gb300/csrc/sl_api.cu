@@ -208,6 +208,9 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (dim == 1 && mesh->K[0] > sl::kMaxThreads1D * sl::kMaxCluster1D) return SL_ERR_UNSUPPORTED;
     if (dim == 2 && N > (precision == SL_FP64 ? 8 : 10)) return SL_ERR_UNSUPPORTED;
     if (opt && (opt->sample0 < 0 || opt->sample0 + M > (1ll << 32))) return SL_ERR_ARG;
+    const double bc_w = opt && opt->bc_weight > 0.0 ? opt->bc_weight : 1.0;
+    if (opt && std::isnan(opt->bc_weight)) return SL_ERR_ARG;
+    if (dim == 2 && std::isinf(bc_w)) return SL_ERR_UNSUPPORTED;  // hard constraints: 1D only
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
     if (sl::ensure_loaded() != cudaSuccess) {
@@ -222,6 +225,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     c->sample0 = opt ? opt->sample0 : 0ll;
     c->strict_dt = opt ? opt->strict_dt : 0;
     c->launch_chunk = opt && opt->launch_chunk > 0 ? opt->launch_chunk : 0;
+    c->bc_weight = bc_w;
+    c->inv_w2 = std::isinf(bc_w) ? 0.0 : 1.0 / (bc_w * bc_w);
     if (c->launch_chunk > 0)
         for (cudaEvent_t &ev : c->throttle.ev)
             if (cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
@@ -388,6 +393,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.nsteps = n;
             a.dt = dt;
             a.h = m.h[0];
+            a.inv_w2 = c->inv_w2;
             a.xi = c->xi;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
@@ -424,6 +430,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.err = c->err;
             a.chunk = c->launch_chunk;
             a.g0 = a.g1 = 0;
+            a.w = c->bc_weight;
             a.throttle = c->launch_chunk > 0 ? &c->throttle : nullptr;
             e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
         }

@@ -123,6 +123,7 @@ sl::Step1DArgs args1d(const sl_ctx *c, double dt, int steps)
     a.nsteps = steps;
     a.dt = dt;
     a.h = c->m.h[0];
+    a.inv_w2 = c->inv_w2;
     a.xi = c->xi;
     a.nodeU = c->nodeU;
     a.nodeB = c->nodeB;
@@ -155,6 +156,7 @@ sl::Step2DArgs args2d(const sl_ctx *c, double dt, int steps)
     a.Q = c->Q;
     a.faces = c->faces2d;
     a.err = c->err;
+    a.w = c->bc_weight;
     a.chunk = 0;  // the batched launch covers all instances' groups
     a.g0 = a.g1 = 0;
     a.throttle = nullptr;
@@ -317,6 +319,7 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
         sl_options oi = o;
         oi.seed = s.seed;
         oi.sample0 = 0;
+        if (s.bc_weight != 0.0) oi.bc_weight = s.bc_weight;
         sl_ctx *c = nullptr;
         const int rc = sl_init(&c, &s.mesh, s.N, s.M, &s.drift, &s.diffusion, &s.phi0, &oi);
         if (rc != SL_OK) {

@@ -37,6 +37,7 @@ struct Step1DArgs {
     int T;            // thread slots per sample per CTA (>= elements per CTA)
     int nsteps;
     double dt, h;
+    double inv_w2;         // 1 / w^2 of the boundary rows (0: hard constraints)
     const double *xi;      // [N] reference nodes on [0,1]
     const double *nodeU;   // [K][N] drift at the nodes
     const double *nodeB;   // [K][N] sqrt(2 D) at the nodes
@@ -81,6 +82,7 @@ struct Step2DArgs {
     void *Q;               // [M][E][n]
     void *faces;           // scratch [M][E][4N] face values of the advected interpolant
     int *err;
+    double w;              // weight of the face rows (1 unless the caller set one)
     long long chunk;       // element-sample groups per launch (0: all in one launch)
     long long g0, g1;      // groups [g0, g1) of this launch (set by the launcher)
     LaunchThrottle *throttle;  // host object; with chunk > 0: bounded queue depth (may be null)
@@ -185,6 +187,8 @@ struct sl_ctx {
     int *err = nullptr;
     void *faces2d = nullptr;  // 2D face-value scratch
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
+    double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
+    double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)
     sl::LaunchThrottle throttle;  // events created when launch_chunk > 0
     // 1D launch geometry
     int S = 1, C = 1, T = 1;

@@ -239,6 +239,7 @@ void create_request(sl_server *s, Request *r)
         sl_options o = {};
         o.seed = r->spec.seed;
         o.precision = s->cfg.precision;
+        o.bc_weight = r->spec.bc_weight;
         o.device = -1;
         o.stream = r->st;
         o.launch_chunk = r->heavy ? launch_chunk_of(r->spec) : 0;

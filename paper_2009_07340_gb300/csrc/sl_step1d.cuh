@@ -364,7 +364,8 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
                 g01 = fma(E0[j], E1[j], g01);
                 g11 = fma(E1[j], E1[j], g11);
             }
-            const Fac G00 = Fac(1) + Fac(g00), G01 = Fac(g01), G11 = Fac(1) + Fac(g11);
+            // I / w^2 + E E^T (w = 1 unless the caller weights the boundary rows)
+            const Fac G00 = Fac(a.inv_w2) + Fac(g00), G01 = Fac(g01), G11 = Fac(a.inv_w2) + Fac(g11);
             Fac r0, r1;  // jumps E phi* - g
             if constexpr (kPair) {
                 r0 = Fac((f0.x - gL.x) + (f0.y - gL.y));

@@ -256,7 +256,8 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
                 gd = fma2(E[j], E[j], gd);
                 g01 = fmaf(E[j].x, E[j].y, g01);
             }
-            const Fac G00 = Fac(1) + Fac(gd.x), G01 = Fac(g01), G11 = Fac(1) + Fac(gd.y);
+            // I / w^2 + E E^T (w = 1 unless the caller weights the boundary rows)
+            const Fac G00 = Fac(a.inv_w2) + Fac(gd.x), G01 = Fac(g01), G11 = Fac(a.inv_w2) + Fac(gd.y);
             const Fac r0 = Fac((f0.x - gL.x) + (f0.y - gL.y));
             const Fac r1 = Fac((f1.x - gR.x) + (f1.y - gR.y));
             const Fac det = G00 * G11 - G01 * G01;

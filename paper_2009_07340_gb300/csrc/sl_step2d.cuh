@@ -288,19 +288,21 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
                 gr = (gv.x - ch) + (gv.y - cl);
             else
                 gr = gv - ch;
-            rhs[n + c] = gr;
+            // the face rows and values carry the boundary weight w (1 by default)
+            const R w = R(a.w);
+            rhs[n + c] = w * gr;
             if (side == 0)
 #pragma unroll
-                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = sh0[ii];
+                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh0[ii];
             else if (side == 1)
 #pragma unroll
-                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = sh1[ii];
+                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh1[ii];
             else if (side == 2)
 #pragma unroll
-                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = sh0[jj];
+                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh0[jj];
             else
 #pragma unroll
-                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = sh1[jj];
+                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh1[jj];
         }
     }
     group_sync(bar_id, G::GS);
