@@ -189,3 +189,74 @@ def test_amplification_at_the_bound(orc):
     g_half = growth(0.5, 400)
     assert g_bound > 30.0
     assert g_half < 10.0
+
+
+def _advected_fourier_reference(p, T, nm=256, dt=2e-6):
+    """Fourier pseudo-spectral solution of phi_t + (u phi)_x = 0 on periodic
+    [0, 2], u = 1 + 0.5 sin(pi x), phi0 the Fourier series of parameters p,
+    classical RK4 in time; returns an evaluator at arbitrary points."""
+    L = 2.0
+    x = np.arange(nm) * L / nm
+    k = 2 * np.pi * np.fft.fftfreq(nm, d=L / nm)
+    u = 1.0 + 0.5 * np.sin(np.pi * x)
+
+    def rhs(f):
+        return -np.real(np.fft.ifft(1j * k * np.fft.fft(u * f)))
+
+    f = p[0] + 0 * x
+    for m in range(int(p[2])):
+        f = f + p[3 + 2 * m] * np.cos((m + 1) * p[1] * np.pi * x) + p[4 + 2 * m] * np.sin((m + 1) * p[1] * np.pi * x)
+    for _ in range(int(round(T / dt))):
+        k1 = rhs(f)
+        k2 = rhs(f + 0.5 * dt * k1)
+        k3 = rhs(f + 0.5 * dt * k2)
+        k4 = rhs(f + dt * k3)
+        f = f + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    c = np.fft.fft(f) / nm
+    return lambda xs: np.real(np.exp(1j * np.outer(xs, k)) @ c)
+
+
+def test_deterministic_advection_against_spectral_reference(orc):
+    # Without diffusion every sample is the same deterministic semi-Lagrangian
+    # solution of the mean equation phi_t + (u phi)_x = 0 (Eq. advection_phi
+    # keeps the divergence form).  Against an independent pseudo-spectral
+    # solution, the error falls exponentially in N, then sits on the
+    # first-order time error of the explicit particle advance (Eq. def_dx).
+    p = I.fourier_phi0(2)[1]
+    T = 0.02
+    ref = _advected_fourier_reference(p, T)
+
+    def err(N, dt):
+        pb = I.problem(1, (8,), (0.0,), (2.0,), N, 1, int(round(T / dt)), dt, 2, ("sin", [1.0, 0.5, 1.0]),
+                       ("const", [0.0]), ("fourier", p))
+        x, _ = orc.node_coords(pb)
+        return float(np.abs(orc.run(pb, ns=1)["sum"].ravel() - ref(x.ravel())).max())
+
+    e = {N: err(N, 2e-5) for N in (4, 6, 8, 10)}
+    for N in (4, 6, 8):
+        assert e[N + 2] < e[N] / 4, e
+    # N = 12: the space error is below the time error, which halves with dt
+    e12 = [err(12, dt) for dt in (4e-5, 2e-5, 1e-5)]
+    assert e12[1] <= 5e-6
+    assert 1.7 < e12[0] / e12[1] < 2.3 and 1.7 < e12[1] / e12[2] < 2.3, e12
+
+
+def test_rotation_without_diffusion_against_exact_rotation(orc):
+    # Solid-body rotation (divergence-free) of the Gaussian blob of config 3
+    # with D = 0: the exact solution is the blob rotated by omega t; the error
+    # falls exponentially in N at fixed dt.
+    om, T = 2 * np.pi, 80 * 2e-4
+
+    def exact(x, y):
+        a = -om * T
+        X = 0.5 + np.cos(a) * (x - 0.5) - np.sin(a) * (y - 0.5)
+        Y = 0.5 + np.sin(a) * (x - 0.5) + np.cos(a) * (y - 0.5)
+        return np.exp(-((X - 0.5) ** 2 + (Y - 0.75) ** 2) / (2 * 0.05 ** 2))
+
+    e = {}
+    for N in (4, 6, 8):
+        pb = I.problem(2, (6, 6), (0.0, 0.0), (1.0, 1.0), N, 1, 80, 2e-4, 3, ("rotation", [om, 0.5, 0.5]),
+                       ("const", [0.0]), ("gauss", [1.0, 0.05, 0.5, 0.75]))
+        x, y = orc.node_coords(pb)
+        e[N] = float(np.abs(orc.run(pb, ns=1)["sum"] - exact(x, y)).max())
+    assert e[6] < e[4] / 4 and e[8] < e[6] / 4 and e[8] <= 1e-3, e
