@@ -43,7 +43,7 @@ class _Problem(C.Structure):
                 ("hi", C.c_double * 2), ("N", C.c_int), ("drift_kind", C.c_int),
                 ("drift_p", C.c_double * 8), ("diff_kind", C.c_int), ("diff_p", C.c_double * 8),
                 ("phi0_kind", C.c_int), ("phi0_p", C.c_double * 40), ("seed", C.c_ulonglong),
-                ("dt", C.c_double), ("omega", C.c_double)]
+                ("dt", C.c_double), ("omega", C.c_double), ("periodic", C.c_int), ("reseed_every", C.c_int)]
 
 
 def lib():
@@ -83,7 +83,7 @@ def lib():
             L.orc_init_state.argtypes = [C.POINTER(_Problem), dp]
             L.orc_get_coeffs.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
             L.orc_run.argtypes = [C.POINTER(_Problem), C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
-                                  dp, dp, dp, dp]
+                                  dp, dp, dp, dp, dp]
             L.orc_dt_max.restype = C.c_double
             L.orc_dt_max.argtypes = [C.POINTER(_Problem)]
             L.orc_dt_edge.restype = C.c_double
@@ -123,6 +123,8 @@ def _problem(pb, dt=None):
     p.seed = pb["seed"]
     p.dt = float(dt if dt is not None else (pb["dt"] or 0.0))
     p.omega = float(pb.get("bc_weight", 1.0) or 1.0)
+    p.periodic = 1 if pb.get("periodic", True) else 0
+    p.reseed_every = int(pb.get("reseed_every", 0) or 0)
     return p
 
 
@@ -323,8 +325,10 @@ def dt_edge(pb):
 
 
 def run(pb, nsteps=None, step0=0, s0=0, ns=None, nthreads=1, state_in=None,
-        want_states=False, want_sums=True, dt=None):
+        want_states=False, want_sums=True, dt=None, ghost=None):
     """Run samples [s0, s0+ns) through steps [step0, step0+nsteps).
+    ghost: [nsteps][2] Dirichlet values at x = lo, hi after each step (1D,
+    pb["periodic"] False; default pb["ghost"] when present).
 
     Returns dict with 'states' ([ns][E][n], if asked) and 'sum', 'sumsq'
     ([E][n], sums over the ns samples)."""
@@ -336,7 +340,12 @@ def run(pb, nsteps=None, step0=0, s0=0, ns=None, nthreads=1, state_in=None,
     st = np.zeros((ns, E, n)) if want_states else None
     sm = np.zeros((E, n)) if want_sums else None
     sq = np.zeros((E, n)) if want_sums else None
-    rc = lib().orc_run(C.byref(p), step0, nsteps, s0, ns, nthreads, _dp(sin), _dp(st), _dp(sm), _dp(sq))
+    if ghost is None:
+        ghost = pb.get("ghost")
+    gh = None if ghost is None else np.ascontiguousarray(np.asarray(ghost, dtype=np.float64).reshape(-1, 2)[:nsteps])
+    if gh is not None and gh.shape[0] < nsteps:
+        raise ValueError("ghost values cover fewer steps than the run")
+    rc = lib().orc_run(C.byref(p), step0, nsteps, s0, ns, nthreads, _dp(gh), _dp(sin), _dp(st), _dp(sm), _dp(sq))
     if rc != 0:
         raise RuntimeError("oracle run failed (singular remap or bad problem)")
     return {"states": st, "sum": sm, "sumsq": sq}

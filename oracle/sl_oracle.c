@@ -623,6 +623,9 @@ typedef struct {
     unsigned long long seed;
     double dt;
     double omega; /* weight of the boundary rows of the remap; <= 0 means 1; INFINITY: hard (1D) */
+    int periodic;     /* 1: periodic; 0: Dirichlet ghost values at x = lo, hi (1D)         */
+    int reseed_every; /* > 0: every sample set to the sample mean after each step n with    */
+                      /* (n + 1) % reseed_every == 0 (Eq. re-seed); 0: never                */
 } orc_problem;
 
 /* Drift u(x) (1D: u[0]; 2D: u[0], u[1]).                                    */
@@ -705,6 +708,8 @@ typedef struct {
     double *afx, *bfx;   /* [Ky][Kx][N(2D) or 1] vertical faces: u_x dt, sqrt(2D) */
     double *afy, *bfy;   /* [Ky][Kx][N] horizontal faces (2D)                 */
     double omega;        /* boundary-row weight of the remap                  */
+    int periodic;        /* 0: Dirichlet boundaries (1D)                      */
+    double afx_hi, bfx_hi; /* 1D: u dt and sqrt(2D) at the right boundary x = hi */
 } orc_coeffs;
 
 static void orc_coeffs_free(orc_coeffs *cf)
@@ -748,6 +753,7 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
     cf->hx = (pb->hi[0] - pb->lo[0]) / cf->Kx;
     cf->hy = d == 2 ? (pb->hi[1] - pb->lo[1]) / cf->Ky : 1.0;
     cf->omega = pb->omega > 0.0 ? pb->omega : 1.0;
+    cf->periodic = pb->periodic;
     int E = cf->E, n = cf->n;
     cf->xi = (double *)malloc(sizeof(double) * N);
     orc_nodes(N, cf->xi);
@@ -812,6 +818,12 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
             }
         }
     }
+    if (d == 1) {
+        double u[2];
+        orc_drift(pb, pb->hi[0], 0.0, u);
+        cf->afx_hi = u[0] * pb->dt;
+        cf->bfx_hi = sqrt(2.0 * orc_diffusion(pb, pb->hi[0], 0.0));
+    }
     free(ux);
     free(uy);
     return 0;
@@ -848,14 +860,17 @@ int orc_get_coeffs(const orc_problem *pb, double *ax, double *ay, double *b, dou
 }
 
 /* One SL step of one sample (Sections 5.2-5.3), state Q [E][n] in place.    */
-static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, double *Q)
+/* One SL step of one 1D sample.  ghost (Dirichlet only): the boundary values */
+/* at x = lo and x = hi at the end of the step, the ghost solution that takes */
+/* the place of the missing neighbour in the upwind rule.                     */
+static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, const double *ghost, double *Q)
 {
     int N = cf->N, K = cf->Kx;
     double *d = (double *)malloc(sizeof(double) * K * N);
     double *phs = (double *)malloc(sizeof(double) * K * N);
     double *e0 = (double *)malloc(sizeof(double) * K);
     double *e1 = (double *)malloc(sizeof(double) * K);
-    double *g = (double *)malloc(sizeof(double) * K);
+    double *g = (double *)malloc(sizeof(double) * (K + 1)); /* interface values, g[K]: x = hi */
     int rc = 0;
     /* advance (Eq. def_dx): particle p moves from xi_p by d_p = (u dt +      */
     /* sqrt(2D) dW) / h in element units; compositional update              */
@@ -870,11 +885,17 @@ static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, double *Q)
     /* f (periodic); take the left element's value when u dt + sqrt(2D) dW > 0 */
     for (int f = 0; f < K; ++f) {
         double sigma = cf->afx[f] + cf->bfx[f] * dW;
-        g[f] = sigma > 0.0 ? e1[(f - 1 + K) % K] : e0[f];
+        double left = (f == 0 && !cf->periodic) ? ghost[0] : e1[(f - 1 + K) % K];
+        g[f] = sigma > 0.0 ? left : e0[f];
+    }
+    if (cf->periodic)
+        g[K] = g[0];
+    else {
+        double sigma = cf->afx_hi + cf->bfx_hi * dW;
+        g[K] = sigma > 0.0 ? e1[K - 1] : ghost[1];
     }
     for (int k = 0; k < K && rc == 0; ++k)
-        rc = orc_remap_1d_split_w(N, cf->xi, d + k * N, phs + k * N, g[k], g[(k + 1) % K], cf->omega,
-                                  Q + k * N);
+        rc = orc_remap_1d_split_w(N, cf->xi, d + k * N, phs + k * N, g[k], g[k + 1], cf->omega, Q + k * N);
     free(d);
     free(phs);
     free(e0);
@@ -950,6 +971,7 @@ typedef struct {
     const double *phi0; /* [E][n] initial state when state_in is NULL */
     double *state_out;
     double *sum, *sumsq; /* this thread's partial sums [E][n] */
+    const double *ghost; /* [nsteps][2] Dirichlet values (1D, non-periodic), else NULL */
     int rc;
 } orc_job;
 
@@ -971,7 +993,7 @@ static void *orc_worker(void *arg)
             orc_normals(jb->pb->seed, (uint32_t)(jb->step0 + t), (uint32_t)s, 0u, z);
             dW[0] = sdt * z[0];
             dW[1] = sdt * z[1];
-            jb->rc = cf->dim == 1 ? orc_step_1d(cf, jb->pb->dt, dW[0], Q)
+            jb->rc = cf->dim == 1 ? orc_step_1d(cf, jb->pb->dt, dW[0], jb->ghost ? jb->ghost + 2 * t : NULL, Q)
                                   : orc_step_2d(cf, jb->pb->dt, dW, Q);
         }
         if (jb->state_out) memcpy(jb->state_out + (size_t)(s - jb->s0) * sz, Q, sizeof(double) * sz);
@@ -985,27 +1007,20 @@ static void *orc_worker(void *arg)
     return NULL;
 }
 
-/* Runs samples [s0, s0+ns).  state_in ([ns][E][n]) or NULL for phi0;       */
-/* state_out ([ns][E][n]) may be NULL; sum and sumsq ([E][n]) may be NULL and */
-/* receive sum_s Q and sum_s Q^2, threads' partials added in thread order,  */
-/* each thread in ascending sample order.  Returns 0 or -1.                 */
-int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int nthreads,
-            const double *state_in, double *state_out, double *sum, double *sumsq)
+/* Samples [s0, s0+ns) through steps [step0, step0+nsteps) without          */
+/* reseeding: the samples are independent and run on `nthreads` threads.    */
+static int orc_run_segment(const orc_problem *pb, const orc_coeffs *cf, const double *phi0, long step0,
+                           int nsteps, int s0, int ns, int nthreads, const double *ghost,
+                           const double *state_in, double *state_out, double *sum, double *sumsq)
 {
-    if (pb->dim < 1 || pb->dim > 2 || pb->N < 2 || ns < 0 || nsteps < 0 || pb->dt < 0.0) return -1;
-    if (pb->dim == 2 && isinf(pb->omega)) return -1; /* hard constraints: 1D only */
-    orc_coeffs cf;
-    if (orc_build_coeffs(pb, &cf) != 0) return -1;
-    size_t sz = (size_t)cf.E * cf.n;
+    size_t sz = (size_t)cf->E * cf->n;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > ns && ns > 0) nthreads = ns;
-    double *phi0 = (double *)malloc(sizeof(double) * sz);
-    orc_init_state(pb, phi0);
     orc_job *jobs = (orc_job *)calloc(nthreads, sizeof(orc_job));
     pthread_t *th = (pthread_t *)calloc(nthreads, sizeof(pthread_t));
     for (int t = 0; t < nthreads; ++t) {
         jobs[t].pb = pb;
-        jobs[t].cf = &cf;
+        jobs[t].cf = cf;
         jobs[t].step0 = step0;
         jobs[t].nsteps = nsteps;
         jobs[t].s0 = s0;
@@ -1014,6 +1029,7 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
         jobs[t].state_in = state_in;
         jobs[t].phi0 = phi0;
         jobs[t].state_out = state_out;
+        jobs[t].ghost = ghost;
         if (sum) {
             jobs[t].sum = (double *)calloc(sz, sizeof(double));
             jobs[t].sumsq = (double *)calloc(sz, sizeof(double));
@@ -1044,6 +1060,71 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
     }
     free(jobs);
     free(th);
+    return rc;
+}
+
+/* Runs samples [s0, s0+ns).  state_in ([ns][E][n]) or NULL for phi0;       */
+/* state_out ([ns][E][n]) may be NULL; sum and sumsq ([E][n]) may be NULL and */
+/* receive sum_s Q and sum_s Q^2, threads' partials added in thread order,  */
+/* each thread in ascending sample order.  ghost: [nsteps][2] boundary      */
+/* values at x = lo, hi after each step (1D Dirichlet; NULL when periodic).  */
+/* With reseed_every > 0 the run stops after each step n with               */
+/* (n + 1) % reseed_every == 0 and sets every sample to the mean of the ns  */
+/* samples (summed in ascending sample order), Eq. re-seed.  Returns 0/-1.  */
+int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int nthreads,
+            const double *ghost, const double *state_in, double *state_out, double *sum, double *sumsq)
+{
+    if (pb->dim < 1 || pb->dim > 2 || pb->N < 2 || ns < 0 || nsteps < 0 || pb->dt < 0.0) return -1;
+    if (pb->dim == 2 && isinf(pb->omega)) return -1; /* hard constraints: 1D only */
+    if (!pb->periodic && (pb->dim != 1 || !ghost)) return -1; /* Dirichlet: 1D, with boundary values */
+    if (pb->reseed_every < 0) return -1;
+    orc_coeffs cf;
+    if (orc_build_coeffs(pb, &cf) != 0) return -1;
+    size_t sz = (size_t)cf.E * cf.n;
+    double *phi0 = (double *)malloc(sizeof(double) * sz);
+    orc_init_state(pb, phi0);
+    int rc = 0;
+    if (pb->reseed_every == 0 || nsteps == 0) {
+        rc = orc_run_segment(pb, &cf, phi0, step0, nsteps, s0, ns, nthreads, pb->periodic ? NULL : ghost,
+                             state_in, state_out, sum, sumsq);
+    } else {
+        const long R = pb->reseed_every;
+        double *cur = (double *)malloc(sizeof(double) * sz * (size_t)(ns > 0 ? ns : 1));
+        double *nxt = (double *)malloc(sizeof(double) * sz * (size_t)(ns > 0 ? ns : 1));
+        for (int s = 0; s < ns; ++s) memcpy(cur + (size_t)s * sz, state_in ? state_in + (size_t)s * sz : phi0, sizeof(double) * sz);
+        long t = 0;
+        while (t < nsteps && rc == 0) {
+            long seg = R - (step0 + t) % R; /* steps up to and including the next reseed step */
+            if (seg > nsteps - t) seg = nsteps - t;
+            rc = orc_run_segment(pb, &cf, phi0, step0 + t, (int)seg, s0, ns, nthreads,
+                                 pb->periodic ? NULL : ghost + 2 * t, cur, nxt, NULL, NULL);
+            double *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+            t += seg;
+            if ((step0 + t) % R == 0 && ns > 0) { /* Eq. re-seed */
+                for (size_t i = 0; i < sz; ++i) {
+                    double m = 0.0;
+                    for (int s = 0; s < ns; ++s) m += cur[(size_t)s * sz + i];
+                    nxt[i] = m / ns;
+                }
+                for (int s = 0; s < ns; ++s) memcpy(cur + (size_t)s * sz, nxt, sizeof(double) * sz);
+            }
+        }
+        if (state_out) memcpy(state_out, cur, sizeof(double) * sz * (size_t)ns);
+        if (sum)
+            for (size_t i = 0; i < sz; ++i) {
+                sum[i] = 0.0;
+                sumsq[i] = 0.0;
+                for (int s = 0; s < ns; ++s) {
+                    double q = cur[(size_t)s * sz + i];
+                    sum[i] += q;
+                    sumsq[i] += q * q;
+                }
+            }
+        free(cur);
+        free(nxt);
+    }
     free(phi0);
     orc_coeffs_free(&cf);
     return rc;

@@ -260,3 +260,87 @@ def test_rotation_without_diffusion_against_exact_rotation(orc):
         x, y = orc.node_coords(pb)
         e[N] = float(np.abs(orc.run(pb, ns=1)["sum"] - exact(x, y)).max())
     assert e[6] < e[4] / 4 and e[8] < e[6] / 4 and e[8] <= 1e-3, e
+
+
+# ---------------------------------------------------------------- Dirichlet boundaries, reseeding
+# A Dirichlet boundary takes the place of the missing neighbour in the upwind
+# rule (Eq. bnd_update, ghost solution at the domain boundaries); reseeding
+# sets every sample to the sample mean (Eq. re-seed).
+
+def _fourier_eval(p, x):
+    f = p[0] + 0 * x
+    for m in range(int(p[2])):
+        f = f + p[3 + 2 * m] * np.cos((m + 1) * p[1] * np.pi * x) + p[4 + 2 * m] * np.sin((m + 1) * p[1] * np.pi * x)
+    return f
+
+
+@pytest.mark.parametrize("u", [1.0, -1.0])
+def test_dirichlet_inflow_pure_advection(orc, u):
+    # constant drift, no diffusion: the particle advance is exact in time, so
+    # the solution phi0(x - u t) is reproduced to interpolation accuracy when
+    # the inflow boundary carries the exact values; [0, 1.5] is not a period
+    # of phi0, so a periodic wrap would be wrong
+    p = [1.0, 1.0, 2.0, 0.3, -0.2, 0.1, 0.15]
+    dt, steps = 1e-3, 400
+    pb = I.problem(1, (6,), (0.0,), (1.5,), 10, 1, steps, dt, 2, ("const", [u, 0.0]), ("const", [0.0]), ("fourier", p))
+    pb["periodic"] = False
+    t = dt * np.arange(1, steps + 1)
+    ghost = np.stack([_fourier_eval(p, 0.0 - u * t), _fourier_eval(p, 1.5 - u * t)], axis=1)
+    x, _ = orc.node_coords(pb)
+    exact = _fourier_eval(p, x - u * steps * dt)
+    q = orc.run(pb, ns=1, ghost=ghost)["sum"]
+    assert np.abs(q - exact).max() <= 1e-7
+    # the boundary values are what carries the inflow
+    bad = orc.run(pb, ns=1, ghost=np.zeros_like(ghost))["sum"]
+    assert np.abs(bad - exact).max() > 1e-2
+
+
+def _heat(x, t, D=1.0):
+    return np.exp(-x * x / (4 * D * t)) / np.sqrt(4 * np.pi * D * t)
+
+
+def _heat_problem(orc, M, steps, reseed=0):
+    """The heat kernel on [-1, 1] from t0 = 0.05 (nodal initial values: the
+    Gaussian initial kinds add periodic images)."""
+    t0, dt = 0.05, 1e-5
+    pb = I.problem(1, (4,), (-1.0,), (1.0,), 8, M, steps, dt, 21, ("const", [0.0, 0.0]), ("const", [1.0]),
+                   ("gauss", [1.0, 0.3, 0.0, 0.0]))
+    pb["periodic"] = False
+    pb["reseed_every"] = reseed
+    t = t0 + dt * np.arange(1, steps + 1)
+    pb["ghost"] = np.stack([_heat(-1.0, t), _heat(1.0, t)], axis=1)
+    x, _ = orc.node_coords(pb)
+    state0 = np.broadcast_to(_heat(x, t0), (M,) + x.shape).copy()
+    return pb, state0, t0 + dt * steps
+
+
+def test_dirichlet_heat_kernel_mean_within_standard_error(orc):
+    # the paper's 1D Gaussian diffusion test (D = 1 on [-1, 1], heat kernel at
+    # t0 = 0.05, Dirichlet values from the exact solution, dt = 1e-5, 100 steps)
+    M = 4000
+    pb, state0, T = _heat_problem(orc, M, 100)
+    r = orc.run(pb, nthreads=8, state_in=state0)
+    mean, m2 = r["sum"] / M, r["sumsq"] / M
+    x, _ = orc.node_coords(pb)
+    se = np.sqrt(np.maximum(m2 - mean ** 2, 0.0) / (M - 1)).max()
+    # every sample is a translate of the same field, so the sampling error is
+    # one shared shift: compare with the largest standard error
+    assert np.abs(mean - _heat(x, T)).max() <= 4.0 * se + 1e-4
+    # reseeding every 50 steps (Eq. re-seed) keeps the mean: after a reseed the
+    # samples agree, so the spread no longer measures the sampling error and
+    # the standard error above is the scale
+    rr = orc.run(I.with_(pb, reseed_every=50), nthreads=8, state_in=state0)
+    mean_r = rr["sum"] / M
+    assert np.abs(mean_r - _heat(x, T)).max() <= 4.0 * se + 1e-4
+    assert np.abs(mean_r - mean).max() <= 0.5 * se
+
+
+def test_reseed_sets_every_sample_to_the_mean(orc):
+    pb, state0, _ = _heat_problem(orc, 6, 40)
+    with_r = orc.run(I.with_(pb, reseed_every=20), want_states=True, state_in=state0)
+    assert all(np.array_equal(with_r["states"][0], with_r["states"][s]) for s in range(1, 6))
+    # the mean is what reseeding keeps: the first 20 steps run the same
+    # samples either way, and the reseed after step 20 replaces them by their mean
+    plain = orc.run(I.with_(pb, steps=20), want_states=True, state_in=state0)
+    reseeded = orc.run(I.with_(pb, steps=20, reseed_every=20), want_states=True, state_in=state0)
+    assert np.allclose(reseeded["states"][0], plain["states"].mean(axis=0), rtol=0, atol=1e-15)
