@@ -95,7 +95,8 @@ typedef struct {
     int K[2];        /* elements per direction; K[1] ignored in 1D    */
     double lo[2];
     double hi[2];
-    int periodic[2]; /* must be 1 (Dirichlet ghost values: not provided) */
+    int periodic[2]; /* 1: periodic; 0 (1D only): Dirichlet boundaries whose values */
+                     /* the caller gives per step with sl_set_boundary              */
 } sl_mesh;
 
 typedef struct {
@@ -119,6 +120,10 @@ typedef struct {
                              /* set, sl_step keeps at most 2 launches queued on the  */
                              /* stream, waiting on the host for earlier ones, and so */
                              /* returns only when the last launches are queued       */
+    int reseed_every;        /* > 0: after every step n with (n + 1) % reseed_every  */
+                             /* == 0, every sample is set to the sample mean         */
+                             /* (Eq. re-seed; the paper reseeds every 100 steps with  */
+                             /* Dirichlet boundaries); 0: never                       */
 } sl_options;
 
 typedef struct sl_ctx sl_ctx; /* opaque; owns all of its device memory */
@@ -142,6 +147,20 @@ int sl_preload(int device);
 /* The step counter starts at 0.  opt may be NULL (seed 0, SL_FP64).         */
 int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift,
             const sl_field *diffusion, const sl_field *phi0, const sl_options *opt);
+
+/* Dirichlet boundary values (1D, periodic[0] = 0), Section 5.3: at a domain */
+/* boundary the given value is the ghost solution that takes the place of   */
+/* the missing neighbour in the upwind rule (Eq. bnd_update).  values: host */
+/* [nsteps][2], the values at x = lo and x = hi at the end of each of the   */
+/* next nsteps steps (step counters n .. n + nsteps - 1 from the current    */
+/* one), copied before return.  Each call replaces the previous table;      */
+/* sl_step returns SL_ERR_ARG for a step the table does not cover.          */
+/* SL_ERR_ARG on a periodic context.                                         */
+int sl_set_boundary(sl_ctx *c, int nsteps, const double *values);
+
+/* Sets every sample to the current sample mean (Eq. re-seed), on the       */
+/* context's stream.  sl_step does this itself when reseed_every > 0.       */
+int sl_reseed(sl_ctx *c);
 
 /* Advances every sample by `steps` SL steps of size dt (Sections 5.2-5.3):  */
 /* Wiener increments for the step counters [n, n+steps), particle advance,   */

@@ -50,7 +50,7 @@ class sl_mesh(C.Structure):
 class sl_options(C.Structure):
     _fields_ = [("seed", C.c_ulonglong), ("precision", C.c_int), ("strict_dt", C.c_int),
                 ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong),
-                ("bc_weight", C.c_double), ("launch_chunk", C.c_longlong)]
+                ("bc_weight", C.c_double), ("launch_chunk", C.c_longlong), ("reseed_every", C.c_int)]
 
 
 class sl_instance(C.Structure):
@@ -88,6 +88,8 @@ def lib():
                               C.POINTER(sl_field), C.POINTER(sl_field), C.POINTER(sl_options)]
         L.sl_step.argtypes = [vp, C.c_double, C.c_int]
         L.sl_preload.argtypes = [C.c_int]
+        L.sl_set_boundary.argtypes = [vp, C.c_int, _dp]
+        L.sl_reseed.argtypes = [vp]
         L.sl_moments.argtypes = [vp, _dp, _dp]
         L.sl_moments_device.argtypes = [vp, vp, vp]
         L.sl_dt_max.argtypes = [vp, _dp]
@@ -152,7 +154,7 @@ def _mesh(pb):
         m.K[d] = pb["K"][d]
         m.lo[d] = pb["lo"][d]
         m.hi[d] = pb["hi"][d]
-        m.periodic[d] = 1
+        m.periodic[d] = 1 if pb.get("periodic", True) else 0
     return m
 
 
@@ -185,6 +187,7 @@ def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, devi
     opt.sample0 = int(sample0)
     opt.launch_chunk = int(launch_chunk)
     opt.bc_weight = float(pb.get("bc_weight", 0.0) or 0.0)
+    opt.reseed_every = int(pb.get("reseed_every", 0) or 0)
     h = C.c_void_p()
     _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
                          C.byref(opt)), "sl_init")
@@ -475,6 +478,17 @@ class Solver:
         self.dim = pb["dim"]
         self.ctx = sl_init(pb, precision, seed, stream, strict_dt, phi0_nodal=phi0_nodal, sample0=sample0,
                            launch_chunk=launch_chunk)
+        if not pb.get("periodic", True) and pb.get("ghost") is not None:
+            self.set_boundary(pb["ghost"])
+
+    def set_boundary(self, values):
+        """Dirichlet values [steps][2] (x = lo, x = hi) after each of the next steps."""
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1, 2))
+        _check(lib().sl_set_boundary(C.c_void_p(self.ctx), v.shape[0], _f64p(v)), "sl_set_boundary")
+
+    def reseed(self):
+        """Every sample set to the current sample mean (Eq. re-seed)."""
+        _check(lib().sl_reseed(C.c_void_p(self.ctx)), "sl_reseed")
 
     def step(self, dt=None, steps=None):
         sl_step(self.ctx, self.pb["dt"] if dt is None else dt, self.pb["steps"] if steps is None else steps)

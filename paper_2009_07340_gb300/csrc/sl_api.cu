@@ -169,6 +169,7 @@ void sl_free(sl_ctx *c)
     }
     for (cudaEvent_t ev : c->throttle.ev)
         if (ev) cudaEventDestroy(ev);
+    sl::ctx_free(c, c->ghost);
     sl::ctx_free(c, c->xi);
     sl::ctx_free(c, c->nodeU);
     sl::ctx_free(c, c->nodeB);
@@ -197,7 +198,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     for (int d = 0; d < dim; ++d) {
         if (mesh->K[d] < 1 || !(mesh->hi[d] > mesh->lo[d]) || !std::isfinite(mesh->hi[d] - mesh->lo[d]))
             return SL_ERR_ARG;
-        if (!mesh->periodic[d]) return SL_ERR_UNSUPPORTED;
+        if (!mesh->periodic[d] && dim != 1) return SL_ERR_UNSUPPORTED;  // Dirichlet: 1D
     }
     if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion) || !valid_kind(dim, 2, phi0))
         return SL_ERR_ARG;
@@ -211,6 +212,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     const double bc_w = opt && opt->bc_weight > 0.0 ? opt->bc_weight : 1.0;
     if (opt && std::isnan(opt->bc_weight)) return SL_ERR_ARG;
     if (dim == 2 && std::isinf(bc_w)) return SL_ERR_UNSUPPORTED;  // hard constraints: 1D only
+    if (opt && opt->reseed_every < 0) return SL_ERR_ARG;
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
     if (sl::ensure_loaded() != cudaSuccess) {
@@ -226,6 +228,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     c->strict_dt = opt ? opt->strict_dt : 0;
     c->launch_chunk = opt && opt->launch_chunk > 0 ? opt->launch_chunk : 0;
     c->bc_weight = bc_w;
+    c->periodic = dim == 2 || mesh->periodic[0] ? 1 : 0;
+    c->reseed_every = opt ? opt->reseed_every : 0;
     c->inv_w2 = std::isinf(bc_w) ? 0.0 : 1.0 / (bc_w * bc_w);
     if (c->launch_chunk > 0)
         for (cudaEvent_t &ev : c->throttle.ev)
@@ -250,7 +254,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     }
     const long long V = (long long)m.E * m.n;
     c->state_elem = precision == SL_FP64 ? sizeof(double) : sizeof(float2);  // FP32 modes: hi + lo pair
-    const int nf = dim == 1 ? m.E : 2 * m.E * N;
+    const int nf = dim == 1 ? m.E + 1 : 2 * m.E * N;  // 1D: interfaces 0..K
     c->mom_chunk = 64;
     const int nc = (M + c->mom_chunk - 1) / c->mom_chunk;
     bool ok = dalloc(c, &c->xi, N) == cudaSuccess && dalloc(c, &c->nodeU, size_t(dim) * V) == cudaSuccess &&
@@ -357,6 +361,8 @@ int sl_step(sl_ctx *c, double dt, int steps)
     if (!(dt > 0.0) || !std::isfinite(dt) || steps < 0) return SL_ERR_ARG;
     if (c->strict_dt && dt > c->dtmax * (1.0 + 1e-12)) return SL_ERR_DT;
     if (steps == 0) return SL_OK;
+    if (!c->periodic && (c->step < c->ghost_base || c->step + steps > c->ghost_base + c->ghost_count))
+        return SL_ERR_ARG;  // Dirichlet: boundary values must cover every step (sl_set_boundary)
     const sl::Mesh &m = c->m;
     const int dim = m.dim;
     const size_t per_step = size_t(c->M) * dim * sizeof(double);
@@ -373,7 +379,9 @@ int sl_step(sl_ctx *c, double dt, int steps)
     }
     const double sqrt_dt = std::sqrt(dt);
     for (int done = 0; done < steps;) {
-        const int n = std::min(chunk, steps - done);
+        int n = std::min(chunk, steps - done);
+        if (c->reseed_every > 0)  // stop at the next reseed point
+            n = int(std::min<long long>(n, c->reseed_every - c->step % c->reseed_every));
         cudaError_t e = sl::launch_wiener(c->seed, c->step, c->sample0, n, c->M, dim, sqrt_dt, c->dW, c->st);
         if (e != cudaSuccess) return fail_cuda(c);
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -394,6 +402,8 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.dt = dt;
             a.h = m.h[0];
             a.inv_w2 = c->inv_w2;
+            a.periodic = c->periodic;
+            a.ghost = c->periodic ? nullptr : c->ghost + 2 * (c->step - c->ghost_base);
             a.xi = c->xi;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
@@ -439,7 +449,50 @@ int sl_step(sl_ctx *c, double dt, int steps)
         if (c->profiling && cudaEventRecord(ev.second, c->st) != cudaSuccess) return fail_cuda(c);
         c->step += n;
         done += n;
+        if (c->reseed_every > 0 && c->step % c->reseed_every == 0) {
+            const int rc = sl_reseed(c);
+            if (rc != SL_OK) return rc;
+        }
     }
+    return SL_OK;
+}
+
+int sl_reseed(sl_ctx *c)
+{
+    if (!c) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const long long V = (long long)c->m.E * c->m.n;
+    const int dbl = c->precision == SL_FP64;
+    if (sl::launch_moments(c->Q, dbl, c->M, V, c->mom_chunk, c->psum, c->psq, c->mean_tmp, nullptr, c->st) !=
+            cudaSuccess ||
+        sl::launch_reseed(c->Q, dbl, c->M, V, c->mean_tmp, c->st) != cudaSuccess)
+        return fail_cuda(c);
+    return SL_OK;
+}
+
+int sl_set_boundary(sl_ctx *c, int nsteps, const double *values)
+{
+    if (!c || nsteps < 0 || (nsteps > 0 && !values)) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    if (c->periodic) return SL_ERR_ARG;
+    if (nsteps > c->ghost_cap) {
+        sl::ctx_free(c, c->ghost);
+        c->ghost = nullptr;
+        c->ghost_cap = 0;
+        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&c->ghost), size_t(nsteps) * 2 * sizeof(double)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return SL_ERR_OOM;
+        }
+        c->ghost_cap = nsteps;
+    }
+    if (nsteps > 0 &&
+        (cudaMemcpyAsync(c->ghost, values, size_t(nsteps) * 2 * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(c->st) != cudaSuccess))
+        return fail_cuda(c);
+    c->ghost_base = c->step;
+    c->ghost_count = nsteps;
     return SL_OK;
 }
 

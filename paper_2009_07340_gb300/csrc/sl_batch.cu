@@ -124,6 +124,8 @@ sl::Step1DArgs args1d(const sl_ctx *c, double dt, int steps)
     a.dt = dt;
     a.h = c->m.h[0];
     a.inv_w2 = c->inv_w2;
+    a.periodic = 1;  // batches hold periodic instances only
+    a.ghost = nullptr;
     a.xi = c->xi;
     a.nodeU = c->nodeU;
     a.nodeB = c->nodeB;
@@ -315,6 +317,10 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
         if (!(s.dt > 0.0) || !std::isfinite(s.dt) || s.dt_rule < 0 || s.dt_rule > 2 || (s.dt_rule > 0 && s.dt > 1.0)) {
             sl_batch_free(b);
             return SL_ERR_ARG;
+        }
+        if (s.mesh.dim == 1 && !s.mesh.periodic[0]) {  // Dirichlet instances run alone (sl_init)
+            sl_batch_free(b);
+            return SL_ERR_UNSUPPORTED;
         }
         sl_options oi = o;
         oi.seed = s.seed;

@@ -38,12 +38,14 @@ struct Step1DArgs {
     int nsteps;
     double dt, h;
     double inv_w2;         // 1 / w^2 of the boundary rows (0: hard constraints)
+    int periodic;          // 0: Dirichlet boundaries with the ghost values below
+    const double *ghost;   // [nsteps][2] boundary values at x = lo, hi after each step (Dirichlet)
     const double *xi;      // [N] reference nodes on [0,1]
     const double *nodeU;   // [K][N] drift at the nodes
     const double *nodeB;   // [K][N] sqrt(2 D) at the nodes
     const double *nodeDiv; // [K][N] du/dx at the nodes
-    const double *faceU;   // [K] drift at interface k (left face of element k)
-    const double *faceB;   // [K] sqrt(2 D) at interface k
+    const double *faceU;   // [K + 1] drift at interface k (left face of element k; K: x = hi)
+    const double *faceB;   // [K + 1] sqrt(2 D) at interface k
     const double *dW;      // [nsteps][M] Wiener increments
     void *Q;               // [M][K][N] state (double for SL_FP64, float otherwise)
     int *err;              // device error word (bit 0: non-finite remap)
@@ -128,6 +130,8 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
                           double sqrt_dt, double *out, cudaStream_t st);
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk,
                            double *psum, double *psq, double *mean, double *m2, cudaStream_t st);
+// Every sample set to `mean` (Eq. re-seed).
+cudaError_t launch_reseed(void *Q, int state_is_double, int M, long long V, const double *mean, cudaStream_t st);
 
 // Module loading.  With lazy loading (the default), the first launch of a
 // kernel loads it, and a load may synchronise the whole device: a request
@@ -189,6 +193,10 @@ struct sl_ctx {
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
     double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)
+    int periodic = 1;             // 0: 1D Dirichlet boundaries
+    int reseed_every = 0;         // > 0: samples set to their mean after every such step count
+    double *ghost = nullptr;      // device [ghost_cap][2] boundary values (Dirichlet)
+    long long ghost_cap = 0, ghost_base = 0, ghost_count = 0;  // rows, first step, steps covered
     sl::LaunchThrottle throttle;  // events created when launch_chunk > 0
     // 1D launch geometry
     int S = 1, C = 1, T = 1;

@@ -450,6 +450,8 @@ int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long
     if (!s || !spec || steps < 1 || !(spec->dt > 0.0) || spec->dt_rule < 0 || spec->dt_rule > 2 ||
         (spec->dt_rule > 0 && spec->dt > 1.0))
         return SL_ERR_ARG;
+    if (!spec->mesh.periodic[0] || (spec->mesh.dim == 2 && !spec->mesh.periodic[1]))
+        return SL_ERR_UNSUPPORTED;  // requests carry no boundary values: periodic meshes only
     Request r;
     r.owner = s;
     r.spec = *spec;

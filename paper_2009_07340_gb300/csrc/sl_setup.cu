@@ -3,6 +3,8 @@
 // increments (Section 5.2) and the sample moments (Section 5.4).
 #include <cmath>
 
+#include <algorithm>
+
 #include "sl_internal.cuh"
 #include "sl_rng.cuh"
 
@@ -139,7 +141,7 @@ __global__ void init_nodes_kernel(Mesh m, FieldDev fu, FieldDev fD, FieldDev fph
 // (normal drift u_x) and of its low-y face (u_y), at the Gauss-node positions.
 __global__ void init_faces_kernel(Mesh m, FieldDev fu, FieldDev fD, double *faceU, double *faceB)
 {
-    const int nf = m.dim == 1 ? m.E : m.E * m.N;
+    const int nf = m.dim == 1 ? m.E + 1 : m.E * m.N;  // 1D: interfaces 0..K (K: x = hi)
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nf) return;
     double ux, uy;
@@ -178,7 +180,7 @@ cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev 
                                                      static_cast<float2 *>(Q), M);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int nf = m.dim == 1 ? m.E : m.E * m.N;
+    const int nf = m.dim == 1 ? m.E + 1 : m.E * m.N;
     init_faces_kernel<<<(nf + tb - 1) / tb, tb, 0, st>>>(m, u, D, faceU, faceB);
     return cudaGetLastError();
 }
@@ -285,6 +287,28 @@ __global__ void moments_final_kernel(const double *__restrict__ psum, const doub
     if (m2) m2[v] = b / M;
 }
 
+// Eq. re-seed: every sample of every node set to the node's sample mean.
+template <typename State>
+__global__ void reseed_kernel(State *Q, const double *__restrict__ mean, int M, long long V)
+{
+    const long long total = (long long)M * V;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        store_state(Q, i, mean[i % V]);
+}
+
+cudaError_t launch_reseed(void *Q, int state_is_double, int M, long long V, const double *mean, cudaStream_t st)
+{
+    const int tb = 256;
+    const long long total = (long long)M * V;
+    const unsigned grid = unsigned(std::min<long long>((total + tb - 1) / tb, 152LL * 16));
+    if (total == 0) return cudaSuccess;
+    if (state_is_double)
+        reseed_kernel<double><<<grid, tb, 0, st>>>(static_cast<double *>(Q), mean, M, V);
+    else
+        reseed_kernel<float2><<<grid, tb, 0, st>>>(static_cast<float2 *>(Q), mean, M, V);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
                            double *psq, double *mean, double *m2, cudaStream_t st)
 {
@@ -312,6 +336,8 @@ cudaError_t preload_setup()
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double>);
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<float2>);
     return e;
 }
 

@@ -93,6 +93,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// A boundary value as a face value: FP64, or the float pair hi + lo.
+template <typename FaceT>
+__device__ __forceinline__ FaceT ghost_face(double g)
+{
+    if constexpr (std::is_same<FaceT, double>::value) {
+        return g;
+    } else {
+        const float hi = float(g);
+        return make_float2(hi, float(g - double(hi)));
+    }
+}
+
 // Row of a shared-memory table into registers with 16-byte loads.
 template <int NP>
 __device__ __forceinline__ void load_row(const float *src, float (&z)[NP])
@@ -167,7 +179,7 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
         sZ[idx] = m < N ? R(4.0 * (a.xi[i] - a.xi[m])) : R(0);
     }
     for (int idx = threadIdx.x; idx <= Kc; idx += blockDim.x) {
-        const int f = (k0 + idx) % K;  // interface f: left face of element f
+        const int f = a.periodic ? (k0 + idx) % K : k0 + idx;  // interface f: left face of element f
         sfa[idx] = R(a.faceU[f] * a.dt);
         sfb[idx] = R(a.faceB[f]);
     }
@@ -349,6 +361,10 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
             } else {
                 left_e1 = fR[sbase + lnb_idx];
                 right_e0 = fL[sbase + rnb_idx];
+            }
+            if (!a.periodic) {  // a domain boundary: the ghost value takes the missing neighbour's place
+                if (k0 + kl == 0) left_e1 = ghost_face<FaceT>(a.ghost[2 * t + 0]);
+                if (k0 + kl == K - 1) right_e0 = ghost_face<FaceT>(a.ghost[2 * t + 1]);
             }
             gL = sigL > R(0) ? left_e1 : f0;
             gR = sigR > R(0) ? f1 : right_e0;

@@ -84,7 +84,7 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
         sZ[idx] = m < N ? float(4.0 * (a.xi[j] - a.xi[m])) : 0.f;
     }
     for (int idx = threadIdx.x; idx <= Kc; idx += blockDim.x) {
-        const int f = (k0 + idx) % K;
+        const int f = a.periodic ? (k0 + idx) % K : k0 + idx;  // K: the boundary x = hi
         sfa[idx] = float(a.faceU[f] * a.dt);
         sfb[idx] = float(a.faceB[f]);
     }
@@ -241,6 +241,10 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
             } else {
                 left_e1 = fR[sbase + lnb_idx];
                 right_e0 = fL[sbase + rnb_idx];
+            }
+            if (!a.periodic) {  // a domain boundary: the ghost value takes the missing neighbour's place
+                if (k0 + kl == 0) left_e1 = ghost_face<float2>(a.ghost[2 * t + 0]);
+                if (k0 + kl == K - 1) right_e0 = ghost_face<float2>(a.ghost[2 * t + 1]);
             }
             gL = sigL > 0.f ? left_e1 : f0;
             gR = sigR > 0.f ? f1 : right_e0;

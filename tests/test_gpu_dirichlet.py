@@ -1,0 +1,141 @@
+"""Dirichlet boundaries (ghost values in the upwind rule at the domain
+boundaries, Eq. bnd_update) and reseeding (Eq. re-seed) on the GPU, through
+the C ABI, against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import sl_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sl():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_07340_gb300 import build
+
+    build.build()
+    import paper_2009_07340_gb300 as sl
+
+    return sl
+
+
+def _fourier(p, x):
+    f = p[0] + 0 * x
+    for m in range(int(p[2])):
+        f = f + p[3 + 2 * m] * np.cos((m + 1) * p[1] * np.pi * x) + p[4 + 2 * m] * np.sin((m + 1) * p[1] * np.pi * x)
+    return f
+
+
+def _advection(u, M=3, steps=400, dt=1e-3, K=6, N=10):
+    p = [1.0, 1.0, 2.0, 0.3, -0.2, 0.1, 0.15]
+    pb = I.problem(1, (K,), (0.0,), (1.5,), N, M, steps, dt, 2, ("const", [u, 0.0]), ("const", [0.0]), ("fourier", p))
+    pb["periodic"] = False
+    t = dt * np.arange(1, steps + 1)
+    pb["ghost"] = np.stack([_fourier(p, 0.0 - u * t), _fourier(p, 1.5 - u * t)], axis=1)
+    return pb, p
+
+
+@pytest.mark.parametrize("u", [1.0, -1.0])
+def test_inflow_advection_fp64_vs_oracle_and_exact(sl, orc, u):
+    pb, p = _advection(u)
+    ref = orc.run(pb, ns=pb["M"], want_states=True)["states"]
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        st = s.samples()
+    assert np.abs(st - ref).max() / np.abs(ref).max() <= FP64_TOL
+    x, _ = orc.node_coords(pb)
+    assert np.abs(st[0] - _fourier(p, x - u * pb["steps"] * pb["dt"])).max() <= 1e-7
+    for precision in ("fp32", "mixed"):
+        with sl.Solver(pb, precision) as s:
+            s.step()
+            assert np.abs(s.samples() - st).max() / np.abs(st).max() <= MIXED_TOL, precision
+
+
+def _heat(x, t):
+    return np.exp(-x * x / (4 * t)) / np.sqrt(4 * np.pi * t)
+
+
+def _heat_problem(orc, M, steps, reseed, K=4, N=8):
+    t0, dt = 0.05, 1e-5
+    pb = I.problem(1, (K,), (-1.0,), (1.0,), N, M, steps, dt, 21, ("const", [0.0, 0.0]), ("const", [1.0]),
+                   ("gauss", [1.0, 0.3, 0.0, 0.0]))
+    pb["periodic"] = False
+    pb["reseed_every"] = reseed
+    t = t0 + dt * np.arange(1, steps + 1)
+    pb["ghost"] = np.stack([_heat(-1.0, t), _heat(1.0, t)], axis=1)
+    x, _ = orc.node_coords(pb)
+    return pb, _heat(x, t0)
+
+
+@pytest.mark.parametrize("reseed", [0, 50, 30])
+def test_heat_kernel_with_reseeding(sl, orc, reseed):
+    pb, phi0 = _heat_problem(orc, 64, 100, reseed)
+    ref = orc.run(pb, ns=pb["M"], want_states=True, state_in=np.broadcast_to(phi0, (pb["M"],) + phi0.shape).copy(),
+                  nthreads=8)["states"]
+    with sl.Solver(pb, "fp64", phi0_nodal=phi0) as s:
+        s.step()
+        st = s.samples()
+        mean64, _ = s.moments()
+    assert np.abs(st - ref).max() / np.abs(ref).max() <= FP64_TOL
+    if reseed and pb["steps"] % reseed == 0:  # the last step reseeded: every sample is the mean
+        assert all(np.array_equal(st[0], st[k]) for k in range(1, pb["M"]))
+    for precision in ("fp32", "mixed"):
+        with sl.Solver(pb, precision, phi0_nodal=phi0) as s:
+            s.step()
+            m, _ = s.moments()
+        assert np.abs(m - mean64).max() / np.abs(mean64).max() <= MIXED_TOL, precision
+
+
+def test_dirichlet_on_a_cluster_mesh(sl, orc):
+    pb = I.config2(N=5, M=3, steps=15, K=300)
+    pb["periodic"] = False
+    pb["dt"] = 0.5 * orc.dt_max(pb)
+    pb["ghost"] = np.tile([0.8, 1.3], (15, 1))  # fixed boundary values
+    ref = orc.run(pb, ns=3, want_states=True)["states"]
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        assert np.abs(s.samples() - ref).max() / np.abs(ref).max() <= FP64_TOL
+
+
+def test_boundary_table_and_reseed_calls(sl, orc):
+    pb, phi0 = _heat_problem(orc, 8, 10, 0)
+    with sl.Solver(I.with_(pb, ghost=None), "fp64", phi0_nodal=phi0) as s:
+        with pytest.raises(sl.SLError) as e:  # no boundary values yet
+            s.step()
+        assert e.value.code == -1
+        s.set_boundary(pb["ghost"][:4])
+        s.step(steps=4)
+        with pytest.raises(sl.SLError):  # the table covers 4 steps only
+            s.step(steps=1)
+        s.set_boundary(pb["ghost"][4:])  # steps 4 .. 9
+        s.step(steps=6)
+        before, _ = s.moments()
+        s.reseed()
+        st = s.samples()
+        mean, m2 = s.moments()
+    assert all(np.array_equal(st[0], st[k]) for k in range(1, 8))
+    assert np.abs(mean - before).max() <= 1e-15 * np.abs(before).max()
+    np.testing.assert_allclose(m2, mean * mean, rtol=1e-14)
+    with sl.Solver(I.config2(N=4, M=2, steps=1, K=8), "fp64") as s:  # periodic: no boundary table
+        with pytest.raises(sl.SLError):
+            s.set_boundary([[1.0, 1.0]])
+
+
+def test_batch_and_server_reject_dirichlet(sl, orc):
+    pb, _ = _advection(1.0, steps=2)
+    pb["dt"] = 1e-3
+    with pytest.raises(sl.SLError) as e:
+        sl.Batch([pb], "fp64")
+    assert e.value.code == -8
+    with sl.Server(budget_bytes=1 << 26, precision="fp64") as srv:
+        with pytest.raises(sl.SLError) as e:
+            srv.submit(pb)
+        assert e.value.code == -8
