@@ -179,6 +179,16 @@ int sl_moments(sl_ctx *c, double *mean, double *m2);
 /* context's stream (no synchronisation, no error check of earlier steps).  */
 int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2);
 
+/* The PDF at every node recovered by binning the samples (Section 5.4):    */
+/* counts [elements][N^dim][nbins] (uint32) of the M samples in nbins equal */
+/* bins over [lo, hi]: bin b = floor((x - lo) * (nbins / (hi - lo))) in    */
+/* FP64 (FP32 pair states as hi + lo), x = hi in the last bin, x outside    */
+/* [lo, hi] or NaN not counted.  1 <= nbins <= 4096, lo < hi finite.        */
+/* sl_pdf: host counts, synchronous; sl_pdf_device: caller-owned device     */
+/* counts, asynchronous on the context's stream.                            */
+int sl_pdf(sl_ctx *c, int nbins, double lo, double hi, unsigned int *counts);
+int sl_pdf_device(sl_ctx *c, int nbins, double lo, double hi, unsigned int *d_counts);
+
 /* Largest dt satisfying |u|max dt + sqrt(2 Dmax dt) <= dx_min in every      */
 /* direction (Eq. 1d_timestep), dx_min = smallest node gap times h.          */
 int sl_dt_max(const sl_ctx *c, double *dt);

@@ -359,6 +359,26 @@ def moments(pb, **kw):
     return r["sum"] / M, r["sumsq"] / M
 
 
+def pdf(states, nbins, lo, hi):
+    """The PDF at every node recovered by binning the samples (Section 5.4):
+    states [M][E][n] -> counts [E][n][nbins] (uint32); bin b = floor((x - lo)
+    * (nbins / (hi - lo))) in FP64, x = hi in the last bin, x outside [lo, hi]
+    or NaN not counted."""
+    x = np.asarray(states, dtype=np.float64)
+    M = x.shape[0]
+    flat = x.reshape(M, -1)
+    scale = float(nbins) / (hi - lo)
+    counts = np.zeros((flat.shape[1], nbins), dtype=np.uint32)
+    for v in range(flat.shape[1]):
+        for s in range(M):
+            xv = flat[s, v]
+            if not (xv >= lo and xv <= hi):
+                continue
+            b = int(np.floor((xv - lo) * scale))
+            counts[v, min(b, nbins - 1)] += 1
+    return counts.reshape(x.shape[1:] + (nbins,))
+
+
 def node_coords(pb):
     """Physical coordinates of every node, [E][n] (x) and [E][n] (y, 2D)."""
     xi = nodes(pb["N"])

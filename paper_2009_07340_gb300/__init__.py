@@ -90,6 +90,8 @@ def lib():
         L.sl_preload.argtypes = [C.c_int]
         L.sl_set_boundary.argtypes = [vp, C.c_int, _dp]
         L.sl_reseed.argtypes = [vp]
+        L.sl_pdf.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_uint32)]
+        L.sl_pdf_device.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
         L.sl_moments.argtypes = [vp, _dp, _dp]
         L.sl_moments_device.argtypes = [vp, vp, vp]
         L.sl_dt_max.argtypes = [vp, _dp]
@@ -485,6 +487,13 @@ class Solver:
         """Dirichlet values [steps][2] (x = lo, x = hi) after each of the next steps."""
         v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1, 2))
         _check(lib().sl_set_boundary(C.c_void_p(self.ctx), v.shape[0], _f64p(v)), "sl_set_boundary")
+
+    def pdf(self, nbins, lo, hi):
+        """Per-node histogram of the samples, uint32 [E][n][nbins] (see sl_pdf)."""
+        out = np.zeros((self.E, self.n, int(nbins)), dtype=np.uint32)
+        _check(lib().sl_pdf(C.c_void_p(self.ctx), int(nbins), float(lo), float(hi),
+                            out.ctypes.data_as(C.POINTER(C.c_uint32))), "sl_pdf")
+        return out
 
     def reseed(self):
         """Every sample set to the current sample mean (Eq. re-seed)."""

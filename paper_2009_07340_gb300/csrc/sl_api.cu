@@ -524,6 +524,35 @@ int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2)
     return SL_OK;
 }
 
+int sl_pdf_device(sl_ctx *c, int nbins, double lo, double hi, unsigned int *d_counts)
+{
+    if (!c || !d_counts || nbins < 1 || nbins > 4096 || !std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo))
+        return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const long long V = (long long)c->m.E * c->m.n;
+    if (sl::launch_pdf(c->Q, c->precision == SL_FP64, c->M, V, nbins, lo, hi, d_counts, c->st) != cudaSuccess)
+        return fail_cuda(c);
+    return SL_OK;
+}
+
+int sl_pdf(sl_ctx *c, int nbins, double lo, double hi, unsigned int *counts)
+{
+    if (!c || !counts || nbins < 1 || nbins > 4096) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const size_t bytes = size_t(c->m.E) * c->m.n * nbins * sizeof(unsigned int);
+    unsigned int *d = nullptr;
+    if (sl::ctx_alloc(c, reinterpret_cast<void **>(&d), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SL_ERR_OOM;
+    }
+    int rc = sl_pdf_device(c, nbins, lo, hi, d);
+    if (rc == SL_OK && (cudaMemcpyAsync(counts, d, bytes, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+                        cudaStreamSynchronize(c->st) != cudaSuccess))
+        rc = fail_cuda(c);
+    sl::ctx_free(c, d);
+    return rc;
+}
+
 int sl_moments(sl_ctx *c, double *mean, double *m2)
 {
     if (!c || !mean) return SL_ERR_ARG;

@@ -130,6 +130,9 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
                           double sqrt_dt, double *out, cudaStream_t st);
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk,
                            double *psum, double *psq, double *mean, double *m2, cudaStream_t st);
+// Per-node histogram of the samples into B bins over [lo, hi] (device [V][B]).
+cudaError_t launch_pdf(const void *Q, int state_is_double, int M, long long V, int B, double lo, double hi,
+                       unsigned int *counts, cudaStream_t st);
 // Every sample set to `mean` (Eq. re-seed).
 cudaError_t launch_reseed(void *Q, int state_is_double, int M, long long V, const double *mean, cudaStream_t st);
 

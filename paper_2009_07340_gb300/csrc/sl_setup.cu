@@ -287,6 +287,49 @@ __global__ void moments_final_kernel(const double *__restrict__ psum, const doub
     if (m2) m2[v] = b / M;
 }
 
+// Histogram of the M samples at every node (recovery of the PDF by binning
+// the samples, Section 5.4): bin b = floor((x - lo) * scale), scale = B /
+// (hi - lo), in FP64; x = hi goes to the last bin; x outside [lo, hi] (or
+// NaN) is not counted.  A block owns `npb` consecutive nodes and counts in
+// shared memory; consecutive threads read consecutive nodes of one sample.
+template <typename State>
+__global__ void pdf_kernel(const State *__restrict__ Q, int M, long long V, int B, double lo, double hi,
+                           double scale, int npb, unsigned int *__restrict__ counts)
+{
+    extern __shared__ unsigned int hist[];  // [npb][B]
+    const long long v0 = (long long)blockIdx.x * npb;
+    const int nb = int(min((long long)npb, V - v0));
+    for (int i = threadIdx.x; i < nb * B; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const long long work = (long long)nb * M;
+    for (long long i = threadIdx.x; i < work; i += blockDim.x) {
+        const int j = int(i % nb);
+        const long long s = i / nb;
+        const double x = load_state(Q, s * V + v0 + j);
+        if (!(x >= lo && x <= hi)) continue;
+        int b = int(floor((x - lo) * scale));
+        if (b > B - 1) b = B - 1;
+        atomicAdd(&hist[j * B + b], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb * B; i += blockDim.x) counts[v0 * B + i] = hist[i];
+}
+
+cudaError_t launch_pdf(const void *Q, int state_is_double, int M, long long V, int B, double lo, double hi,
+                       unsigned int *counts, cudaStream_t st)
+{
+    const int npb = std::max(1, std::min(64, int((48 * 1024 / 4) / B)));
+    const size_t smem = size_t(npb) * B * sizeof(unsigned int);
+    const unsigned grid = unsigned((V + npb - 1) / npb);
+    const double scale = double(B) / (hi - lo);
+    if (V == 0) return cudaSuccess;
+    if (state_is_double)
+        pdf_kernel<double><<<grid, 256, smem, st>>>(static_cast<const double *>(Q), M, V, B, lo, hi, scale, npb, counts);
+    else
+        pdf_kernel<float2><<<grid, 256, smem, st>>>(static_cast<const float2 *>(Q), M, V, B, lo, hi, scale, npb, counts);
+    return cudaGetLastError();
+}
+
 // Eq. re-seed: every sample of every node set to the node's sample mean.
 template <typename State>
 __global__ void reseed_kernel(State *Q, const double *__restrict__ mean, int M, long long V)
@@ -337,6 +380,8 @@ cudaError_t preload_setup()
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
     if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(pdf_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(pdf_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<float2>);
     return e;
 }

@@ -164,3 +164,21 @@ def test_lu_and_lstsq_against_numpy(orc):
         assert np.allclose(orc.lstsq(A, b), ref, rtol=1e-10, atol=1e-11)
     with pytest.raises(np.linalg.LinAlgError):
         orc.lu_solve(np.zeros((3, 3)), np.ones(3))
+
+
+def test_pdf_binning_against_numpy_histogram(orc):
+    # recovery of the PDF at each node by binning the samples (Section 5.4)
+    rng = np.random.default_rng(12)
+    lo, hi, B = -1.0, 2.5, 7
+    x = rng.uniform(lo - 0.5, hi + 0.5, size=(50, 2, 3))
+    edges = np.linspace(lo, hi, B + 1)
+    x[np.min(np.abs(x[..., None] - edges), axis=-1) < 1e-9] = 0.123  # keep away from the edges
+    counts = orc.pdf(x, B, lo, hi)
+    for e in range(2):
+        for p in range(3):
+            ref, _ = np.histogram(x[:, e, p], bins=B, range=(lo, hi))
+            assert np.array_equal(counts[e, p], ref)
+    # the edge rules: lo in the first bin, hi in the last, outside and NaN not counted
+    y = np.array([lo, hi, lo - 1e-12, hi + 1e-12, np.nan, 0.0]).reshape(6, 1, 1)
+    c = orc.pdf(y, B, lo, hi)[0, 0]
+    assert c[0] == 1 and c[-1] == 1 and c.sum() == 3 and c[2] == 1  # 0.0 = lo + 2 widths
