@@ -148,6 +148,14 @@ int sl_preload(int device);
 int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift,
             const sl_field *diffusion, const sl_field *phi0, const sl_options *opt);
 
+/* New drift and diffusion fields for the following steps (a time-dependent */
+/* or externally computed flow, e.g. the velocity of an Eulerian solver the */
+/* particles are coupled to): the node and face coefficients, the           */
+/* divergence (spectral differentiation of the nodal drift) and the         */
+/* time-step bounds are evaluated again; the samples are not touched.       */
+/* Stream-ordered after earlier steps; synchronises the context's stream.   */
+int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion);
+
 /* Dirichlet boundary values (1D, periodic[0] = 0), Section 5.3: at a domain */
 /* boundary the given value is the ghost solution that takes the place of   */
 /* the missing neighbour in the upwind rule (Eq. bnd_update).  values: host */

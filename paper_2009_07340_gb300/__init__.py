@@ -90,6 +90,7 @@ def lib():
         L.sl_preload.argtypes = [C.c_int]
         L.sl_set_boundary.argtypes = [vp, C.c_int, _dp]
         L.sl_reseed.argtypes = [vp]
+        L.sl_set_fields.argtypes = [vp, C.POINTER(sl_field), C.POINTER(sl_field)]
         L.sl_pdf.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_uint32)]
         L.sl_pdf_device.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
         L.sl_moments.argtypes = [vp, _dp, _dp]
@@ -494,6 +495,12 @@ class Solver:
         _check(lib().sl_pdf(C.c_void_p(self.ctx), int(nbins), float(lo), float(hi),
                             out.ctypes.data_as(C.POINTER(C.c_uint32))), "sl_pdf")
         return out
+
+    def set_fields(self, drift, diffusion):
+        """New drift and diffusion (problem-dict form, e.g. ("sin", [...])) for the following steps."""
+        u, D = _field(_U, drift), _field(_D, diffusion)
+        _check(lib().sl_set_fields(C.c_void_p(self.ctx), C.byref(u), C.byref(D)), "sl_set_fields")
+        self.pb = dict(self.pb, drift=drift, diffusion=diffusion)
 
     def reseed(self):
         """Every sample set to the current sample mean (Eq. re-seed)."""

@@ -129,6 +129,39 @@ cudaError_t ensure_loaded()
 
 }  // namespace sl
 
+namespace {
+
+// The time-step bounds (Eq. 1d_timestep with the node gap, and with the edge
+// distance) from the current node coefficients (host copy; synchronises the
+// context's stream).
+int refresh_bounds(sl_ctx *c)
+{
+    const sl::Mesh &m = c->m;
+    const int dim = m.dim, N = m.N;
+    const long long V = (long long)m.E * m.n;
+    std::vector<double> hu(size_t(dim) * V), hb(V);
+    cudaError_t e = cudaMemcpyAsync(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return SL_ERR_CUDA;
+    double best = INFINITY, best_edge = INFINITY;
+    const double gap = host_min_gap(N), edge = host_edge_gap(N);
+    double bmax = 0.0;
+    for (double b : hb) bmax = std::max(bmax, b);
+    for (int d = 0; d < dim; ++d) {
+        double umax = 0.0;
+        for (long long v = 0; v < V; ++v) umax = std::max(umax, std::fabs(hu[size_t(d) * V + v]));
+        best = std::min(best, step_bound(umax, bmax, gap * m.h[d]));
+        best_edge = std::min(best_edge, step_bound(umax, bmax, edge * m.h[d]));
+    }
+    c->dtmax = best;
+    c->dtedge = best_edge;
+    return SL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sl_preload(int device)
@@ -284,30 +317,12 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (e == cudaSuccess)
         e = sl::launch_init_fields(m, to_dev(drift), to_dev(diffusion), to_dev(phi0), nodal_dev, c->xi, c->nodeU,
                                    c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M, precision == SL_FP64, c->st);
-    // maxima for the time-step guard (host copy of the node coefficients)
-    std::vector<double> hu(size_t(dim) * V), hb(V);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hu.data(), c->nodeU, hu.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hb.data(), c->nodeB, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     sl::ctx_free(c, nodal_dev);
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess || refresh_bounds(c) != SL_OK) {
+        cudaGetLastError();
         sl_free(c);
         return SL_ERR_CUDA;
     }
-    double best = INFINITY, best_edge = INFINITY;
-    const double gap = host_min_gap(N), edge = host_edge_gap(N);
-    double bmax = 0.0;
-    for (double b : hb) bmax = std::max(bmax, b);
-    for (int d = 0; d < dim; ++d) {
-        double umax = 0.0;
-        for (long long v = 0; v < V; ++v) umax = std::max(umax, std::fabs(hu[size_t(d) * V + v]));
-        best = std::min(best, step_bound(umax, bmax, gap * m.h[d]));
-        best_edge = std::min(best_edge, step_bound(umax, bmax, edge * m.h[d]));
-    }
-    c->dtmax = best;
-    c->dtedge = best_edge;
 
     if (dim == 1) {
         const int K = m.K[0];
@@ -351,6 +366,24 @@ int sl_set_step_count(sl_ctx *c, long long n)
     if (!c || n < 0) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     c->step = n;
+    return SL_OK;
+}
+
+int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
+{
+    if (!c) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const int dim = c->m.dim;
+    if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion)) return SL_ERR_ARG;
+    if (diffusion->kind != SL_D_CONST && std::fabs(diffusion->p[1]) > 1.0) return SL_ERR_ARG;  // D >= 0
+    if (diffusion->p[0] < 0.0) return SL_ERR_ARG;
+    sl_field none;
+    std::memset(&none, 0, sizeof(none));
+    none.kind = SL_PHI_GAUSS;  // no state is written
+    const cudaError_t e = sl::launch_init_fields(c->m, to_dev(drift), to_dev(diffusion), to_dev(&none), nullptr, c->xi,
+                                                 c->nodeU, c->nodeB, c->nodeDiv, c->faceU, c->faceB, nullptr, c->M,
+                                                 c->precision == SL_FP64, c->st);
+    if (e != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
     return SL_OK;
 }
 

@@ -132,6 +132,7 @@ __global__ void init_nodes_kernel(Mesh m, FieldDev fu, FieldDev fD, FieldDev fph
         }
     }
     nodeDiv[v] = dx / m.h[0] + (m.dim == 2 ? dy / m.h[1] : 0.0);
+    if (!Q) return;  // coefficients only (new fields between steps)
     const double phi = phi0_nodal ? phi0_nodal[v] : phi0_at(fphi, m, x, y);
     for (int s = 0; s < M; ++s) store_state(Q, (long long)s * V + v, phi);
 }
