@@ -120,6 +120,14 @@ typedef struct {
                              /* set, sl_step keeps at most 2 launches queued on the  */
                              /* stream, waiting on the host for earlier ones, and so */
                              /* returns only when the last launches are queued       */
+    int components;          /* scalar fields per sample sharing the particles and    */
+                             /* so the remap factorization (Section 5.3: its cost     */
+                             /* does not grow with the components); 0 or 1: one; 2:   */
+                             /* two (1D, periodic, SL_FP64 or SL_FP32; otherwise     */
+                             /* SL_ERR_UNSUPPORTED).  Each sample's state, samples   */
+                             /* and moments are [components][elements][N]; every     */
+                             /* component starts from phi0 (set others with          */
+                             /* sl_set_samples)                                       */
     int reseed_every;        /* > 0: after every step n with (n + 1) % reseed_every  */
                              /* == 0, every sample is set to the sample mean         */
                              /* (Eq. re-seed; the paper reseeds every 100 steps with  */

@@ -50,7 +50,8 @@ class sl_mesh(C.Structure):
 class sl_options(C.Structure):
     _fields_ = [("seed", C.c_ulonglong), ("precision", C.c_int), ("strict_dt", C.c_int),
                 ("stream", C.c_void_p), ("device", C.c_int), ("sample0", C.c_longlong),
-                ("bc_weight", C.c_double), ("launch_chunk", C.c_longlong), ("reseed_every", C.c_int)]
+                ("bc_weight", C.c_double), ("launch_chunk", C.c_longlong), ("components", C.c_int),
+                ("reseed_every", C.c_int)]
 
 
 class sl_instance(C.Structure):
@@ -191,6 +192,7 @@ def sl_init(pb, precision=SL_FP64, seed=None, stream=None, strict_dt=False, devi
     opt.launch_chunk = int(launch_chunk)
     opt.bc_weight = float(pb.get("bc_weight", 0.0) or 0.0)
     opt.reseed_every = int(pb.get("reseed_every", 0) or 0)
+    opt.components = int(pb.get("components", 1) or 1)
     h = C.c_void_p()
     _check(lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(u), C.byref(D), C.byref(phi),
                          C.byref(opt)), "sl_init")
@@ -476,9 +478,11 @@ class Solver:
         self.pb = pb
         self.E = int(np.prod(pb["K"]))
         self.n = pb["N"] ** pb["dim"]
-        self.V = self.E * self.n
+        self.ncomp = int(pb.get("components", 1) or 1)
+        self.V = self.ncomp * self.E * self.n  # values per sample
         self.M = pb["M"]
         self.dim = pb["dim"]
+        self._shape = (self.E, self.n) if self.ncomp == 1 else (self.ncomp, self.E, self.n)
         self.ctx = sl_init(pb, precision, seed, stream, strict_dt, phi0_nodal=phi0_nodal, sample0=sample0,
                            launch_chunk=launch_chunk)
         if not pb.get("periodic", True) and pb.get("ghost") is not None:
@@ -491,7 +495,7 @@ class Solver:
 
     def pdf(self, nbins, lo, hi):
         """Per-node histogram of the samples, uint32 [E][n][nbins] (see sl_pdf)."""
-        out = np.zeros((self.E, self.n, int(nbins)), dtype=np.uint32)
+        out = np.zeros(self._shape + (int(nbins),), dtype=np.uint32)
         _check(lib().sl_pdf(C.c_void_p(self.ctx), int(nbins), float(lo), float(hi),
                             out.ctypes.data_as(C.POINTER(C.c_uint32))), "sl_pdf")
         return out
@@ -511,14 +515,14 @@ class Solver:
 
     def moments(self, want_m2=True):
         mean, m2 = sl_moments(self.ctx, self.V, want_m2)
-        return mean.reshape(self.E, self.n), (m2.reshape(self.E, self.n) if m2 is not None else None)
+        return mean.reshape(self._shape), (m2.reshape(self._shape) if m2 is not None else None)
 
     def moments_device(self, mean_t, m2_t=None):
         sl_moments_device(self.ctx, mean_t.data_ptr(), m2_t.data_ptr() if m2_t is not None else None)
 
     def samples(self, s0=0, count=None):
         count = self.M - s0 if count is None else count
-        return sl_get_samples(self.ctx, s0, count, self.V).reshape(count, self.E, self.n)
+        return sl_get_samples(self.ctx, s0, count, self.V).reshape((count,) + self._shape)
 
     def set_samples(self, s0, states):
         sl_set_samples(self.ctx, s0, np.asarray(states).reshape(-1, self.V))

@@ -246,6 +246,9 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (opt && std::isnan(opt->bc_weight)) return SL_ERR_ARG;
     if (dim == 2 && std::isinf(bc_w)) return SL_ERR_UNSUPPORTED;  // hard constraints: 1D only
     if (opt && opt->reseed_every < 0) return SL_ERR_ARG;
+    const int ncomp = opt && opt->components > 1 ? opt->components : 1;
+    if (opt && (opt->components < 0 || opt->components > 2)) return SL_ERR_UNSUPPORTED;
+    if (ncomp > 1 && (dim != 1 || precision == SL_MIXED || !mesh->periodic[0])) return SL_ERR_UNSUPPORTED;
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
     if (sl::ensure_loaded() != cudaSuccess) {
@@ -263,6 +266,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     c->bc_weight = bc_w;
     c->periodic = dim == 2 || mesh->periodic[0] ? 1 : 0;
     c->reseed_every = opt ? opt->reseed_every : 0;
+    c->ncomp = ncomp;
     c->inv_w2 = std::isinf(bc_w) ? 0.0 : 1.0 / (bc_w * bc_w);
     if (c->launch_chunk > 0)
         for (cudaEvent_t &ev : c->throttle.ev)
@@ -287,15 +291,17 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     }
     const long long V = (long long)m.E * m.n;
     c->state_elem = precision == SL_FP64 ? sizeof(double) : sizeof(float2);  // FP32 modes: hi + lo pair
+    c->vals = (long long)ncomp * V;
     const int nf = dim == 1 ? m.E + 1 : 2 * m.E * N;  // 1D: interfaces 0..K
     c->mom_chunk = 64;
     const int nc = (M + c->mom_chunk - 1) / c->mom_chunk;
     bool ok = dalloc(c, &c->xi, N) == cudaSuccess && dalloc(c, &c->nodeU, size_t(dim) * V) == cudaSuccess &&
               dalloc(c, &c->nodeB, V) == cudaSuccess && dalloc(c, &c->nodeDiv, V) == cudaSuccess &&
               dalloc(c, &c->faceU, nf) == cudaSuccess && dalloc(c, &c->faceB, nf) == cudaSuccess &&
-              sl::ctx_alloc(c, &c->Q, size_t(M) * V * c->state_elem) == cudaSuccess &&
-              dalloc(c, &c->psum, size_t(nc) * V) == cudaSuccess && dalloc(c, &c->psq, size_t(nc) * V) == cudaSuccess &&
-              dalloc(c, &c->mean_tmp, V) == cudaSuccess && dalloc(c, &c->m2_tmp, V) == cudaSuccess &&
+              sl::ctx_alloc(c, &c->Q, size_t(M) * ncomp * V * c->state_elem) == cudaSuccess &&
+              dalloc(c, &c->psum, size_t(nc) * ncomp * V) == cudaSuccess &&
+              dalloc(c, &c->psq, size_t(nc) * ncomp * V) == cudaSuccess &&
+              dalloc(c, &c->mean_tmp, ncomp * V) == cudaSuccess && dalloc(c, &c->m2_tmp, ncomp * V) == cudaSuccess &&
               dalloc(c, &c->err, 1) == cudaSuccess;
     if (ok && dim == 2)
         ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
@@ -316,7 +322,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
     if (e == cudaSuccess)
         e = sl::launch_init_fields(m, to_dev(drift), to_dev(diffusion), to_dev(phi0), nodal_dev, c->xi, c->nodeU,
-                                   c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M, precision == SL_FP64, c->st);
+                                   c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M * ncomp, precision == SL_FP64,
+                                   c->st);  // [M][ncomp] fields of E n values, each phi0
     sl::ctx_free(c, nodal_dev);
     if (e != cudaSuccess || refresh_bounds(c) != SL_OK) {
         cudaGetLastError();
@@ -436,6 +443,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.h = m.h[0];
             a.inv_w2 = c->inv_w2;
             a.periodic = c->periodic;
+            a.ncomp = c->ncomp;
             a.ghost = c->periodic ? nullptr : c->ghost + 2 * (c->step - c->ghost_base);
             a.xi = c->xi;
             a.nodeU = c->nodeU;
@@ -494,7 +502,7 @@ int sl_reseed(sl_ctx *c)
 {
     if (!c) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const long long V = (long long)c->m.E * c->m.n;
+    const long long V = c->vals;  // values per sample (components x nodes)
     const int dbl = c->precision == SL_FP64;
     if (sl::launch_moments(c->Q, dbl, c->M, V, c->mom_chunk, c->psum, c->psq, c->mean_tmp, nullptr, c->st) !=
             cudaSuccess ||
@@ -550,7 +558,7 @@ int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2)
 {
     if (!c || !d_mean) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const long long V = (long long)c->m.E * c->m.n;
+    const long long V = c->vals;  // values per sample (components x nodes)
     if (sl::launch_moments(c->Q, c->precision == SL_FP64, c->M, V, c->mom_chunk, c->psum, c->psq, d_mean, d_m2,
                            c->st) != cudaSuccess)
         return fail_cuda(c);
@@ -562,7 +570,7 @@ int sl_pdf_device(sl_ctx *c, int nbins, double lo, double hi, unsigned int *d_co
     if (!c || !d_counts || nbins < 1 || nbins > 4096 || !std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo))
         return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const long long V = (long long)c->m.E * c->m.n;
+    const long long V = c->vals;  // values per sample (components x nodes)
     if (sl::launch_pdf(c->Q, c->precision == SL_FP64, c->M, V, nbins, lo, hi, d_counts, c->st) != cudaSuccess)
         return fail_cuda(c);
     return SL_OK;
@@ -572,7 +580,7 @@ int sl_pdf(sl_ctx *c, int nbins, double lo, double hi, unsigned int *counts)
 {
     if (!c || !counts || nbins < 1 || nbins > 4096) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const size_t bytes = size_t(c->m.E) * c->m.n * nbins * sizeof(unsigned int);
+    const size_t bytes = size_t(c->vals) * nbins * sizeof(unsigned int);
     unsigned int *d = nullptr;
     if (sl::ctx_alloc(c, reinterpret_cast<void **>(&d), bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -590,7 +598,7 @@ int sl_moments(sl_ctx *c, double *mean, double *m2)
 {
     if (!c || !mean) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const long long V = (long long)c->m.E * c->m.n;
+    const long long V = c->vals;  // values per sample (components x nodes)
     int rc = sl_moments_device(c, c->mean_tmp, m2 ? c->m2_tmp : nullptr);
     if (rc != SL_OK) return rc;
     if (cudaMemcpyAsync(mean, c->mean_tmp, V * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
@@ -604,7 +612,7 @@ int sl_get_samples(sl_ctx *c, int s0, int count, double *out)
 {
     if (!c || !out || s0 < 0 || count < 0 || s0 + count > c->M) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const size_t V = size_t(c->m.E) * c->m.n;
+    const size_t V = size_t(c->vals);  // values per sample (components x nodes)
     const size_t n = V * count;
     if (c->precision == SL_FP64) {
         if (cudaMemcpyAsync(out, static_cast<double *>(c->Q) + V * s0, n * sizeof(double), cudaMemcpyDeviceToHost,
@@ -625,7 +633,7 @@ int sl_set_samples(sl_ctx *c, int s0, int count, const double *in)
 {
     if (!c || !in || s0 < 0 || count < 0 || s0 + count > c->M) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
-    const size_t V = size_t(c->m.E) * c->m.n;
+    const size_t V = size_t(c->vals);  // values per sample (components x nodes)
     const size_t n = V * count;
     cudaError_t e;
     if (c->precision == SL_FP64) {

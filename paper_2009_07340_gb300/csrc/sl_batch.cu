@@ -124,7 +124,8 @@ sl::Step1DArgs args1d(const sl_ctx *c, double dt, int steps)
     a.dt = dt;
     a.h = c->m.h[0];
     a.inv_w2 = c->inv_w2;
-    a.periodic = 1;  // batches hold periodic instances only
+    a.periodic = 1;  // batches hold periodic, single-field instances only
+    a.ncomp = 1;
     a.ghost = nullptr;
     a.xi = c->xi;
     a.nodeU = c->nodeU;
@@ -318,7 +319,7 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
             sl_batch_free(b);
             return SL_ERR_ARG;
         }
-        if (s.mesh.dim == 1 && !s.mesh.periodic[0]) {  // Dirichlet instances run alone (sl_init)
+        if ((s.mesh.dim == 1 && !s.mesh.periodic[0]) || (opt && opt->components > 1)) {  // these run alone (sl_init)
             sl_batch_free(b);
             return SL_ERR_UNSUPPORTED;
         }

@@ -39,6 +39,7 @@ struct Step1DArgs {
     double dt, h;
     double inv_w2;         // 1 / w^2 of the boundary rows (0: hard constraints)
     int periodic;          // 0: Dirichlet boundaries with the ghost values below
+    int ncomp;             // scalar fields per sample (1 or 2), state [M][ncomp][K][N]
     const double *ghost;   // [nsteps][2] boundary values at x = lo, hi after each step (Dirichlet)
     const double *xi;      // [N] reference nodes on [0,1]
     const double *nodeU;   // [K][N] drift at the nodes
@@ -197,6 +198,8 @@ struct sl_ctx {
     double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)
     int periodic = 1;             // 0: 1D Dirichlet boundaries
+    int ncomp = 1;                // scalar fields per sample (state [M][ncomp][E][n])
+    long long vals = 0;           // values per sample: ncomp E n
     int reseed_every = 0;         // > 0: samples set to their mean after every such step count
     double *ghost = nullptr;      // device [ghost_cap][2] boundary values (Dirichlet)
     long long ghost_cap = 0, ghost_base = 0, ghost_count = 0;  // rows, first step, steps covered

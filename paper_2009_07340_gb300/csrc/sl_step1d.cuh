@@ -129,7 +129,12 @@ __device__ __forceinline__ void load_row(const double *src, double (&z)[NP])
     }
 }
 
-template <int N, int MODE>
+// NCOMP scalar fields per sample share the particles and so the advance, the
+// weights, the advected face basis, the upwind choice and the capacitance
+// factor (Section 5.3: the remap cost does not grow with the number of
+// components); the compositional update, face values, jumps, mu and the
+// final evaluation are per component.  State layout [M][NCOMP][K][N].
+template <int N, int MODE, int NCOMP>
 __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
 {
     using R = typename Prec1D<MODE>::R;
@@ -143,8 +148,8 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
     constexpr int NP = (N + 3) & ~3;            // padded row of the Z table
     // face pairs first (8-byte aligned for any S, T), then the 16-byte
     // aligned Z table (4 S T faces of 8 bytes = a multiple of 32 bytes)
-    FaceT *sface = reinterpret_cast<FaceT *>(smem_raw);           // [2 buf][2 side][S][T]
-    R *sZ = reinterpret_cast<R *>(smem_raw + sizeof(FaceT) * 4 * S * T);  // [N][NP] zeta_i - zeta_m
+    FaceT *sface = reinterpret_cast<FaceT *>(smem_raw);           // [2 buf][2 side][NCOMP][S][T]
+    R *sZ = reinterpret_cast<R *>(smem_raw + sizeof(FaceT) * 4 * NCOMP * S * T);  // [N][NP] zeta_i - zeta_m
     R *sal = sZ + N * NP;                      // [N][T] 4 u dt / h
     R *sbe = sal + N * T;                      // [N][T] 4 b / h
     R *sga = sbe + N * T;                      // [N][T] dt du/dx
@@ -194,22 +199,27 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
     const bool active = sl < S && kl < Kc && s < a.M;
 
     State *Qg = reinterpret_cast<State *>(a.Q);
-    R Q[N], Ql[N];  // state (hi part in Q; lo part used by the pair modes only)
+    R Q[NCOMP][N], Ql[NCOMP][N];  // state (hi part in Q; lo part used by the pair modes only)
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        Q[j] = R(0);
-        Ql[j] = R(0);
-    }
-    if (active) {
-        const State *src = Qg + ((long long)s * K + (k0 + kl)) * N;
+    for (int cc = 0; cc < NCOMP; ++cc)
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            if constexpr (kPair) {
-                const float2 v = src[j];
-                Q[j] = v.x;
-                Ql[j] = v.y;
-            } else {
-                Q[j] = src[j];
+            Q[cc][j] = R(0);
+            Ql[cc][j] = R(0);
+        }
+    if (active) {
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) {
+            const State *src = Qg + (((long long)s * NCOMP + cc) * K + (k0 + kl)) * N;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if constexpr (kPair) {
+                    const float2 v = src[j];
+                    Q[cc][j] = v.x;
+                    Ql[cc][j] = v.y;
+                } else {
+                    Q[cc][j] = src[j];
+                }
             }
         }
     }
@@ -250,14 +260,21 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
         // advance (Eq. def_dx) and compositional update (Eq. advection_phi)
         // every value enters relative to c = Q_ref (the middle node's state):
         // ph_j = phi*_j - c = (Q_j - c) - (dt du/dx)_j Q_j
-        R dl[N], ph[N];
-        const R ch = Q[N / 2], cl = Ql[N / 2];
+        R dl[N], ph[NCOMP][N], ch[NCOMP], cl[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) {
+            ch[cc] = Q[cc][N / 2];
+            cl[cc] = Ql[cc][N / 2];
+        }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             dl[j] = fma(sbe[j * T + kl], dWr, sal[j * T + kl]);
-            R dq = Q[j] - ch;
-            if constexpr (kPair) dq += Ql[j] - cl;
-            ph[j] = fma(-sga[j * T + kl], Q[j], dq);
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                R dq = Q[cc][j] - ch[cc];
+                if constexpr (kPair) dq += Ql[cc][j] - cl[cc];
+                ph[cc][j] = fma(-sga[j * T + kl], Q[cc][j], dq);
+            }
         }
 
         // barycentric weights of the advected nodes
@@ -292,7 +309,9 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
 
         // advected basis at the two faces and the face values
         R E0[N], E1[N];
-        R e0 = R(0), e1 = R(0);
+        R e0[NCOMP], e1[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) e0[cc] = e1[cc] = R(0);
         {
             R pre[N];
             pre[0] = R(1);
@@ -314,28 +333,36 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
                 suf *= sF1[j] - dl[j];
             }
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                e0 = fma(ph[j], E0[j], e0);  // face values relative to c
-                e1 = fma(ph[j], E1[j], e1);
-            }
+            for (int cc = 0; cc < NCOMP; ++cc)
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    e0[cc] = fma(ph[cc][j], E0[j], e0[cc]);  // face values relative to c
+                    e1[cc] = fma(ph[cc][j], E1[j], e1[cc]);
+                }
         }
-        FaceT f0, f1;  // absolute face values
-        if constexpr (kPair) {
-            two_sum(ch, e0, f0.x, f0.y);
-            f0.y += cl;
-            two_sum(ch, e1, f1.x, f1.y);
-            f1.y += cl;
-        } else {
-            f0 = ch + e0;
-            f1 = ch + e1;
+        FaceT f0[NCOMP], f1[NCOMP];  // absolute face values
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) {
+            if constexpr (kPair) {
+                two_sum(ch[cc], e0[cc], f0[cc].x, f0[cc].y);
+                f0[cc].y += cl[cc];
+                two_sum(ch[cc], e1[cc], f1[cc].x, f1[cc].y);
+                f1[cc].y += cl[cc];
+            } else {
+                f0[cc] = ch[cc] + e0[cc];
+                f1[cc] = ch[cc] + e1[cc];
+            }
         }
 
         const int buf = t & 1;
-        FaceT *fL = sface + (buf * 2 + 0) * S * T;  // value at xi = 0 of each element
-        FaceT *fR = sface + (buf * 2 + 1) * S * T;  // value at xi = 1
+        FaceT *fL = sface + (buf * 2 + 0) * NCOMP * S * T;  // value at xi = 0 of each element, [NCOMP][S][T]
+        FaceT *fR = sface + (buf * 2 + 1) * NCOMP * S * T;  // value at xi = 1
         if (sl < S) {
-            fL[sbase + kl] = f0;
-            fR[sbase + kl] = f1;
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                fL[cc * S * T + sbase + kl] = f0[cc];
+                fR[cc * S * T + sbase + kl] = f1[cc];
+            }
         }
         if (C > 1)
             cluster.sync();
@@ -344,7 +371,7 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
 
         // upwind interface values (Eq. bnd_update): at interface f take the
         // left element's value when u dt + sqrt(2D) dW > 0
-        FaceT gL, gR;
+        FaceT gL[NCOMP], gR[NCOMP];
         {
             R sigL, sigR;
             if constexpr (sizeof(R) == 8) {  // same operation order as the definition
@@ -354,24 +381,27 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
                 sigL = fmaf(sfb[kl], dWr, sfa[kl]);
                 sigR = fmaf(sfb[kl + 1], dWr, sfa[kl + 1]);
             }
-            FaceT left_e1, right_e0;
-            if (C > 1) {
-                left_e1 = *cluster.map_shared_rank(fR + lnb_idx, lnb_rank);
-                right_e0 = *cluster.map_shared_rank(fL + rnb_idx, rnb_rank);
-            } else {
-                left_e1 = fR[sbase + lnb_idx];
-                right_e0 = fL[sbase + rnb_idx];
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                FaceT left_e1, right_e0;
+                if (C > 1) {
+                    left_e1 = *cluster.map_shared_rank(fR + cc * S * T + lnb_idx, lnb_rank);
+                    right_e0 = *cluster.map_shared_rank(fL + cc * S * T + rnb_idx, rnb_rank);
+                } else {
+                    left_e1 = fR[cc * S * T + sbase + lnb_idx];
+                    right_e0 = fL[cc * S * T + sbase + rnb_idx];
+                }
+                if (!a.periodic) {  // a domain boundary: the ghost value takes the missing neighbour's place
+                    if (k0 + kl == 0) left_e1 = ghost_face<FaceT>(a.ghost[2 * t + 0]);
+                    if (k0 + kl == K - 1) right_e0 = ghost_face<FaceT>(a.ghost[2 * t + 1]);
+                }
+                gL[cc] = sigL > R(0) ? left_e1 : f0[cc];
+                gR[cc] = sigR > R(0) ? f1[cc] : right_e0;
             }
-            if (!a.periodic) {  // a domain boundary: the ghost value takes the missing neighbour's place
-                if (k0 + kl == 0) left_e1 = ghost_face<FaceT>(a.ghost[2 * t + 0]);
-                if (k0 + kl == K - 1) right_e0 = ghost_face<FaceT>(a.ghost[2 * t + 1]);
-            }
-            gL = sigL > R(0) ? left_e1 : f0;
-            gR = sigR > R(0) ? f1 : right_e0;
         }
 
         // 2x2 capacitance solve: (I + E E^T) mu = E phi* - g
-        R mu0, mu1;
+        R mu0[NCOMP], mu1[NCOMP];
         {
             R g00 = R(0), g01 = R(0), g11 = R(0);
 #pragma unroll
@@ -382,55 +412,70 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
             }
             // I / w^2 + E E^T (w = 1 unless the caller weights the boundary rows)
             const Fac G00 = Fac(a.inv_w2) + Fac(g00), G01 = Fac(g01), G11 = Fac(a.inv_w2) + Fac(g11);
-            Fac r0, r1;  // jumps E phi* - g
-            if constexpr (kPair) {
-                r0 = Fac((f0.x - gL.x) + (f0.y - gL.y));
-                r1 = Fac((f1.x - gR.x) + (f1.y - gR.y));
-            } else {
-                r0 = f0 - gL;
-                r1 = f1 - gR;
-            }
             const Fac det = G00 * G11 - G01 * G01;
             const Fac idet = Fac(1) / det;
-            const Fac m0 = (G11 * r0 - G01 * r1) * idet;
-            const Fac m1 = (G00 * r1 - G01 * r0) * idet;
-            mu0 = R(m0);
-            mu1 = R(m1);
-            bad |= !(det > Fac(0)) || !isfinite(m0) || !isfinite(m1);
+            bad |= !(det > Fac(0));
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                Fac r0, r1;  // jumps E phi* - g
+                if constexpr (kPair) {
+                    r0 = Fac((f0[cc].x - gL[cc].x) + (f0[cc].y - gL[cc].y));
+                    r1 = Fac((f1[cc].x - gR[cc].x) + (f1[cc].y - gR[cc].y));
+                } else {
+                    r0 = f0[cc] - gL[cc];
+                    r1 = f1[cc] - gR[cc];
+                }
+                const Fac m0 = (G11 * r0 - G01 * r1) * idet;
+                const Fac m1 = (G00 * r1 - G01 * r0) * idet;
+                mu0[cc] = R(m0);
+                mu1[cc] = R(m1);
+                bad |= !isfinite(m0) || !isfinite(m1);
+            }
         }
 
         // q_i = c + sum_j (phi*_j - c - E0_j mu0 - E1_j mu1) h*_j(xi_i)
 #pragma unroll
-        for (int j = 0; j < N; ++j) ph[j] = (ph[j] - fma(E0[j], mu0, E1[j] * mu1)) * w[j];
+        for (int cc = 0; cc < NCOMP; ++cc)
+#pragma unroll
+            for (int j = 0; j < N; ++j) ph[cc][j] = (ph[cc][j] - fma(E0[j], mu0[cc], E1[j] * mu1[cc])) * w[j];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             R z[NP];
             load_row<NP>(sZ + i * NP, z);
-            R A = ph[0];
+            R A[NCOMP];
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) A[cc] = ph[cc][0];
             R P = z[0] - dl[0];
 #pragma unroll
             for (int k = 1; k < N; ++k) {
                 const R d = z[k] - dl[k];
-                A = fma(A, d, ph[k] * P);
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) A[cc] = fma(A[cc], d, ph[cc][k] * P);
                 if (k + 1 < N) P *= d;
             }
-            if constexpr (kPair) {
-                two_sum(ch, A, Q[i], Ql[i]);
-                Ql[i] += cl;
-            } else {
-                Q[i] = ch + A;
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                if constexpr (kPair) {
+                    two_sum(ch[cc], A[cc], Q[cc][i], Ql[cc][i]);
+                    Ql[cc][i] += cl[cc];
+                } else {
+                    Q[cc][i] = ch[cc] + A[cc];
+                }
             }
         }
     }
 
     if (active) {
-        State *dst = Qg + ((long long)s * K + (k0 + kl)) * N;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            if constexpr (kPair)
-                dst[j] = make_float2(Q[j], Ql[j]);
-            else
-                dst[j] = Q[j];
+        for (int cc = 0; cc < NCOMP; ++cc) {
+            State *dst = Qg + (((long long)s * NCOMP + cc) * K + (k0 + kl)) * N;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if constexpr (kPair)
+                    dst[j] = make_float2(Q[cc][j], Ql[cc][j]);
+                else
+                    dst[j] = Q[cc][j];
+            }
         }
         if (bad) atomicOr(a.err, 1);
     }
@@ -442,7 +487,14 @@ __device__ __forceinline__ void step1d_body(const Step1DArgs &a, const int slot)
 template <int N, int MODE>
 __global__ void __launch_bounds__(kMaxThreads1D, MODE == SL_FP64 ? 1 : SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel(const Step1DArgs a)
 {
-    step1d_body<N, MODE>(a, int(blockIdx.x) / a.C);
+    step1d_body<N, MODE, 1>(a, int(blockIdx.x) / a.C);
+}
+
+// Two scalar fields per sample sharing the remap factorization.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kMaxThreads1D, MODE == SL_FP64 ? 1 : SL1D_FP32_MIN_BLOCKS) sl1d_step_kernel_c2(const Step1DArgs a)
+{
+    step1d_body<N, MODE, 2>(a, int(blockIdx.x) / a.C);
 }
 
 // Persistent batched launch over many instances of one order N (K <= 256,
@@ -468,24 +520,24 @@ __global__ void __launch_bounds__(kMaxThreads1D, MODE == SL_FP64 ? 1 : SL1D_FP32
             else hi = mid - 1;
         }
         const Step1DArgs ai = args[lo];
-        step1d_body<N, MODE>(ai, item - item_prefix[lo]);
+        step1d_body<N, MODE, 1>(ai, item - item_prefix[lo]);
         __syncthreads();  // shared tables of this item are dead before the next fill
     }
 }
 
 template <int MODE>
-size_t step1d_smem_bytes_t(int N, int S, int T)
+size_t step1d_smem_bytes_t(int N, int S, int T, int ncomp = 1)
 {
     using R = typename Prec1D<MODE>::R;
     const int NP = (N + 3) & ~3;
-    return sizeof(R) * (size_t(N) * NP + size_t(3) * N * T + 2 * N + 2 * (T + 1)) + size_t(8) * 4 * S * T;
+    return sizeof(R) * (size_t(N) * NP + size_t(3) * N * T + 2 * N + 2 * (T + 1)) + size_t(8) * 4 * ncomp * S * T;
 }
 
 template <int N, int MODE>
 cudaError_t launch_step1d_n(const Step1DArgs &a, cudaStream_t st)
 {
-    const size_t smem = step1d_smem_bytes_t<MODE>(N, a.S, a.T);
-    auto kern = sl1d_step_kernel<N, MODE>;
+    const size_t smem = step1d_smem_bytes_t<MODE>(N, a.S, a.T, a.ncomp);
+    auto kern = a.ncomp == 2 ? sl1d_step_kernel_c2<N, MODE> : sl1d_step_kernel<N, MODE>;
     cudaLaunchConfig_t cfg = {};
     const int slots = (a.M + a.S - 1) / a.S;
     cfg.gridDim = dim3(unsigned(slots * a.C));
@@ -567,6 +619,7 @@ cudaError_t preload_step1d_seq(std::integer_sequence<int, I...>)
         if (e == cudaSuccess) e = prepare_kernel(f);
     };
     (one(sl1d_step_kernel<I + 2, MODE>), ...);
+    (one(sl1d_step_kernel_c2<I + 2, MODE>), ...);
     (one(sl1d_step_kernel_batch<I + 2, MODE>), ...);
     return e;
 }
