@@ -327,8 +327,10 @@ def dt_edge(pb):
 def run(pb, nsteps=None, step0=0, s0=0, ns=None, nthreads=1, state_in=None,
         want_states=False, want_sums=True, dt=None, ghost=None):
     """Run samples [s0, s0+ns) through steps [step0, step0+nsteps).
-    ghost: [nsteps][2] Dirichlet values at x = lo, hi after each step (1D,
-    pb["periodic"] False; default pb["ghost"] when present).
+    ghost: [nsteps][width] Dirichlet values after each step (pb["periodic"]
+    False; default pb["ghost"] when present): 1D x = lo, hi (width 2); 2D the
+    face points of the left, right, bottom and top boundaries (width
+    2 (Kx + Ky) N).
 
     Returns dict with 'states' ([ns][E][n], if asked) and 'sum', 'sumsq'
     ([E][n], sums over the ns samples)."""
@@ -342,7 +344,8 @@ def run(pb, nsteps=None, step0=0, s0=0, ns=None, nthreads=1, state_in=None,
     sq = np.zeros((E, n)) if want_sums else None
     if ghost is None:
         ghost = pb.get("ghost")
-    gh = None if ghost is None else np.ascontiguousarray(np.asarray(ghost, dtype=np.float64).reshape(-1, 2)[:nsteps])
+    width = 2 if pb["dim"] == 1 else 2 * (pb["K"][0] + pb["K"][1]) * pb["N"]
+    gh = None if ghost is None else np.ascontiguousarray(np.asarray(ghost, dtype=np.float64).reshape(-1, width)[:nsteps])
     if gh is not None and gh.shape[0] < nsteps:
         raise ValueError("ghost values cover fewer steps than the run")
     rc = lib().orc_run(C.byref(p), step0, nsteps, s0, ns, nthreads, _dp(gh), _dp(sin), _dp(st), _dp(sm), _dp(sq))

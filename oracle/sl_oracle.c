@@ -708,8 +708,10 @@ typedef struct {
     double *afx, *bfx;   /* [Ky][Kx][N(2D) or 1] vertical faces: u_x dt, sqrt(2D) */
     double *afy, *bfy;   /* [Ky][Kx][N] horizontal faces (2D)                 */
     double omega;        /* boundary-row weight of the remap                  */
-    int periodic;        /* 0: Dirichlet boundaries (1D)                      */
+    int periodic;        /* 0: Dirichlet boundaries                           */
     double afx_hi, bfx_hi; /* 1D: u dt and sqrt(2D) at the right boundary x = hi */
+    double *afx_hi2, *bfx_hi2; /* 2D: [Ky][N] u_x dt, sqrt(2D) on the face x = hi */
+    double *afy_hi2, *bfy_hi2; /* 2D: [Kx][N] u_y dt, sqrt(2D) on the face y = hi */
 } orc_coeffs;
 
 static void orc_coeffs_free(orc_coeffs *cf)
@@ -724,6 +726,10 @@ static void orc_coeffs_free(orc_coeffs *cf)
     free(cf->bfx);
     free(cf->afy);
     free(cf->bfy);
+    free(cf->afx_hi2);
+    free(cf->bfx_hi2);
+    free(cf->afy_hi2);
+    free(cf->bfy_hi2);
 }
 
 /* Node (x, y) of node p in element e. */
@@ -823,6 +829,25 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
         orc_drift(pb, pb->hi[0], 0.0, u);
         cf->afx_hi = u[0] * pb->dt;
         cf->bfx_hi = sqrt(2.0 * orc_diffusion(pb, pb->hi[0], 0.0));
+    } else {
+        cf->afx_hi2 = (double *)calloc((size_t)cf->Ky * N, sizeof(double));
+        cf->bfx_hi2 = (double *)calloc((size_t)cf->Ky * N, sizeof(double));
+        cf->afy_hi2 = (double *)calloc((size_t)cf->Kx * N, sizeof(double));
+        cf->bfy_hi2 = (double *)calloc((size_t)cf->Kx * N, sizeof(double));
+        for (int ky = 0; ky < cf->Ky; ++ky)
+            for (int f = 0; f < N; ++f) { /* x = hi at the Gauss nodes of row ky */
+                double u[2], yf = pb->lo[1] + (ky + cf->xi[f]) * cf->hy;
+                orc_drift(pb, pb->hi[0], yf, u);
+                cf->afx_hi2[ky * N + f] = u[0] * pb->dt;
+                cf->bfx_hi2[ky * N + f] = sqrt(2.0 * orc_diffusion(pb, pb->hi[0], yf));
+            }
+        for (int kx = 0; kx < cf->Kx; ++kx)
+            for (int f = 0; f < N; ++f) { /* y = hi at the Gauss nodes of column kx */
+                double u[2], xf = pb->lo[0] + (kx + cf->xi[f]) * cf->hx;
+                orc_drift(pb, xf, pb->hi[1], u);
+                cf->afy_hi2[kx * N + f] = u[1] * pb->dt;
+                cf->bfy_hi2[kx * N + f] = sqrt(2.0 * orc_diffusion(pb, xf, pb->hi[1]));
+            }
     }
     free(ux);
     free(uy);
@@ -904,7 +929,12 @@ static int orc_step_1d(const orc_coeffs *cf, double dt, double dW, const double 
     return rc;
 }
 
-static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], double *Q)
+/* One SL step of one 2D sample.  ghost (Dirichlet only): boundary values at */
+/* the face points after the step, [left Ky][N] (x = lo), [right Ky][N]       */
+/* (x = hi), [bottom Kx][N] (y = lo), [top Kx][N] (y = hi), each at the Gauss */
+/* nodes along the face; they take the place of the missing neighbour in the */
+/* upwind rule.                                                              */
+static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], const double *ghost, double *Q)
 {
     int N = cf->N, n = cf->n, Kx = cf->Kx, Ky = cf->Ky, E = cf->E;
     double *dx = (double *)malloc(sizeof(double) * E * n);
@@ -914,6 +944,11 @@ static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], doub
     double *gv = (double *)malloc(sizeof(double) * E * N); /* vertical face at low x of e */
     double *gh = (double *)malloc(sizeof(double) * E * N); /* horizontal face at low y of e */
     double *g = (double *)malloc(sizeof(double) * 4 * N);
+    double *gvR = (double *)malloc(sizeof(double) * Ky * N); /* x = hi interface (Dirichlet) */
+    double *ghT = (double *)malloc(sizeof(double) * Kx * N); /* y = hi interface (Dirichlet) */
+    const int dir = !cf->periodic;
+    const double *gL = dir ? ghost : NULL, *gR = dir ? ghost + Ky * N : NULL;
+    const double *gB = dir ? ghost + 2 * Ky * N : NULL, *gT = dir ? ghost + 2 * Ky * N + Kx * N : NULL;
     int rc = 0;
     for (int e = 0; e < E; ++e)
         for (int p = 0; p < n; ++p) {
@@ -930,12 +965,27 @@ static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], doub
             int eB = ((ky - 1 + Ky) % Ky) * Kx + kx; /* lower neighbour */
             for (int f = 0; f < N; ++f) {
                 double sx = cf->afx[e * N + f] + cf->bfx[e * N + f] * dW[0];
-                gv[e * N + f] = sx > 0.0 ? faces[eL * 4 * N + N + f] : faces[e * 4 * N + f];
+                double left = (dir && kx == 0) ? gL[ky * N + f] : faces[eL * 4 * N + N + f];
+                gv[e * N + f] = sx > 0.0 ? left : faces[e * 4 * N + f];
                 double sy = cf->afy[e * N + f] + cf->bfy[e * N + f] * dW[1];
-                gh[e * N + f] =
-                    sy > 0.0 ? faces[eB * 4 * N + 3 * N + f] : faces[e * 4 * N + 2 * N + f];
+                double below = (dir && ky == 0) ? gB[kx * N + f] : faces[eB * 4 * N + 3 * N + f];
+                gh[e * N + f] = sy > 0.0 ? below : faces[e * 4 * N + 2 * N + f];
             }
         }
+    if (dir) {
+        for (int ky = 0; ky < Ky; ++ky)
+            for (int f = 0; f < N; ++f) {
+                int e = ky * Kx + Kx - 1;
+                double sx = cf->afx_hi2[ky * N + f] + cf->bfx_hi2[ky * N + f] * dW[0];
+                gvR[ky * N + f] = sx > 0.0 ? faces[e * 4 * N + N + f] : gR[ky * N + f];
+            }
+        for (int kx = 0; kx < Kx; ++kx)
+            for (int f = 0; f < N; ++f) {
+                int e = (Ky - 1) * Kx + kx;
+                double sy = cf->afy_hi2[kx * N + f] + cf->bfy_hi2[kx * N + f] * dW[1];
+                ghT[kx * N + f] = sy > 0.0 ? faces[e * 4 * N + 3 * N + f] : gT[kx * N + f];
+            }
+    }
     for (int ky = 0; ky < Ky && rc == 0; ++ky)
         for (int kx = 0; kx < Kx && rc == 0; ++kx) {
             int e = ky * Kx + kx;
@@ -943,9 +993,9 @@ static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], doub
             int eT = ((ky + 1) % Ky) * Kx + kx;
             for (int f = 0; f < N; ++f) {
                 g[f] = gv[e * N + f];
-                g[N + f] = gv[eR * N + f];
+                g[N + f] = (dir && kx == Kx - 1) ? gvR[ky * N + f] : gv[eR * N + f];
                 g[2 * N + f] = gh[e * N + f];
-                g[3 * N + f] = gh[eT * N + f];
+                g[3 * N + f] = (dir && ky == Ky - 1) ? ghT[kx * N + f] : gh[eT * N + f];
             }
             rc = orc_remap_2d_split_w(N, cf->xi, dx + e * n, dy + e * n, phs + e * n, g, cf->omega, Q + e * n);
         }
@@ -956,6 +1006,8 @@ static int orc_step_2d(const orc_coeffs *cf, double dt, const double dW[2], doub
     free(gv);
     free(gh);
     free(g);
+    free(gvR);
+    free(ghT);
     return rc;
 }
 
@@ -975,6 +1027,9 @@ typedef struct {
     int rc;
 } orc_job;
 
+/* Boundary values per step: 2 in 1D (x = lo, hi), 2 (Kx + Ky) N in 2D.    */
+static int orc_ghost_width(const orc_coeffs *cf) { return cf->dim == 1 ? 2 : 2 * (cf->Kx + cf->Ky) * cf->N; }
+
 static void *orc_worker(void *arg)
 {
     orc_job *jb = (orc_job *)arg;
@@ -993,8 +1048,8 @@ static void *orc_worker(void *arg)
             orc_normals(jb->pb->seed, (uint32_t)(jb->step0 + t), (uint32_t)s, 0u, z);
             dW[0] = sdt * z[0];
             dW[1] = sdt * z[1];
-            jb->rc = cf->dim == 1 ? orc_step_1d(cf, jb->pb->dt, dW[0], jb->ghost ? jb->ghost + 2 * t : NULL, Q)
-                                  : orc_step_2d(cf, jb->pb->dt, dW, Q);
+            const double *gt = jb->ghost ? jb->ghost + (size_t)orc_ghost_width(cf) * t : NULL;
+            jb->rc = cf->dim == 1 ? orc_step_1d(cf, jb->pb->dt, dW[0], gt, Q) : orc_step_2d(cf, jb->pb->dt, dW, gt, Q);
         }
         if (jb->state_out) memcpy(jb->state_out + (size_t)(s - jb->s0) * sz, Q, sizeof(double) * sz);
         if (jb->sum)
@@ -1066,8 +1121,9 @@ static int orc_run_segment(const orc_problem *pb, const orc_coeffs *cf, const do
 /* Runs samples [s0, s0+ns).  state_in ([ns][E][n]) or NULL for phi0;       */
 /* state_out ([ns][E][n]) may be NULL; sum and sumsq ([E][n]) may be NULL and */
 /* receive sum_s Q and sum_s Q^2, threads' partials added in thread order,  */
-/* each thread in ascending sample order.  ghost: [nsteps][2] boundary      */
-/* values at x = lo, hi after each step (1D Dirichlet; NULL when periodic).  */
+/* each thread in ascending sample order.  ghost: [nsteps][width] boundary  */
+/* values after each step (Dirichlet; NULL when periodic): 1D x = lo, hi;    */
+/* 2D left, right, bottom, top faces (see orc_step_2d).                      */
 /* With reseed_every > 0 the run stops after each step n with               */
 /* (n + 1) % reseed_every == 0 and sets every sample to the mean of the ns  */
 /* samples (summed in ascending sample order), Eq. re-seed.  Returns 0/-1.  */
@@ -1076,7 +1132,7 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
 {
     if (pb->dim < 1 || pb->dim > 2 || pb->N < 2 || ns < 0 || nsteps < 0 || pb->dt < 0.0) return -1;
     if (pb->dim == 2 && isinf(pb->omega)) return -1; /* hard constraints: 1D only */
-    if (!pb->periodic && (pb->dim != 1 || !ghost)) return -1; /* Dirichlet: 1D, with boundary values */
+    if (!pb->periodic && !ghost) return -1; /* Dirichlet: boundary values needed */
     if (pb->reseed_every < 0) return -1;
     orc_coeffs cf;
     if (orc_build_coeffs(pb, &cf) != 0) return -1;
@@ -1097,7 +1153,7 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
             long seg = R - (step0 + t) % R; /* steps up to and including the next reseed step */
             if (seg > nsteps - t) seg = nsteps - t;
             rc = orc_run_segment(pb, &cf, phi0, step0 + t, (int)seg, s0, ns, nthreads,
-                                 pb->periodic ? NULL : ghost + 2 * t, cur, nxt, NULL, NULL);
+                                 pb->periodic ? NULL : ghost + (size_t)orc_ghost_width(&cf) * t, cur, nxt, NULL, NULL);
             double *tmp = cur;
             cur = nxt;
             nxt = tmp;

@@ -344,3 +344,55 @@ def test_reseed_sets_every_sample_to_the_mean(orc):
     plain = orc.run(I.with_(pb, steps=20), want_states=True, state_in=state0)
     reseeded = orc.run(I.with_(pb, steps=20, reseed_every=20), want_states=True, state_in=state0)
     assert np.allclose(reseeded["states"][0], plain["states"].mean(axis=0), rtol=0, atol=1e-15)
+
+
+def _ghost_2d(orc, K, N, L, fn, times):
+    """Boundary values at the face points after each step: left (x = lo),
+    right (x = hi), bottom (y = lo), top (y = hi), each along the face's Gauss
+    nodes, elements in order."""
+    pts = (np.arange(K)[:, None] + orc.nodes(N)[None, :]).ravel() * (L / K)
+    rows = []
+    for t in times:
+        rows.append(np.concatenate([fn(0 * pts, pts, t), fn(L + 0 * pts, pts, t), fn(pts, 0 * pts, t),
+                                    fn(pts, L + 0 * pts, t)]))
+    return np.array(rows)
+
+
+def test_dirichlet_2d_inflow_pure_advection(orc):
+    # constant drift (0.6, -0.4), no diffusion: inflow through x = lo and
+    # y = hi; the domain [0, 0.8]^2 is not a period of phi0, so the boundary
+    # values are what carries the inflow; the particle advance is exact in
+    # time, so the solution is reproduced to interpolation accuracy
+    u, v, L, K, N, dt, steps = 0.6, -0.4, 0.8, 3, 8, 2e-3, 100
+
+    def phi(x, y, t):
+        return 1.0 + 0.5 * np.sin(2 * np.pi * (x - u * t)) * np.sin(2 * np.pi * (y - v * t))
+
+    pb = I.problem(2, (K, K), (0.0, 0.0), (L, L), N, 1, steps, dt, 3, ("const", [u, v]), ("const", [0.0]),
+                   ("sinsin", [1.0, 0.5, 1.0]))
+    pb["periodic"] = False
+    ghost = _ghost_2d(orc, K, N, L, phi, dt * np.arange(1, steps + 1))
+    x, y = orc.node_coords(pb)
+    exact = phi(x, y, steps * dt)
+    assert np.abs(orc.run(pb, ns=1, ghost=ghost)["sum"] - exact).max() <= 2e-7
+    assert np.abs(orc.run(pb, ns=1, ghost=0 * ghost)["sum"] - exact).max() > 0.1
+
+
+def test_dirichlet_2d_sine_diffusion_within_standard_error(orc):
+    # the paper's 2D sine diffusion test: D = 1, phi0 = 2 + sin 2 pi x sin 2 pi y
+    # on [0, 1]^2 with Dirichlet values from the exact mean
+    # 2 + exp(-8 pi^2 t) sin 2 pi x sin 2 pi y, dt = 1e-5, 50 steps
+    K, N, M, dt, steps = 2, 6, 400, 1e-5, 50
+
+    def mean_exact(x, y, t):
+        return 2.0 + np.exp(-8 * np.pi ** 2 * t) * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+
+    pb = I.problem(2, (K, K), (0.0, 0.0), (1.0, 1.0), N, M, steps, dt, 31, ("const", [0.0, 0.0]), ("const", [1.0]),
+                   ("sinsin", [2.0, 1.0, 1.0]))
+    pb["periodic"] = False
+    ghost = _ghost_2d(orc, K, N, 1.0, mean_exact, dt * np.arange(1, steps + 1))
+    r = orc.run(pb, nthreads=8, ghost=ghost)
+    mean, m2 = r["sum"] / M, r["sumsq"] / M
+    se = np.sqrt(np.maximum(m2 - mean ** 2, 0.0) / (M - 1)).max()
+    x, y = orc.node_coords(pb)
+    assert np.abs(mean - mean_exact(x, y, steps * dt)).max() <= 4.0 * se + 1e-3
