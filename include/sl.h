@@ -95,8 +95,8 @@ typedef struct {
     int K[2];        /* elements per direction; K[1] ignored in 1D    */
     double lo[2];
     double hi[2];
-    int periodic[2]; /* 1: periodic; 0 (1D only): Dirichlet boundaries whose values */
-                     /* the caller gives per step with sl_set_boundary              */
+    int periodic[2]; /* 1: periodic; 0: Dirichlet boundaries whose values the   */
+                     /* caller gives per step with sl_set_boundary (2D: both 0)  */
 } sl_mesh;
 
 typedef struct {
@@ -167,9 +167,13 @@ int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion);
 /* Dirichlet boundary values (1D, periodic[0] = 0), Section 5.3: at a domain */
 /* boundary the given value is the ghost solution that takes the place of   */
 /* the missing neighbour in the upwind rule (Eq. bnd_update).  values: host */
-/* [nsteps][2], the values at x = lo and x = hi at the end of each of the   */
-/* next nsteps steps (step counters n .. n + nsteps - 1 from the current    */
-/* one), copied before return.  Each call replaces the previous table;      */
+/* [nsteps][width], the values at the end of each of the next nsteps steps  */
+/* (step counters n .. n + nsteps - 1 from the current one), copied before  */
+/* return.  1D: width 2, the values at x = lo and x = hi.  2D: width        */
+/* 2 (K[0] + K[1]) N, the face points of the left boundary x = lo ([K[1]][N], */
+/* along y), the right boundary x = hi ([K[1]][N]), the bottom y = lo       */
+/* ([K[0]][N], along x) and the top y = hi ([K[0]][N]), each at the Gauss   */
+/* nodes of the boundary elements.  Each call replaces the previous table;  */
 /* sl_step returns SL_ERR_ARG for a step the table does not cover.          */
 /* SL_ERR_ARG on a periodic context.                                         */
 int sl_set_boundary(sl_ctx *c, int nsteps, const double *values);

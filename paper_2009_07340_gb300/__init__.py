@@ -489,8 +489,11 @@ class Solver:
             self.set_boundary(pb["ghost"])
 
     def set_boundary(self, values):
-        """Dirichlet values [steps][2] (x = lo, x = hi) after each of the next steps."""
-        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1, 2))
+        """Dirichlet values after each of the next steps: [steps][2] in 1D (x = lo,
+        hi); [steps][2 (Kx + Ky) N] in 2D (left, right, bottom, top face points)."""
+        pb = self.pb
+        width = 2 if pb["dim"] == 1 else 2 * (pb["K"][0] + pb["K"][1]) * pb["N"]
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1, width))
         _check(lib().sl_set_boundary(C.c_void_p(self.ctx), v.shape[0], _f64p(v)), "sl_set_boundary")
 
     def pdf(self, nbins, lo, hi):

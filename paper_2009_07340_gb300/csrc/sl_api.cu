@@ -203,6 +203,8 @@ void sl_free(sl_ctx *c)
     for (cudaEvent_t ev : c->throttle.ev)
         if (ev) cudaEventDestroy(ev);
     sl::ctx_free(c, c->ghost);
+    sl::ctx_free(c, c->faceUhi);
+    sl::ctx_free(c, c->faceBhi);
     sl::ctx_free(c, c->xi);
     sl::ctx_free(c, c->nodeU);
     sl::ctx_free(c, c->nodeB);
@@ -231,7 +233,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     for (int d = 0; d < dim; ++d) {
         if (mesh->K[d] < 1 || !(mesh->hi[d] > mesh->lo[d]) || !std::isfinite(mesh->hi[d] - mesh->lo[d]))
             return SL_ERR_ARG;
-        if (!mesh->periodic[d] && dim != 1) return SL_ERR_UNSUPPORTED;  // Dirichlet: 1D
+        if (dim == 2 && !mesh->periodic[d] != !mesh->periodic[0]) return SL_ERR_UNSUPPORTED;  // all or none
     }
     if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion) || !valid_kind(dim, 2, phi0))
         return SL_ERR_ARG;
@@ -264,7 +266,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     c->strict_dt = opt ? opt->strict_dt : 0;
     c->launch_chunk = opt && opt->launch_chunk > 0 ? opt->launch_chunk : 0;
     c->bc_weight = bc_w;
-    c->periodic = dim == 2 || mesh->periodic[0] ? 1 : 0;
+    c->periodic = mesh->periodic[0] ? 1 : 0;
+    c->ghost_w = dim == 1 ? 2 : 2 * (mesh->K[0] + mesh->K[1]) * N;
     c->reseed_every = opt ? opt->reseed_every : 0;
     c->ncomp = ncomp;
     c->inv_w2 = std::isinf(bc_w) ? 0.0 : 1.0 / (bc_w * bc_w);
@@ -302,7 +305,9 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
               dalloc(c, &c->psum, size_t(nc) * ncomp * V) == cudaSuccess &&
               dalloc(c, &c->psq, size_t(nc) * ncomp * V) == cudaSuccess &&
               dalloc(c, &c->mean_tmp, ncomp * V) == cudaSuccess && dalloc(c, &c->m2_tmp, ncomp * V) == cudaSuccess &&
-              dalloc(c, &c->err, 1) == cudaSuccess;
+              dalloc(c, &c->err, 1) == cudaSuccess &&
+              (dim == 1 || (dalloc(c, &c->faceUhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess &&
+                            dalloc(c, &c->faceBhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess));
     if (ok && dim == 2)
         ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
     if (!ok) {
@@ -324,6 +329,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
         e = sl::launch_init_fields(m, to_dev(drift), to_dev(diffusion), to_dev(phi0), nodal_dev, c->xi, c->nodeU,
                                    c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M * ncomp, precision == SL_FP64,
                                    c->st);  // [M][ncomp] fields of E n values, each phi0
+    if (e == cudaSuccess && dim == 2)
+        e = sl::launch_init_faces_hi(m, to_dev(drift), to_dev(diffusion), c->faceUhi, c->faceBhi, c->st);
     sl::ctx_free(c, nodal_dev);
     if (e != cudaSuccess || refresh_bounds(c) != SL_OK) {
         cudaGetLastError();
@@ -390,7 +397,10 @@ int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
     const cudaError_t e = sl::launch_init_fields(c->m, to_dev(drift), to_dev(diffusion), to_dev(&none), nullptr, c->xi,
                                                  c->nodeU, c->nodeB, c->nodeDiv, c->faceU, c->faceB, nullptr, c->M,
                                                  c->precision == SL_FP64, c->st);
-    if (e != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
+    cudaError_t e2 = e;
+    if (e2 == cudaSuccess && dim == 2)
+        e2 = sl::launch_init_faces_hi(c->m, to_dev(drift), to_dev(diffusion), c->faceUhi, c->faceBhi, c->st);
+    if (e2 != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
     return SL_OK;
 }
 
@@ -444,7 +454,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.inv_w2 = c->inv_w2;
             a.periodic = c->periodic;
             a.ncomp = c->ncomp;
-            a.ghost = c->periodic ? nullptr : c->ghost + 2 * (c->step - c->ghost_base);
+            a.ghost = c->periodic ? nullptr : c->ghost + c->ghost_w * (c->step - c->ghost_base);
             a.xi = c->xi;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
@@ -482,6 +492,11 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.chunk = c->launch_chunk;
             a.g0 = a.g1 = 0;
             a.w = c->bc_weight;
+            a.periodic = c->periodic;
+            a.ghost = c->periodic ? nullptr : c->ghost + c->ghost_w * (c->step - c->ghost_base);
+            a.ghost_w = c->ghost_w;
+            a.faceUhi = c->faceUhi;
+            a.faceBhi = c->faceBhi;
             a.throttle = c->launch_chunk > 0 ? &c->throttle : nullptr;
             e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
         }
@@ -520,7 +535,7 @@ int sl_set_boundary(sl_ctx *c, int nsteps, const double *values)
         sl::ctx_free(c, c->ghost);
         c->ghost = nullptr;
         c->ghost_cap = 0;
-        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&c->ghost), size_t(nsteps) * 2 * sizeof(double)) !=
+        if (sl::ctx_alloc(c, reinterpret_cast<void **>(&c->ghost), size_t(nsteps) * c->ghost_w * sizeof(double)) !=
             cudaSuccess) {
             cudaGetLastError();
             return SL_ERR_OOM;
@@ -528,7 +543,7 @@ int sl_set_boundary(sl_ctx *c, int nsteps, const double *values)
         c->ghost_cap = nsteps;
     }
     if (nsteps > 0 &&
-        (cudaMemcpyAsync(c->ghost, values, size_t(nsteps) * 2 * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
+        (cudaMemcpyAsync(c->ghost, values, size_t(nsteps) * c->ghost_w * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
              cudaSuccess ||
          cudaStreamSynchronize(c->st) != cudaSuccess))
         return fail_cuda(c);

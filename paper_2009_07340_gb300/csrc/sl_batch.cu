@@ -160,6 +160,10 @@ sl::Step2DArgs args2d(const sl_ctx *c, double dt, int steps)
     a.faces = c->faces2d;
     a.err = c->err;
     a.w = c->bc_weight;
+    a.periodic = 1;  // batches hold periodic instances only
+    a.ghost = nullptr;
+    a.ghost_w = 0;
+    a.faceUhi = a.faceBhi = nullptr;
     a.chunk = 0;  // the batched launch covers all instances' groups
     a.g0 = a.g1 = 0;
     a.throttle = nullptr;
@@ -319,7 +323,7 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
             sl_batch_free(b);
             return SL_ERR_ARG;
         }
-        if ((s.mesh.dim == 1 && !s.mesh.periodic[0]) || (opt && opt->components > 1)) {  // these run alone (sl_init)
+        if (!s.mesh.periodic[0] || (opt && opt->components > 1)) {  // these run alone (sl_init)
             sl_batch_free(b);
             return SL_ERR_UNSUPPORTED;
         }

@@ -86,6 +86,11 @@ struct Step2DArgs {
     void *faces;           // scratch [M][E][4N] face values of the advected interpolant
     int *err;
     double w;              // weight of the face rows (1 unless the caller set one)
+    int periodic;          // 0: Dirichlet boundaries on all four sides
+    const double *ghost;   // [nsteps][ghost_w] boundary values (left, right, bottom, top face points)
+    int ghost_w;           // 2 (Kx + Ky) N
+    const double *faceUhi; // [Ky][N] u_x on x = hi, then [Kx][N] u_y on y = hi (Dirichlet)
+    const double *faceBhi; // the same for sqrt(2 D)
     long long chunk;       // element-sample groups per launch (0: all in one launch)
     long long g0, g1;      // groups [g0, g1) of this launch (set by the launcher)
     LaunchThrottle *throttle;  // host object; with chunk > 0: bounded queue depth (may be null)
@@ -134,6 +139,9 @@ cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long 
 // Per-node histogram of the samples into B bins over [lo, hi] (device [V][B]).
 cudaError_t launch_pdf(const void *Q, int state_is_double, int M, long long V, int B, double lo, double hi,
                        unsigned int *counts, cudaStream_t st);
+// 2D coefficients on the faces x = hi ([Ky][N], u_x) and y = hi ([Kx][N], u_y).
+cudaError_t launch_init_faces_hi(const Mesh &m, const FieldDev &u, const FieldDev &D, double *faceUhi, double *faceBhi,
+                                 cudaStream_t st);
 // Every sample set to `mean` (Eq. re-seed).
 cudaError_t launch_reseed(void *Q, int state_is_double, int M, long long V, const double *mean, cudaStream_t st);
 
@@ -199,6 +207,8 @@ struct sl_ctx {
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)
     int periodic = 1;             // 0: 1D Dirichlet boundaries
     int ncomp = 1;                // scalar fields per sample (state [M][ncomp][E][n])
+    int ghost_w = 2;              // boundary values per step: 1D 2, 2D 2 (Kx + Ky) N
+    double *faceUhi = nullptr, *faceBhi = nullptr;  // 2D faces x = hi, y = hi
     long long vals = 0;           // values per sample: ncomp E n
     int reseed_every = 0;         // > 0: samples set to their mean after every such step count
     double *ghost = nullptr;      // device [ghost_cap][2] boundary values (Dirichlet)

@@ -147,7 +147,7 @@ __global__ void init_faces_kernel(Mesh m, FieldDev fu, FieldDev fD, double *face
     if (v >= nf) return;
     double ux, uy;
     if (m.dim == 1) {
-        const double xf = m.lo[0] + v * m.h[0];
+        const double xf = v == m.E ? m.hi[0] : m.lo[0] + v * m.h[0];  // v = E: the boundary x = hi
         drift_at(fu, xf, 0.0, ux, uy);
         faceU[v] = ux;
         faceB[v] = sqrt(2.0 * diffusion_at(fD, xf, 0.0));
@@ -288,6 +288,35 @@ __global__ void moments_final_kernel(const double *__restrict__ psum, const doub
     if (m2) m2[v] = b / M;
 }
 
+// 2D faces on the upper domain boundaries (used with Dirichlet boundaries):
+// x = hi at the Gauss nodes of each row, then y = hi at those of each column.
+__global__ void init_faces_hi_kernel(Mesh m, FieldDev fu, FieldDev fD, double *faceUhi, double *faceBhi)
+{
+    const int nx = m.K[1] * m.N, ny = m.K[0] * m.N;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nx + ny) return;
+    double x, y, ux, uy;
+    if (v < nx) {
+        x = m.hi[0];
+        y = m.lo[1] + (v / m.N + gauss_node(v % m.N, m.N)) * m.h[1];
+    } else {
+        const int w = v - nx;
+        x = m.lo[0] + (w / m.N + gauss_node(w % m.N, m.N)) * m.h[0];
+        y = m.hi[1];
+    }
+    drift_at(fu, x, y, ux, uy);
+    faceUhi[v] = v < nx ? ux : uy;
+    faceBhi[v] = sqrt(2.0 * diffusion_at(fD, x, y));
+}
+
+cudaError_t launch_init_faces_hi(const Mesh &m, const FieldDev &u, const FieldDev &D, double *faceUhi, double *faceBhi,
+                                 cudaStream_t st)
+{
+    const int total = (m.K[0] + m.K[1]) * m.N;
+    init_faces_hi_kernel<<<(total + 127) / 128, 128, 0, st>>>(m, u, D, faceUhi, faceBhi);
+    return cudaGetLastError();
+}
+
 // Histogram of the M samples at every node (recovery of the PDF by binning
 // the samples, Section 5.4): bin b = floor((x - lo) * scale), scale = B /
 // (hi - lo), in FP64; x = hi goes to the last bin; x outside [lo, hi] (or
@@ -381,6 +410,7 @@ cudaError_t preload_setup()
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
     if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(init_faces_hi_kernel);
     if (e == cudaSuccess) e = prepare_kernel(pdf_kernel<double>);
     if (e == cudaSuccess) e = prepare_kernel(pdf_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<float2>);

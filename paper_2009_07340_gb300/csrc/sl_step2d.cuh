@@ -47,6 +47,18 @@ __device__ __forceinline__ void two_sum2d(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// A boundary value as a face value: FP64, or the float pair hi + lo.
+template <typename FaceT>
+__device__ __forceinline__ FaceT ghost_face2d(double g)
+{
+    if constexpr (std::is_same<FaceT, double>::value) {
+        return g;
+    } else {
+        const float hi = float(g);
+        return make_float2(hi, float(g - double(hi)));
+    }
+}
+
 __device__ __forceinline__ void group_sync(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -258,8 +270,23 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
             else if (side == 1) e_face = ky * a.Kx + (kx + 1) % a.Kx;
             else if (side == 2) e_face = e;
             else e_face = ((ky + 1) % a.Ky) * a.Kx + kx;
+            // a face on a Dirichlet domain boundary: the ghost value takes the
+            // place of the missing neighbour (low side at x = lo / y = lo, high
+            // side at x = hi / y = hi); the faces x = hi, y = hi have their own
+            // coefficients
+            const bool dir = !a.periodic;
+            const bool ghost_low = dir && ((side == 0 && kx == 0) || (side == 2 && ky == 0));
+            const bool ghost_high = dir && ((side == 1 && kx == a.Kx - 1) || (side == 3 && ky == a.Ky - 1));
             const long long fidx = (long long)(side < 2 ? 0 : 1) * E * N + (long long)e_face * N + f;
-            const double af = a.faceU[fidx] * a.dt, bf = a.faceB[fidx];
+            double af, bf;
+            if (ghost_high) {
+                const long long hidx = side == 1 ? (long long)ky * N + f : (long long)a.Ky * N + (long long)kx * N + f;
+                af = a.faceUhi[hidx] * a.dt;
+                bf = a.faceBhi[hidx];
+            } else {
+                af = a.faceU[fidx] * a.dt;
+                bf = a.faceB[fidx];
+            }
             bool from_low;  // take the value from the element on the low side
             if constexpr (kPair)
                 from_low = fmaf(float(bf), float(dW), float(af)) > 0.f;
@@ -281,8 +308,17 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
             }
             const bool xface = side < 2;
             // low element's far face (right / top) or high element's near face (left / bottom)
-            const FaceT gv = from_low ? faces[(fbase + e_low) * 4 * N + (xface ? N : 3 * N) + f]
-                                      : faces[(fbase + e_high) * 4 * N + (xface ? 0 : 2 * N) + f];
+            FaceT gv;
+            if (from_low && ghost_low)  // left [Ky][N] or bottom [Kx][N] boundary values
+                gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 0 ? (long long)ky * N + f
+                                                                        : 2LL * a.Ky * N + (long long)kx * N + f)]);
+            else if (!from_low && ghost_high)  // right [Ky][N] or top [Kx][N]
+                gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 1 ? (long long)a.Ky * N + (long long)ky * N + f
+                                                                        : 2LL * a.Ky * N + (long long)a.Kx * N +
+                                                                              (long long)kx * N + f)]);
+            else
+                gv = from_low ? faces[(fbase + e_low) * 4 * N + (xface ? N : 3 * N) + f]
+                              : faces[(fbase + e_high) * 4 * N + (xface ? 0 : 2 * N) + f];
             R gr;
             if constexpr (kPair)
                 gr = (gv.x - ch) + (gv.y - cl);

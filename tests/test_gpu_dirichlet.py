@@ -139,3 +139,68 @@ def test_batch_and_server_reject_dirichlet(sl, orc):
         with pytest.raises(sl.SLError) as e:
             srv.submit(pb)
         assert e.value.code == -8
+
+
+def _ghost_2d(orc, K, N, L, fn, times):
+    pts = (np.arange(K)[:, None] + orc.nodes(N)[None, :]).ravel() * (L / K)
+    return np.array([np.concatenate([fn(0 * pts, pts, t), fn(L + 0 * pts, pts, t), fn(pts, 0 * pts, t),
+                                     fn(pts, L + 0 * pts, t)]) for t in times])
+
+
+def test_2d_inflow_advection_vs_oracle_and_exact(sl, orc):
+    u, v, L, K, N, dt, steps = 0.6, -0.4, 0.8, 3, 8, 2e-3, 100
+
+    def phi(x, y, t):
+        return 1.0 + 0.5 * np.sin(2 * np.pi * (x - u * t)) * np.sin(2 * np.pi * (y - v * t))
+
+    pb = I.problem(2, (K, K), (0.0, 0.0), (L, L), N, 2, steps, dt, 3, ("const", [u, v]), ("const", [0.0]),
+                   ("sinsin", [1.0, 0.5, 1.0]))
+    pb["periodic"] = False
+    pb["ghost"] = _ghost_2d(orc, K, N, L, phi, dt * np.arange(1, steps + 1))
+    ref = orc.run(pb, ns=2, want_states=True)["states"]
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        st = s.samples()
+    assert np.abs(st - ref).max() / np.abs(ref).max() <= FP64_TOL
+    x, y = orc.node_coords(pb)
+    assert np.abs(st[0] - phi(x, y, steps * dt)).max() <= 2e-7
+    # FP32: without diffusion every step repeats the same particle geometry, so
+    # the rounding of the FP32 advected basis accumulates (about 1.2e-7 of the
+    # field per step in 2D, periodic or not); 50 steps stay within the bar
+    with sl.Solver(pb, "fp64") as s:
+        s.step(dt, 50)
+        st50 = s.samples()
+    with sl.Solver(pb, "fp32") as s:
+        s.step(dt, 50)
+        assert np.abs(s.samples() - st50).max() / np.abs(st50).max() <= MIXED_TOL
+
+
+def test_2d_sine_diffusion_with_reseeding_vs_oracle(sl, orc):
+    K, N, M, dt, steps = 2, 5, 12, 1e-5, 30
+
+    def mean_exact(x, y, t):
+        return 2.0 + np.exp(-8 * np.pi ** 2 * t) * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+
+    pb = I.problem(2, (K, K), (0.0, 0.0), (1.0, 1.0), N, M, steps, dt, 31, ("const", [0.0, 0.0]), ("const", [1.0]),
+                   ("sinsin", [2.0, 1.0, 1.0]))
+    pb["periodic"] = False
+    pb["reseed_every"] = 10
+    pb["ghost"] = _ghost_2d(orc, K, N, 1.0, mean_exact, dt * np.arange(1, steps + 1))
+    ref = orc.run(pb, ns=M, want_states=True)["states"]
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        st = s.samples()
+    assert np.abs(st - ref).max() / np.abs(ref).max() <= FP64_TOL
+    assert all(np.array_equal(st[0], st[k]) for k in range(1, M))  # reseeded after the last step
+
+
+def test_2d_mixed_periodicity_unsupported(sl, orc):
+    pb = I.problem(2, (2, 2), (0.0, 0.0), (1.0, 1.0), 3, 2, 1, 1e-4, 1, ("const", [0.1, 0.2]), ("const", [0.01]),
+                   ("gauss", [1.0, 0.2, 0.5, 0.5]))
+    L = sl.lib()
+    import ctypes as C
+    m = sl._mesh(pb)
+    m.periodic[0], m.periodic[1] = 0, 1
+    u, D, p = sl._field(sl._U, pb["drift"]), sl._field(sl._D, pb["diffusion"]), sl._field(sl._PHI, pb["phi0"])
+    h = C.c_void_p()
+    assert L.sl_init(C.byref(h), C.byref(m), 3, 2, C.byref(u), C.byref(D), C.byref(p), None) == -8
