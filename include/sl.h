@@ -53,7 +53,7 @@ enum {
     SL_ERR_SINGULAR = -5,    /* coincident advected particles: non-finite remap */
     SL_ERR_TIMEOUT = -6,     /* a bounded device wait expired */
     SL_ERR_STATE = -7,       /* context poisoned by an earlier error */
-    SL_ERR_UNSUPPORTED = -8  /* valid but not provided (e.g. non-periodic mesh) */
+    SL_ERR_UNSUPPORTED = -8  /* valid but not provided (e.g. 2D order above the limit) */
 };
 
 /* Arithmetic of the step.  Wiener increments and moments are FP64 always.  */
