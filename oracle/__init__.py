@@ -23,8 +23,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-_DRIFT = {"const": 0, "sin": 1, "rotation": 2}
-_DIFF = {"const": 0, "cos": 1, "sinsin": 2}
+_DRIFT = {"const": 0, "sin": 1, "rotation": 2, "nodal": 3}
+_DIFF = {"const": 0, "cos": 1, "sinsin": 2, "nodal": 3}
 _PHI0 = {"gauss": 0, "fourier": 1, "sine": 2, "sinsin": 3}
 
 
@@ -43,7 +43,9 @@ class _Problem(C.Structure):
                 ("hi", C.c_double * 2), ("N", C.c_int), ("drift_kind", C.c_int),
                 ("drift_p", C.c_double * 8), ("diff_kind", C.c_int), ("diff_p", C.c_double * 8),
                 ("phi0_kind", C.c_int), ("phi0_p", C.c_double * 40), ("seed", C.c_ulonglong),
-                ("dt", C.c_double), ("omega", C.c_double), ("periodic", C.c_int), ("reseed_every", C.c_int)]
+                ("dt", C.c_double), ("omega", C.c_double), ("periodic", C.c_int), ("reseed_every", C.c_int),
+                ("drift_nodal", C.POINTER(C.c_double)), ("drift_face", C.POINTER(C.c_double)),
+                ("diff_nodal", C.POINTER(C.c_double)), ("diff_face", C.POINTER(C.c_double))]
 
 
 def lib():
@@ -82,6 +84,7 @@ def lib():
             L.orc_remap_2d.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_init_state.argtypes = [C.POINTER(_Problem), dp]
             L.orc_get_coeffs.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
+            L.orc_get_face_coeffs.argtypes = [C.POINTER(_Problem), dp, dp]
             L.orc_run.argtypes = [C.POINTER(_Problem), C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
                                   dp, dp, dp, dp, dp]
             L.orc_dt_max.restype = C.c_double
@@ -111,12 +114,27 @@ def _problem(pb, dt=None):
         p.K[1] = 1
         p.lo[1], p.hi[1] = 0.0, 1.0
     p.N = pb["N"]
+    keep = []
+
+    def nodal(spec):
+        # ("nodal", values at the nodes[, values at the interface points])
+        arrs = [_f64(a).ravel() if a is not None else None for a in (list(spec[1:]) + [None])[:2]]
+        keep.extend(a for a in arrs if a is not None)
+        return _dp(arrs[0]), _dp(arrs[1])
+
     p.drift_kind = _DRIFT[pb["drift"][0]]
-    for i, v in enumerate(pb["drift"][1]):
-        p.drift_p[i] = v
+    if pb["drift"][0] == "nodal":
+        p.drift_nodal, p.drift_face = nodal(pb["drift"])
+    else:
+        for i, v in enumerate(pb["drift"][1]):
+            p.drift_p[i] = v
     p.diff_kind = _DIFF[pb["diffusion"][0]]
-    for i, v in enumerate(pb["diffusion"][1]):
-        p.diff_p[i] = v
+    if pb["diffusion"][0] == "nodal":
+        p.diff_nodal, p.diff_face = nodal(pb["diffusion"])
+    else:
+        for i, v in enumerate(pb["diffusion"][1]):
+            p.diff_p[i] = v
+    p._keep = keep  # the nodal arrays live as long as the struct
     p.phi0_kind = _PHI0[pb["phi0"][0]]
     for i, v in enumerate(pb["phi0"][1]):
         p.phi0_p[i] = v
@@ -312,6 +330,27 @@ def coeffs(pb, dt=None):
     if lib().orc_get_coeffs(C.byref(p), _dp(ax), _dp(ay), _dp(b), _dp(c)) != 0:
         raise ValueError("bad problem")
     return ax, ay, b, c
+
+
+def n_interface_points(pb):
+    """Length of the interface table of a nodal field: K+1 in 1D; in 2D
+    Ky (Kx+1) N vertical then (Ky+1) Kx N horizontal interface points."""
+    if pb["dim"] == 1:
+        return pb["K"][0] + 1
+    Kx, Ky, N = pb["K"][0], pb["K"][1], pb["N"]
+    return Ky * (Kx + 1) * N + (Ky + 1) * Kx * N
+
+
+def face_coeffs(pb, dt=None):
+    """Interface coefficients (a = u_normal dt, b = sqrt(2 D)) in the interface
+    layout of ``n_interface_points`` (the last interface of a periodic line
+    repeats the first)."""
+    nf = n_interface_points(pb)
+    a, b = np.zeros(nf), np.zeros(nf)
+    p = _problem(pb, dt)
+    if lib().orc_get_face_coeffs(C.byref(p), _dp(a), _dp(b)) != 0:
+        raise ValueError("bad problem")
+    return a, b
 
 
 def dt_max(pb):

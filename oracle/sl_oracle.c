@@ -605,8 +605,8 @@ int orc_remap_2d_split(int N, const double *xi, const double *dx, const double *
 /* ------------------------------------------------------------------------ */
 /* Problem description and prescribed fields.                               */
 /* ------------------------------------------------------------------------ */
-enum { ORC_U_CONST = 0, ORC_U_SIN = 1, ORC_U_ROTATION = 2 };
-enum { ORC_D_CONST = 0, ORC_D_COS = 1, ORC_D_SINSIN = 2 };
+enum { ORC_U_CONST = 0, ORC_U_SIN = 1, ORC_U_ROTATION = 2, ORC_U_NODAL = 3 };
+enum { ORC_D_CONST = 0, ORC_D_COS = 1, ORC_D_SINSIN = 2, ORC_D_NODAL = 3 };
 enum { ORC_PHI_GAUSS = 0, ORC_PHI_FOURIER = 1, ORC_PHI_SINE = 2, ORC_PHI_SINSIN = 3 };
 
 typedef struct {
@@ -626,6 +626,13 @@ typedef struct {
     int periodic;     /* 1: periodic; 0: Dirichlet ghost values at x = lo, hi (1D)         */
     int reseed_every; /* > 0: every sample set to the sample mean after each step n with    */
                       /* (n + 1) % reseed_every == 0 (Eq. re-seed); 0: never                */
+    /* Nodal fields, the form a field solver hands over (Section 5.2 takes    */
+    /* du/dx from the DSEM solver).  Nodes: [dim][E][n] drift components,     */
+    /* [E][n] D.  Interface points (optional, NULL: derived): the normal      */
+    /* drift component or D, 1D [K+1] at x = lo + f h; 2D the vertical        */
+    /* interfaces [Ky][Kx+1][N] then the horizontal ones [Ky+1][Kx][N].       */
+    const double *drift_nodal, *drift_face;
+    const double *diff_nodal, *diff_face;
 } orc_problem;
 
 /* Drift u(x) (1D: u[0]; 2D: u[0], u[1]).                                    */
@@ -742,6 +749,77 @@ static void orc_node_xy(const orc_problem *pb, const orc_coeffs *cf, int e, int 
     *y = cf->dim == 2 ? pb->lo[1] + (ky + cf->xi[j]) * cf->hy : 0.0;
 }
 
+/* Element index of the element at position k along direction dir on grid  */
+/* line `line` (the row ky for dir 0, the column kx for dir 1).              */
+static int orc_elem_on_line(const orc_coeffs *cf, int dir, int line, int k)
+{
+    return dir == 0 ? line * cf->Kx + k : k * cf->Kx + line;
+}
+
+/* Trace of element e's nodal interpolant of `vals` ([E][n]) on its face     */
+/* xi_dir = side (0 or 1), at the face's Gauss point pt (2D; 0 in 1D).       */
+static double orc_trace(const orc_coeffs *cf, const double *vals, int e, int dir, int side, int pt)
+{
+    int N = cf->N;
+    double s = 0.0;
+    for (int l = 0; l < N; ++l) {
+        int node = cf->dim == 1 ? l : (dir == 0 ? pt * N + l : l * N + pt);
+        s += orc_lagrange(N, cf->xi, l, (double)side) * vals[(size_t)e * cf->n + node];
+    }
+    return s;
+}
+
+/* A nodal field at interface point pt of interface idx (0..K along dir) on  */
+/* grid line `line`: the caller's interface table if given, else the mean of */
+/* the traces of the elements on both sides (the one inside trace at a       */
+/* Dirichlet boundary).  On a periodic mesh interface K is interface 0.      */
+static double orc_iface_nodal(const orc_problem *pb, const orc_coeffs *cf, const double *vals,
+                              const double *face, int dir, int line, int idx, int pt)
+{
+    int K = dir == 0 ? cf->Kx : cf->Ky;
+    if (pb->periodic && idx == K) idx = 0;
+    if (face) {
+        if (cf->dim == 1) return face[idx];
+        if (dir == 0) return face[((size_t)line * (cf->Kx + 1) + idx) * cf->N + pt];
+        return face[(size_t)cf->Ky * (cf->Kx + 1) * cf->N + ((size_t)idx * cf->Kx + line) * cf->N + pt];
+    }
+    double left = 0.0, right = 0.0;
+    int have_left = idx > 0 || pb->periodic, have_right = idx < K;
+    if (have_left)
+        left = orc_trace(cf, vals, orc_elem_on_line(cf, dir, line, (idx - 1 + K) % K), dir, 1, pt);
+    if (have_right) right = orc_trace(cf, vals, orc_elem_on_line(cf, dir, line, idx), dir, 0, pt);
+    if (have_left && have_right) return 0.5 * (left + right);
+    return have_left ? left : right;
+}
+
+/* Normal drift u_dir and D at an interface point.  Analytic kinds are       */
+/* evaluated at (x, y); nodal ones by orc_iface_nodal, D clipped at 0 where  */
+/* a derived trace undershoots (D >= 0 on the nodes does not bound the       */
+/* interpolant between them).  Returns -1 for a negative given value.        */
+static int orc_face_fields(const orc_problem *pb, const orc_coeffs *cf, int dir, int line, int idx,
+                           int pt, double x, double y, double *un, double *D)
+{
+    if (pb->drift_kind == ORC_U_NODAL) {
+        *un = orc_iface_nodal(pb, cf, pb->drift_nodal + (size_t)dir * cf->E * cf->n, pb->drift_face,
+                              dir, line, idx, pt);
+    } else {
+        double u[2];
+        orc_drift(pb, x, y, u);
+        *un = u[dir];
+    }
+    if (pb->diff_kind == ORC_D_NODAL) {
+        *D = orc_iface_nodal(pb, cf, pb->diff_nodal, pb->diff_face, dir, line, idx, pt);
+        if (pb->diff_face) {
+            if (!(*D >= 0.0)) return -1;
+        } else if (*D < 0.0) {
+            *D = 0.0;
+        }
+    } else {
+        *D = orc_diffusion(pb, x, y);
+    }
+    return 0;
+}
+
 /* Coefficients of Section 5.2: a = u dt, b = sqrt(2 D) at the Gauss nodes   */
 /* (Eq. def_dx, explicit in time), c = 1 - dt du_j/dx_j (Eq. advection_phi) */
 /* with the divergence by spectral differentiation of the nodal drift within */
@@ -773,14 +851,20 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
     cf->bfx = (double *)calloc((size_t)E * nf, sizeof(double));
     cf->afy = (double *)calloc((size_t)E * nf, sizeof(double));
     cf->bfy = (double *)calloc((size_t)E * nf, sizeof(double));
+    int rc = 0;
     double *ux = (double *)malloc(sizeof(double) * n), *uy = (double *)malloc(sizeof(double) * n);
     for (int e = 0; e < E; ++e) {
         for (int p = 0; p < n; ++p) {
-            double x, y, u[2];
+            double x, y, u[2], D;
             orc_node_xy(pb, cf, e, p, &x, &y);
-            orc_drift(pb, x, y, u);
-            double D = orc_diffusion(pb, x, y);
-            if (D < 0.0) return -1;
+            if (pb->drift_kind == ORC_U_NODAL) {
+                u[0] = pb->drift_nodal[(size_t)e * n + p];
+                u[1] = d == 2 ? pb->drift_nodal[(size_t)E * n + (size_t)e * n + p] : 0.0;
+            } else {
+                orc_drift(pb, x, y, u);
+            }
+            D = pb->diff_kind == ORC_D_NODAL ? pb->diff_nodal[(size_t)e * n + p] : orc_diffusion(pb, x, y);
+            if (!(D >= 0.0)) { rc = -1; goto done; }
             ux[p] = u[0];
             uy[p] = u[1];
             cf->ax[e * n + p] = u[0] * pb->dt;
@@ -809,26 +893,26 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
         /* (2D) horizontal face y = y_ky, at the Gauss-node positions.       */
         int kx = e % cf->Kx, ky = e / cf->Kx;
         for (int f = 0; f < nf; ++f) {
-            double u[2];
+            double un, D;
             double xf = pb->lo[0] + kx * cf->hx;
             double yf = d == 2 ? pb->lo[1] + (ky + cf->xi[f]) * cf->hy : 0.0;
-            orc_drift(pb, xf, yf, u);
-            cf->afx[e * nf + f] = u[0] * pb->dt;
-            cf->bfx[e * nf + f] = sqrt(2.0 * orc_diffusion(pb, xf, yf));
+            if (orc_face_fields(pb, cf, 0, ky, kx, d == 2 ? f : 0, xf, yf, &un, &D) != 0) { rc = -1; goto done; }
+            cf->afx[e * nf + f] = un * pb->dt;
+            cf->bfx[e * nf + f] = sqrt(2.0 * D);
             if (d == 2) {
                 double xh = pb->lo[0] + (kx + cf->xi[f]) * cf->hx;
                 double yh = pb->lo[1] + ky * cf->hy;
-                orc_drift(pb, xh, yh, u);
-                cf->afy[e * nf + f] = u[1] * pb->dt;
-                cf->bfy[e * nf + f] = sqrt(2.0 * orc_diffusion(pb, xh, yh));
+                if (orc_face_fields(pb, cf, 1, kx, ky, f, xh, yh, &un, &D) != 0) { rc = -1; goto done; }
+                cf->afy[e * nf + f] = un * pb->dt;
+                cf->bfy[e * nf + f] = sqrt(2.0 * D);
             }
         }
     }
     if (d == 1) {
-        double u[2];
-        orc_drift(pb, pb->hi[0], 0.0, u);
-        cf->afx_hi = u[0] * pb->dt;
-        cf->bfx_hi = sqrt(2.0 * orc_diffusion(pb, pb->hi[0], 0.0));
+        double un, D;
+        if (orc_face_fields(pb, cf, 0, 0, cf->Kx, 0, pb->hi[0], 0.0, &un, &D) != 0) { rc = -1; goto done; }
+        cf->afx_hi = un * pb->dt;
+        cf->bfx_hi = sqrt(2.0 * D);
     } else {
         cf->afx_hi2 = (double *)calloc((size_t)cf->Ky * N, sizeof(double));
         cf->bfx_hi2 = (double *)calloc((size_t)cf->Ky * N, sizeof(double));
@@ -836,22 +920,23 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
         cf->bfy_hi2 = (double *)calloc((size_t)cf->Kx * N, sizeof(double));
         for (int ky = 0; ky < cf->Ky; ++ky)
             for (int f = 0; f < N; ++f) { /* x = hi at the Gauss nodes of row ky */
-                double u[2], yf = pb->lo[1] + (ky + cf->xi[f]) * cf->hy;
-                orc_drift(pb, pb->hi[0], yf, u);
-                cf->afx_hi2[ky * N + f] = u[0] * pb->dt;
-                cf->bfx_hi2[ky * N + f] = sqrt(2.0 * orc_diffusion(pb, pb->hi[0], yf));
+                double un, D, yf = pb->lo[1] + (ky + cf->xi[f]) * cf->hy;
+                if (orc_face_fields(pb, cf, 0, ky, cf->Kx, f, pb->hi[0], yf, &un, &D) != 0) { rc = -1; goto done; }
+                cf->afx_hi2[ky * N + f] = un * pb->dt;
+                cf->bfx_hi2[ky * N + f] = sqrt(2.0 * D);
             }
         for (int kx = 0; kx < cf->Kx; ++kx)
             for (int f = 0; f < N; ++f) { /* y = hi at the Gauss nodes of column kx */
-                double u[2], xf = pb->lo[0] + (kx + cf->xi[f]) * cf->hx;
-                orc_drift(pb, xf, pb->hi[1], u);
-                cf->afy_hi2[kx * N + f] = u[1] * pb->dt;
-                cf->bfy_hi2[kx * N + f] = sqrt(2.0 * orc_diffusion(pb, xf, pb->hi[1]));
+                double un, D, xf = pb->lo[0] + (kx + cf->xi[f]) * cf->hx;
+                if (orc_face_fields(pb, cf, 1, kx, cf->Ky, f, xf, pb->hi[1], &un, &D) != 0) { rc = -1; goto done; }
+                cf->afy_hi2[kx * N + f] = un * pb->dt;
+                cf->bfy_hi2[kx * N + f] = sqrt(2.0 * D);
             }
     }
+done:
     free(ux);
     free(uy);
-    return 0;
+    return rc;
 }
 
 /* Initial nodal state phi0 at the Gauss nodes, [E][n] (Eq. soln_init; every */
@@ -859,7 +944,10 @@ static int orc_build_coeffs(const orc_problem *pb, orc_coeffs *cf)
 int orc_init_state(const orc_problem *pb, double *out)
 {
     orc_coeffs cf;
-    if (orc_build_coeffs(pb, &cf) != 0) return -1;
+    if (orc_build_coeffs(pb, &cf) != 0) {
+        orc_coeffs_free(&cf);
+        return -1;
+    }
     for (int e = 0; e < cf.E; ++e)
         for (int p = 0; p < cf.n; ++p) {
             double x, y;
@@ -874,12 +962,63 @@ int orc_init_state(const orc_problem *pb, double *out)
 int orc_get_coeffs(const orc_problem *pb, double *ax, double *ay, double *b, double *c)
 {
     orc_coeffs cf;
-    if (orc_build_coeffs(pb, &cf) != 0) return -1;
+    if (orc_build_coeffs(pb, &cf) != 0) {
+        orc_coeffs_free(&cf);
+        return -1;
+    }
     size_t sz = sizeof(double) * cf.E * cf.n;
     memcpy(ax, cf.ax, sz);
     memcpy(ay, cf.ay, sz);
     memcpy(b, cf.b, sz);
     memcpy(c, cf.c, sz);
+    orc_coeffs_free(&cf);
+    return 0;
+}
+
+/* Interface coefficients for inspection, in the interface layout of the    */
+/* nodal fields: a = u_normal dt and b = sqrt(2 D); 1D [K+1], 2D the         */
+/* vertical interfaces [Ky][Kx+1][N] then the horizontal [Ky+1][Kx][N].      */
+/* On a periodic mesh the last interface of a line repeats the first.        */
+int orc_get_face_coeffs(const orc_problem *pb, double *a, double *b)
+{
+    orc_coeffs cf;
+    if (orc_build_coeffs(pb, &cf) != 0) {
+        orc_coeffs_free(&cf);
+        return -1;
+    }
+    int N = cf.N, Kx = cf.Kx, Ky = cf.Ky;
+    if (cf.dim == 1) {
+        for (int f = 0; f <= Kx; ++f) {
+            a[f] = f < Kx ? cf.afx[f] : (cf.periodic ? cf.afx[0] : cf.afx_hi);
+            b[f] = f < Kx ? cf.bfx[f] : (cf.periodic ? cf.bfx[0] : cf.bfx_hi);
+        }
+    } else {
+        size_t o = 0;
+        for (int ky = 0; ky < Ky; ++ky)
+            for (int f = 0; f <= Kx; ++f)
+                for (int j = 0; j < N; ++j, ++o) {
+                    if (f < Kx || cf.periodic) {
+                        int e = ky * Kx + (f < Kx ? f : 0);
+                        a[o] = cf.afx[e * N + j];
+                        b[o] = cf.bfx[e * N + j];
+                    } else {
+                        a[o] = cf.afx_hi2[ky * N + j];
+                        b[o] = cf.bfx_hi2[ky * N + j];
+                    }
+                }
+        for (int g = 0; g <= Ky; ++g)
+            for (int kx = 0; kx < Kx; ++kx)
+                for (int i = 0; i < N; ++i, ++o) {
+                    if (g < Ky || cf.periodic) {
+                        int e = (g < Ky ? g : 0) * Kx + kx;
+                        a[o] = cf.afy[e * N + i];
+                        b[o] = cf.bfy[e * N + i];
+                    } else {
+                        a[o] = cf.afy_hi2[kx * N + i];
+                        b[o] = cf.bfy_hi2[kx * N + i];
+                    }
+                }
+    }
     orc_coeffs_free(&cf);
     return 0;
 }
@@ -1135,7 +1274,10 @@ int orc_run(const orc_problem *pb, long step0, int nsteps, int s0, int ns, int n
     if (!pb->periodic && !ghost) return -1; /* Dirichlet: boundary values needed */
     if (pb->reseed_every < 0) return -1;
     orc_coeffs cf;
-    if (orc_build_coeffs(pb, &cf) != 0) return -1;
+    if (orc_build_coeffs(pb, &cf) != 0) {
+        orc_coeffs_free(&cf);
+        return -1;
+    }
     size_t sz = (size_t)cf.E * cf.n;
     double *phi0 = (double *)malloc(sizeof(double) * sz);
     orc_init_state(pb, phi0);
@@ -1194,7 +1336,10 @@ static double orc_dt_bound(const orc_problem *pb, int edge)
     orc_problem q = *pb;
     q.dt = 1.0;
     orc_coeffs cf;
-    if (orc_build_coeffs(&q, &cf) != 0) return -1.0;
+    if (orc_build_coeffs(&q, &cf) != 0) {
+        orc_coeffs_free(&cf);
+        return -1.0;
+    }
     double gap = 1.0;
     for (int i = 0; i + 1 < cf.N; ++i)
         if (cf.xi[i + 1] - cf.xi[i] < gap) gap = cf.xi[i + 1] - cf.xi[i];
