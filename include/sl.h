@@ -70,10 +70,12 @@ enum {
     SL_U_CONST = 1,    /* u = (p0, p1)                                        */
     SL_U_SIN = 2,      /* u = p0 + p1 sin(p2 pi x)                       (1D) */
     SL_U_ROTATION = 3, /* u = p0 (-(y - p2), x - p1)                     (2D) */
+    SL_U_NODAL = 4,    /* nodal: [dim][elements][N^dim] u_x (then u_y), see below */
     /* diffusion coefficient D >= 0 */
     SL_D_CONST = 11,   /* D = p0                                              */
     SL_D_COS = 12,     /* D = p0 (1 + p1 cos(p2 pi x))                        */
     SL_D_SINSIN = 13,  /* D = p0 (1 + p1 sin(p2 pi x) sin(p3 pi y))           */
+    SL_D_NODAL = 14,   /* nodal: [elements][N^dim] D >= 0, see below           */
     /* initial condition phi0 */
     SL_PHI_GAUSS = 21,   /* p0 exp(-|x - (p2,p3)|^2 / (2 p1^2)), nearest periodic images */
     SL_PHI_FOURIER = 22, /* p0 + sum_{k=1}^{p2} a_k cos(k p1 pi x) + b_k sin(k p1 pi x), */
@@ -83,10 +85,26 @@ enum {
     SL_PHI_NODAL = 25    /* host array nodal[element][node] of the initial values        */
 };
 
+/* Nodal drift and diffusion: the form in which a field solver hands its    */
+/* velocity and diffusivity over (Section 5.2 takes du/dx from the DSEM      */
+/* solver).  `nodal` holds the values at the Gauss nodes, element-major and  */
+/* x-fastest as the state.  The divergence of the drift is the spectral      */
+/* derivative of the nodal values in each element.  `face` (optional) holds  */
+/* the normal drift component, or D, at the interface points:                */
+/*   1D [K+1]: x = lo + f h, f = 0..K;                                       */
+/*   2D the vertical interfaces [K1][K0+1][N] (x = lo + f h0, y at the Gauss */
+/*      nodes of the element row), then the horizontal ones [K1+1][K0][N].   */
+/* On a periodic mesh the last interface of a line is its first and that    */
+/* entry is not read.  face = NULL: the mean of the traces of the two        */
+/* neighbouring elements' interpolants at the point (the inside trace at a   */
+/* Dirichlet boundary), D clipped at 0 there.  D must be >= 0 at every node  */
+/* and every given interface point (SL_ERR_ARG).  Both arrays are host       */
+/* memory, copied before the call returns.                                   */
 typedef struct {
     int kind;
     double p[40];
-    const double *nodal; /* SL_PHI_NODAL only: host [elements][N^dim], copied at sl_init */
+    const double *nodal; /* *_NODAL kinds: host node values (SL_PHI_NODAL: [elements][N^dim]) */
+    const double *face;  /* SL_U_NODAL / SL_D_NODAL: host interface table, or NULL            */
 } sl_field;
 
 /* Uniform tensor mesh of K[0] (x K[1]) elements on [lo, hi]. */

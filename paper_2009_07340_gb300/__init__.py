@@ -27,8 +27,8 @@ __all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_ini
 SL_FP64, SL_MIXED, SL_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": SL_FP64, "mixed": SL_MIXED, "fp32": SL_FP32}
 
-_U = {"const": 1, "sin": 2, "rotation": 3}
-_D = {"const": 11, "cos": 12, "sinsin": 13}
+_U = {"const": 1, "sin": 2, "rotation": 3, "nodal": 4}
+_D = {"const": 11, "cos": 12, "sinsin": 13, "nodal": 14}
 _PHI = {"gauss": 21, "fourier": 22, "sine": 23, "sinsin": 24, "nodal": 25}
 
 
@@ -39,7 +39,8 @@ class SLError(RuntimeError):
 
 
 class sl_field(C.Structure):
-    _fields_ = [("kind", C.c_int), ("p", C.c_double * 40), ("nodal", C.POINTER(C.c_double))]
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 40), ("nodal", C.POINTER(C.c_double)),
+                ("face", C.POINTER(C.c_double))]
 
 
 class sl_mesh(C.Structure):
@@ -143,10 +144,17 @@ def _check(rc, where):
 
 
 def _field(kind_map, spec):
+    """sl_field of a problem-dict field: (kind, parameters), or ("nodal",
+    node values[, interface values]) with host arrays the struct keeps alive."""
     f = sl_field()
-    kind, p = spec
-    f.kind = kind_map[kind]
-    for i, v in enumerate(p):
+    f.kind = kind_map[spec[0]]
+    if spec[0] == "nodal":
+        f._keep = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in spec[1:3] if a is not None]
+        f.nodal = _f64p(f._keep[0])
+        if len(f._keep) > 1:
+            f.face = _f64p(f._keep[1])
+        return f
+    for i, v in enumerate(spec[1]):
         f.p[i] = float(v)
     return f
 
@@ -288,9 +296,9 @@ def _instance(pb, dt=None, seed=None):
     inst.mesh = _mesh(pb)
     inst.N = pb["N"]
     inst.M = pb["M"]
-    inst.drift = _field(_U, pb["drift"])
-    inst.diffusion = _field(_D, pb["diffusion"])
-    inst.phi0 = _field(_PHI, pb["phi0"])
+    fields = (_field(_U, pb["drift"]), _field(_D, pb["diffusion"]), _field(_PHI, pb["phi0"]))
+    inst.drift, inst.diffusion, inst.phi0 = fields
+    inst._keep = fields  # the assignment copies the structs, not the nodal arrays they point to
     d = pb["dt"] if dt is None else dt
     # a problem's dt may be ("node", f) / ("edge", f): f times sl_dt_max / sl_dt_edge
     if isinstance(d, (tuple, list)):
@@ -305,7 +313,8 @@ def _instance(pb, dt=None, seed=None):
 
 
 def sl_batch_create(problems, precision=SL_FP64, stream=None, strict_dt=False, device=-1):
-    arr = (sl_instance * len(problems))(*[_instance(pb) for pb in problems])
+    insts = [_instance(pb) for pb in problems]  # alive until the call returns (nodal arrays)
+    arr = (sl_instance * len(problems))(*insts)
     opt = sl_options()
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.strict_dt = 1 if strict_dt else 0

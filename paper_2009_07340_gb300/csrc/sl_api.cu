@@ -30,16 +30,48 @@ bool valid_kind(int dim, int what, const sl_field *f)
     if (!f) return false;
     const int k = f->kind;
     if (what == 0)
-        return k == SL_U_CONST || (dim == 1 && k == SL_U_SIN) || (dim == 2 && k == SL_U_ROTATION);
-    if (what == 1) return k == SL_D_CONST || k == SL_D_COS || (dim == 2 && k == SL_D_SINSIN);
+        return k == SL_U_CONST || (dim == 1 && k == SL_U_SIN) || (dim == 2 && k == SL_U_ROTATION) ||
+               (k == SL_U_NODAL && f->nodal != nullptr);
+    if (what == 1)
+        return k == SL_D_CONST || k == SL_D_COS || (dim == 2 && k == SL_D_SINSIN) ||
+               (k == SL_D_NODAL && f->nodal != nullptr);
     if (k == SL_PHI_NODAL) return f->nodal != nullptr;
     if (k == SL_PHI_FOURIER) return dim == 1 && f->p[2] >= 0 && f->p[2] <= 18;
     return k == SL_PHI_GAUSS || (dim == 1 && k == SL_PHI_SINE) || (dim == 2 && k == SL_PHI_SINSIN);
 }
 
+// Entries of the interface table of a nodal field (1D K+1; 2D vertical
+// K1 (K0+1) N then horizontal (K1+1) K0 N).
+long long n_iface(int dim, int K0, int K1, int N)
+{
+    return dim == 1 ? K0 + 1 : (long long)K1 * (K0 + 1) * N + (long long)(K1 + 1) * K0 * N;
+}
+
+// D >= 0 (NaN refused): analytic kinds by their parameters, nodal ones at
+// every node and every interface-table entry that is read (on a periodic
+// mesh the last interface of each line is not).
+bool diffusion_ok(const sl_field *f, int dim, int K0, int K1, int N, bool periodic)
+{
+    if (f->kind != SL_D_NODAL) return f->p[0] >= 0.0 && (f->kind == SL_D_CONST || std::fabs(f->p[1]) <= 1.0);
+    const long long V = (long long)K0 * K1 * (dim == 2 ? N * N : N);
+    for (long long v = 0; v < V; ++v)
+        if (!(f->nodal[v] >= 0.0)) return false;
+    if (!f->face) return true;
+    const long long nif = n_iface(dim, K0, K1, N), nvert = dim == 1 ? K0 + 1 : (long long)K1 * (K0 + 1) * N;
+    for (long long i = 0; i < nif; ++i) {
+        bool last;
+        if (dim == 1) last = i == K0;
+        else if (i < nvert) last = (i / N) % (K0 + 1) == K0;
+        else last = (i - nvert) / ((long long)K0 * N) == K1;
+        if (periodic && last) continue;
+        if (!(f->face[i] >= 0.0)) return false;
+    }
+    return true;
+}
+
 sl::FieldDev to_dev(const sl_field *f)
 {
-    sl::FieldDev d;
+    sl::FieldDev d = {};
     d.kind = f->kind;
     std::memcpy(d.p, f->p, sizeof(d.p));
     return d;
@@ -49,6 +81,53 @@ template <typename T>
 cudaError_t dalloc(const sl_ctx *c, T **p, size_t count)
 {
     return sl::ctx_alloc(c, reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// Device copies of a nodal drift's or diffusion's tables for the setup
+// kernels (nvals node values, nif interface entries), stream-ordered on the
+// context's stream; unstage_nodal frees them after those kernels.
+cudaError_t stage_nodal(const sl_ctx *c, const sl_field *f, long long nvals, long long nif, sl::FieldDev &d)
+{
+    if (f->kind != SL_U_NODAL && f->kind != SL_D_NODAL) return cudaSuccess;
+    double *a = nullptr, *b = nullptr;
+    cudaError_t e = dalloc(c, &a, size_t(nvals));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(a, f->nodal, size_t(nvals) * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && f->face) {
+        e = dalloc(c, &b, size_t(nif));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b, f->face, size_t(nif) * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    }
+    d.nodal = a;
+    d.face = b;
+    return e;
+}
+
+void unstage_nodal(const sl_ctx *c, sl::FieldDev &d)
+{
+    sl::ctx_free(c, const_cast<double *>(d.nodal));
+    sl::ctx_free(c, const_cast<double *>(d.face));
+    d.nodal = d.face = nullptr;
+}
+
+// Node and face coefficients of the current drift and diffusion (the setup
+// kernels), nodal tables staged for the duration.
+cudaError_t set_coefficients(sl_ctx *c, const sl_field *drift, const sl_field *diffusion, const sl_field *phi0,
+                             const double *phi0_nodal_dev, bool write_state)
+{
+    const sl::Mesh &m = c->m;
+    const long long V = (long long)m.E * m.n, nif = n_iface(m.dim, m.K[0], m.K[1], m.N);
+    sl::FieldDev du = to_dev(drift), dD = to_dev(diffusion);
+    cudaError_t e = stage_nodal(c, drift, m.dim * V, nif, du);
+    if (e == cudaSuccess) e = stage_nodal(c, diffusion, V, nif, dD);
+    if (e == cudaSuccess)
+        e = sl::launch_init_fields(m, du, dD, to_dev(phi0), phi0_nodal_dev, c->xi, c->nodeU, c->nodeB, c->nodeDiv,
+                                   c->faceU, c->faceB, write_state ? c->Q : nullptr, c->M * c->ncomp,
+                                   c->precision == SL_FP64, c->st);  // [M][ncomp] fields of E n values
+    if (e == cudaSuccess && m.dim == 2) e = sl::launch_init_faces_hi(m, du, dD, c->faceUhi, c->faceBhi, c->st);
+    unstage_nodal(c, du);
+    unstage_nodal(c, dD);
+    return e;
 }
 
 // Chebyshev-Gauss nodes (host copy for the time-step guards only).
@@ -237,8 +316,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     }
     if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion) || !valid_kind(dim, 2, phi0))
         return SL_ERR_ARG;
-    if (diffusion->kind != SL_D_CONST && std::fabs(diffusion->p[1]) > 1.0) return SL_ERR_ARG;  // D >= 0
-    if (diffusion->p[0] < 0.0) return SL_ERR_ARG;
+    if (!diffusion_ok(diffusion, dim, mesh->K[0], dim == 2 ? mesh->K[1] : 1, N, mesh->periodic[0] != 0))
+        return SL_ERR_ARG;
     const int precision = opt ? opt->precision : SL_FP64;
     if (precision != SL_FP64 && precision != SL_MIXED && precision != SL_FP32) return SL_ERR_ARG;
     if (dim == 1 && mesh->K[0] > sl::kMaxThreads1D * sl::kMaxCluster1D) return SL_ERR_UNSUPPORTED;
@@ -292,6 +371,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
         m.hi[d] = d < dim ? mesh->hi[d] : 1.0;
         m.h[d] = (m.hi[d] - m.lo[d]) / m.K[d];
     }
+    m.periodic = c->periodic;
     const long long V = (long long)m.E * m.n;
     c->state_elem = precision == SL_FP64 ? sizeof(double) : sizeof(float2);  // FP32 modes: hi + lo pair
     c->vals = (long long)ncomp * V;
@@ -325,12 +405,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
         }
     }
     cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
-    if (e == cudaSuccess)
-        e = sl::launch_init_fields(m, to_dev(drift), to_dev(diffusion), to_dev(phi0), nodal_dev, c->xi, c->nodeU,
-                                   c->nodeB, c->nodeDiv, c->faceU, c->faceB, c->Q, M * ncomp, precision == SL_FP64,
-                                   c->st);  // [M][ncomp] fields of E n values, each phi0
-    if (e == cudaSuccess && dim == 2)
-        e = sl::launch_init_faces_hi(m, to_dev(drift), to_dev(diffusion), c->faceUhi, c->faceBhi, c->st);
+    if (e == cudaSuccess) e = set_coefficients(c, drift, diffusion, phi0, nodal_dev, true);  // every sample phi0
     sl::ctx_free(c, nodal_dev);
     if (e != cudaSuccess || refresh_bounds(c) != SL_OK) {
         cudaGetLastError();
@@ -389,18 +464,12 @@ int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
     if (c->poisoned) return SL_ERR_STATE;
     const int dim = c->m.dim;
     if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion)) return SL_ERR_ARG;
-    if (diffusion->kind != SL_D_CONST && std::fabs(diffusion->p[1]) > 1.0) return SL_ERR_ARG;  // D >= 0
-    if (diffusion->p[0] < 0.0) return SL_ERR_ARG;
+    if (!diffusion_ok(diffusion, dim, c->m.K[0], c->m.K[1], c->m.N, c->periodic != 0)) return SL_ERR_ARG;
     sl_field none;
     std::memset(&none, 0, sizeof(none));
     none.kind = SL_PHI_GAUSS;  // no state is written
-    const cudaError_t e = sl::launch_init_fields(c->m, to_dev(drift), to_dev(diffusion), to_dev(&none), nullptr, c->xi,
-                                                 c->nodeU, c->nodeB, c->nodeDiv, c->faceU, c->faceB, nullptr, c->M,
-                                                 c->precision == SL_FP64, c->st);
-    cudaError_t e2 = e;
-    if (e2 == cudaSuccess && dim == 2)
-        e2 = sl::launch_init_faces_hi(c->m, to_dev(drift), to_dev(diffusion), c->faceUhi, c->faceBhi, c->st);
-    if (e2 != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
+    const cudaError_t e = set_coefficients(c, drift, diffusion, &none, nullptr, false);
+    if (e != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
     return SL_OK;
 }
 

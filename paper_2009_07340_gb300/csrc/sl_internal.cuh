@@ -20,6 +20,8 @@ constexpr int kMaxCluster1D = 8;    // CTAs per sample field (portable cluster s
 struct FieldDev {
     int kind;
     double p[40];
+    const double *nodal;  // nodal drift / diffusion: device copy of the node values
+    const double *face;   // and of the interface table (nullptr: derived from the traces)
 };
 
 struct Mesh {
@@ -27,6 +29,7 @@ struct Mesh {
     int K[2];       // elements per direction (K[1] = 1 in 1D)
     int E;          // elements
     double lo[2], hi[2], h[2];
+    int periodic;   // 1: periodic in every direction; 0: Dirichlet boundaries
 };
 
 // Kernel arguments of the 1D step (one launch advances `nsteps` steps).

@@ -74,7 +74,34 @@ struct Request {
     double slice_max = 0.0;      // longest slice turnaround (launch to completion seen)
     std::vector<double> mean, m2;
     long long esu = 0;
+    // Copies of the caller's nodal tables (phi0, drift and diffusion nodes and
+    // interfaces): the solver is created later, on a worker thread.
+    std::vector<double> tables[5];
 };
+
+// Keeps copies of the request's nodal tables and points its spec at them.
+void own_tables(Request &r)
+{
+    sl_instance &s = r.spec;
+    const int dim = s.mesh.dim, N = s.N;
+    const long long K0 = s.mesh.K[0], K1 = dim == 2 ? s.mesh.K[1] : 1;
+    const long long V = K0 * K1 * (dim == 2 ? (long long)N * N : N);
+    const long long nif = dim == 1 ? K0 + 1 : K1 * (K0 + 1) * N + (K1 + 1) * K0 * N;
+    auto keep = [](const double *&p, long long n, std::vector<double> &v) {
+        if (!p) return;
+        v.assign(p, p + n);
+        p = v.data();
+    };
+    if (s.phi0.kind == SL_PHI_NODAL) keep(s.phi0.nodal, V, r.tables[0]);
+    if (s.drift.kind == SL_U_NODAL) {
+        keep(s.drift.nodal, dim * V, r.tables[1]);
+        keep(s.drift.face, nif, r.tables[2]);
+    }
+    if (s.diffusion.kind == SL_D_NODAL) {
+        keep(s.diffusion.nodal, V, r.tables[3]);
+        keep(s.diffusion.face, nif, r.tables[4]);
+    }
+}
 
 size_t footprint_of(const sl_instance &s, int slice)
 {
@@ -452,6 +479,9 @@ int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long
         return SL_ERR_ARG;
     if (!spec->mesh.periodic[0] || (spec->mesh.dim == 2 && !spec->mesh.periodic[1]))
         return SL_ERR_UNSUPPORTED;  // requests carry no boundary values: periodic meshes only
+    if ((spec->mesh.dim != 1 && spec->mesh.dim != 2) || spec->N < 2 || spec->N > sl::kMaxN ||
+        spec->mesh.K[0] < 1 || (spec->mesh.dim == 2 && spec->mesh.K[1] < 1))
+        return SL_ERR_ARG;  // (sizes of the nodal tables copied below)
     Request r;
     r.owner = s;
     r.spec = *spec;
@@ -469,7 +499,7 @@ int sl_server_submit(sl_server *s, const sl_instance *spec, int steps, long long
     s->submitted++;
     s->queue.push_back(r.ticket);
     if (ticket) *ticket = r.ticket;
-    s->req.emplace(r.ticket, std::move(r));
+    own_tables(s->req.emplace(r.ticket, std::move(r)).first->second);
     wake_scheduler(s, true);
     return SL_OK;
 }

@@ -49,6 +49,92 @@ __device__ double diffusion_at(const FieldDev &f, double x, double y)
     }
 }
 
+// h_l(x): the Lagrange basis polynomial l on the Gauss nodes (product form).
+__device__ double lagrange_at(int N, int l, double x)
+{
+    const double xl = gauss_node(l, N);
+    double v = 1.0;
+    for (int k = 0; k < N; ++k)
+        if (k != l) v *= (x - gauss_node(k, N)) / (xl - gauss_node(k, N));
+    return v;
+}
+
+// Nodal fields (node values handed over by a field solver, Section 5.2).
+// Value at node v = e n + p; the drift's y component follows its x block.
+__device__ __forceinline__ void node_drift(const FieldDev &f, const Mesh &m, long long v, double x, double y,
+                                           double &ux, double &uy)
+{
+    if (f.kind == SL_U_NODAL) {
+        ux = f.nodal[v];
+        uy = m.dim == 2 ? f.nodal[(long long)m.E * m.n + v] : 0.0;
+    } else {
+        drift_at(f, x, y, ux, uy);
+    }
+}
+
+__device__ __forceinline__ double node_diffusion(const FieldDev &f, long long v, double x, double y)
+{
+    return f.kind == SL_D_NODAL ? f.nodal[v] : diffusion_at(f, x, y);
+}
+
+// Trace of element e's nodal interpolant of vals ([E][n]) on its face
+// xi_dir = side, at the face's Gauss point pt (0 in 1D).
+__device__ double trace_of(const Mesh &m, const double *vals, int e, int dir, double side, int pt)
+{
+    const int N = m.N;
+    double s = 0.0;
+    for (int l = 0; l < N; ++l) {
+        const int node = m.dim == 1 ? l : (dir == 0 ? pt * N + l : l * N + pt);
+        s += lagrange_at(N, l, side) * vals[(long long)e * m.n + node];
+    }
+    return s;
+}
+
+// A nodal field at point pt of interface idx (0..K along dir) on grid line
+// `line` (the element row for dir 0, the column for dir 1): the interface
+// table when given (1D [K+1]; 2D vertical [K1][K0+1][N] then horizontal
+// [K1+1][K0][N]), else the mean of the traces of the elements on both sides,
+// the inside one alone at a Dirichlet boundary.  On a periodic mesh
+// interface K is interface 0.
+__device__ double iface_nodal(const Mesh &m, const double *vals, const double *face, int dir, int line, int idx,
+                              int pt)
+{
+    const int K = m.K[dir];
+    if (m.periodic && idx == K) idx = 0;
+    if (face) {
+        if (m.dim == 1) return face[idx];
+        if (dir == 0) return face[((long long)line * (m.K[0] + 1) + idx) * m.N + pt];
+        return face[(long long)m.K[1] * (m.K[0] + 1) * m.N + ((long long)idx * m.K[0] + line) * m.N + pt];
+    }
+    const bool has_l = idx > 0 || m.periodic, has_r = idx < K;
+    const int kl = (idx - 1 + K) % K;
+    const int el = dir == 0 ? line * m.K[0] + kl : kl * m.K[0] + line;
+    const int er = dir == 0 ? line * m.K[0] + idx : idx * m.K[0] + line;
+    const double l = has_l ? trace_of(m, vals, el, dir, 1.0, pt) : 0.0;
+    const double r = has_r ? trace_of(m, vals, er, dir, 0.0, pt) : 0.0;
+    if (has_l && has_r) return 0.5 * (l + r);
+    return has_l ? l : r;
+}
+
+// Normal drift u_dir and sqrt(2 D) at an interface point at (x, y); nodal
+// kinds through iface_nodal, a derived D clipped at 0 (D >= 0 on the nodes
+// does not bound the interpolant's trace).
+__device__ void face_fields(const FieldDev &fu, const FieldDev &fD, const Mesh &m, int dir, int line, int idx,
+                            int pt, double x, double y, double &un, double &b)
+{
+    if (fu.kind == SL_U_NODAL) {
+        un = iface_nodal(m, fu.nodal + (long long)dir * m.E * m.n, fu.face, dir, line, idx, pt);
+    } else {
+        double ux, uy;
+        drift_at(fu, x, y, ux, uy);
+        un = dir == 0 ? ux : uy;
+    }
+    double D;
+    if (fD.kind == SL_D_NODAL) D = fmax(iface_nodal(m, fD.nodal, fD.face, dir, line, idx, pt), 0.0);
+    else D = diffusion_at(fD, x, y);
+    b = sqrt(2.0 * D);
+}
+
 __device__ double phi0_at(const FieldDev &f, const Mesh &m, double x, double y)
 {
     const double *p = f.p;
@@ -113,21 +199,22 @@ __global__ void init_nodes_kernel(Mesh m, FieldDev fu, FieldDev fD, FieldDev fph
     const double x = m.lo[0] + (kx + gauss_node(i, N)) * m.h[0];
     const double y = m.dim == 2 ? m.lo[1] + (ky + gauss_node(j, N)) * m.h[1] : 0.0;
     double ux, uy;
-    drift_at(fu, x, y, ux, uy);
+    node_drift(fu, m, v, x, y, ux, uy);
     nodeU[v] = ux;
     if (m.dim == 2) nodeU[V + v] = uy;
-    nodeB[v] = sqrt(2.0 * diffusion_at(fD, x, y));
+    nodeB[v] = sqrt(2.0 * node_diffusion(fD, v, x, y));
     // divergence
+    const long long ve = (long long)e * m.n;
     double dx = 0.0, dy = 0.0;
     for (int l = 0; l < N; ++l) {
         double uxl, uyl, dummy;
         if (m.dim == 1) {
-            drift_at(fu, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], 0.0, uxl, dummy);
+            node_drift(fu, m, ve + l, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], 0.0, uxl, dummy);
             dx += lagrange_deriv(N, l, gauss_node(i, N)) * uxl;
         } else {
-            drift_at(fu, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], y, uxl, dummy);
+            node_drift(fu, m, ve + j * N + l, m.lo[0] + (kx + gauss_node(l, N)) * m.h[0], y, uxl, dummy);
             dx += lagrange_deriv(N, l, gauss_node(i, N)) * uxl;
-            drift_at(fu, x, m.lo[1] + (ky + gauss_node(l, N)) * m.h[1], dummy, uyl);
+            node_drift(fu, m, ve + l * N + i, x, m.lo[1] + (ky + gauss_node(l, N)) * m.h[1], dummy, uyl);
             dy += lagrange_deriv(N, l, gauss_node(j, N)) * uyl;
         }
     }
@@ -145,24 +232,17 @@ __global__ void init_faces_kernel(Mesh m, FieldDev fu, FieldDev fD, double *face
     const int nf = m.dim == 1 ? m.E + 1 : m.E * m.N;  // 1D: interfaces 0..K (K: x = hi)
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nf) return;
-    double ux, uy;
     if (m.dim == 1) {
         const double xf = v == m.E ? m.hi[0] : m.lo[0] + v * m.h[0];  // v = E: the boundary x = hi
-        drift_at(fu, xf, 0.0, ux, uy);
-        faceU[v] = ux;
-        faceB[v] = sqrt(2.0 * diffusion_at(fD, xf, 0.0));
+        face_fields(fu, fD, m, 0, 0, v, 0, xf, 0.0, faceU[v], faceB[v]);
         return;
     }
     const int e = v / m.N, f = v % m.N;
     const int kx = e % m.K[0], ky = e / m.K[0];
     const double xv = m.lo[0] + kx * m.h[0], yv = m.lo[1] + (ky + gauss_node(f, m.N)) * m.h[1];
-    drift_at(fu, xv, yv, ux, uy);
-    faceU[v] = ux;
-    faceB[v] = sqrt(2.0 * diffusion_at(fD, xv, yv));
+    face_fields(fu, fD, m, 0, ky, kx, f, xv, yv, faceU[v], faceB[v]);
     const double xh = m.lo[0] + (kx + gauss_node(f, m.N)) * m.h[0], yh = m.lo[1] + ky * m.h[1];
-    drift_at(fu, xh, yh, ux, uy);
-    faceU[nf + v] = uy;
-    faceB[nf + v] = sqrt(2.0 * diffusion_at(fD, xh, yh));
+    face_fields(fu, fD, m, 1, kx, ky, f, xh, yh, faceU[nf + v], faceB[nf + v]);
 }
 
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
@@ -295,18 +375,14 @@ __global__ void init_faces_hi_kernel(Mesh m, FieldDev fu, FieldDev fD, double *f
     const int nx = m.K[1] * m.N, ny = m.K[0] * m.N;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nx + ny) return;
-    double x, y, ux, uy;
-    if (v < nx) {
-        x = m.hi[0];
-        y = m.lo[1] + (v / m.N + gauss_node(v % m.N, m.N)) * m.h[1];
-    } else {
+    if (v < nx) {  // x = hi at the Gauss nodes of element row v / N
+        const double y = m.lo[1] + (v / m.N + gauss_node(v % m.N, m.N)) * m.h[1];
+        face_fields(fu, fD, m, 0, v / m.N, m.K[0], v % m.N, m.hi[0], y, faceUhi[v], faceBhi[v]);
+    } else {  // y = hi at the Gauss nodes of element column w / N
         const int w = v - nx;
-        x = m.lo[0] + (w / m.N + gauss_node(w % m.N, m.N)) * m.h[0];
-        y = m.hi[1];
+        const double x = m.lo[0] + (w / m.N + gauss_node(w % m.N, m.N)) * m.h[0];
+        face_fields(fu, fD, m, 1, w / m.N, m.K[1], w % m.N, x, m.hi[1], faceUhi[v], faceBhi[v]);
     }
-    drift_at(fu, x, y, ux, uy);
-    faceUhi[v] = v < nx ? ux : uy;
-    faceBhi[v] = sqrt(2.0 * diffusion_at(fD, x, y));
 }
 
 cudaError_t launch_init_faces_hi(const Mesh &m, const FieldDev &u, const FieldDev &D, double *faceUhi, double *faceBhi,

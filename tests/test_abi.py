@@ -99,3 +99,47 @@ def test_sample_range_and_batch_server_arguments(sl):
     assert L.sl_server_create(C.byref(h), C.byref(cfg)) == -1  # negative cap
     cfg.max_active, cfg.budget_bytes = 0, 0
     assert L.sl_server_create(C.byref(h), C.byref(cfg)) == -1  # no budget
+
+
+def _nodal_init_rc(sl, pb, drift, diffusion):
+    """sl_init's return code for the given sl_field structs (a context that
+    was created, on a machine with a GPU, is freed)."""
+    mesh = sl._mesh(pb)
+    phi = sl._field(sl._PHI, pb["phi0"])
+    opt = sl.sl_options()
+    opt.device = -1
+    h = C.c_void_p()
+    rc = sl.lib().sl_init(C.byref(h), C.byref(mesh), pb["N"], pb["M"], C.byref(drift), C.byref(diffusion),
+                          C.byref(phi), C.byref(opt))
+    if rc == 0:
+        sl.lib().sl_free(h)
+    return rc
+
+
+def test_nodal_fields_are_checked_before_device(sl):
+    """Nodal drift / diffusion: a missing node table, a negative or NaN D at a
+    node, or a negative D in a read interface entry is SL_ERR_ARG; on a
+    periodic line the last interface entry is not read, so a NaN there passes
+    the checks (and the call goes on to the device)."""
+    import numpy as np
+
+    pb = I.with_(I.config1(), K=(3,), N=4)
+    u = sl._field(sl._U, pb["drift"])
+    D = sl._field(sl._D, pb["diffusion"])
+    none = sl.sl_field()
+    none.kind = sl._U["nodal"]
+    assert _nodal_init_rc(sl, pb, none, D) == -1
+    none.kind = sl._D["nodal"]
+    assert _nodal_init_rc(sl, pb, u, none) == -1
+    good = np.full((3, 4), 0.01)
+    for bad in (-1e-3, np.nan):
+        nodes = good.copy()
+        nodes[1, 2] = bad
+        assert _nodal_init_rc(sl, pb, u, sl._field(sl._D, ("nodal", nodes))) == -1
+    face = np.full(4, 0.01)
+    face[1] = -0.01
+    assert _nodal_init_rc(sl, pb, u, sl._field(sl._D, ("nodal", good, face))) == -1
+    face[1], face[3] = 0.01, np.nan  # the periodic line's last interface: not read
+    assert _nodal_init_rc(sl, pb, u, sl._field(sl._D, ("nodal", good, face))) != -1
+    dirichlet = I.with_(pb, periodic=False)  # ... but read at a Dirichlet boundary
+    assert _nodal_init_rc(sl, dirichlet, u, sl._field(sl._D, ("nodal", good, face))) == -1
