@@ -221,7 +221,9 @@ def leg_batch(sl, stream):
     import torch
 
     out = {}
-    two_d = [pb for pb in I.batch_instances(512) if pb["N"] <= 8][:12]
+    draws = I.batch_instances(512)
+    two_d = [pb for pb in draws if pb["N"] <= 8][:12]
+    high = [dict(pb, M=64) for pb in draws if pb["N"] >= 9][:4]  # Gram rows split over lanes at N >= 11
     one_d = []
     rng = np.random.default_rng(45)
     for i in range(32):
@@ -229,8 +231,8 @@ def leg_batch(sl, stream):
         pb["seed"] = 7000 + i
         one_d.append(pb)
     small = I.small_instances_1d()
-    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config5_1d_mix", one_d, 20),
-                             ("small_1d_uneven", small, 20)):
+    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config4_high_orders", high, 1),
+                             ("config5_1d_mix", one_d, 20), ("small_1d_uneven", small, 20)):
         for pb in pbs:  # half of each instance's particle bound (2D: edge distance)
             pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
         esu = sum(int(np.prod(pb["K"])) * pb["M"] for pb in pbs) * steps
@@ -258,9 +260,11 @@ def leg_batch(sl, stream):
                      "speedup": t_seq / t_batch, "tuned_grids": grids, "tune_ms": tune_ms}
     out["small_1d_uneven"]["what"] = ("256 instances, K ~ U{8..64}, N ~ U{4..8}, M ~ U{16..128}: each alone is "
                                       "far from filling the GPU, so one-by-one stepping is launch-bound")
-    out["note"] = ("config 4 as drawn (512 instances, N up to 12, 100 steps, ~8.8e10 ESU) is not run: 2D N>10 is "
-                   "not supported and the 2D path runs at ~1e7 ESU/s at N=8; the first 12 draws with N<=8 are "
-                   "timed for one step")
+    out["config4_high_orders"]["what"] = ("the first 4 config-4 draws with N >= 9, M reduced to 64, one step "
+                                          "(orders 11 and 12 split each Gram row over four lanes)")
+    out["note"] = ("config 4 as drawn (512 instances, N up to 12, 100 steps, ~8.8e10 ESU) is not run: the 2D path "
+                   "runs at ~1e7 ESU/s at N=8 and the cost grows as N^6; the first 12 draws with N<=8 and the "
+                   "first 4 with N>=9 (M=64) are timed for one step")
     return out
 
 
@@ -316,7 +320,7 @@ def leg_serving(sl, duration=5.0, drain=10.0, max_active=0):
             "esu_per_s": st["esu_per_s"], "memory_peak_bytes": st["memory_peak"], "light_slices": st["slices"],
             "scheduler_busy_s": st["sched_busy_s"], "launch_s": st["launch_s"], "launch_max_s": st["launch_max_s"],
             "by_class": per_class, "note": "the offered 2D load exceeds the GPU's capacity; heavy requests still queued at the deadline are "
-                    "counted as pending; 2D N > 10 is not provided in FP32 (those requests fail)",
+                    "counted as pending",
             "config": "budget 64 GiB (reserved at creation), slice 5 steps, 2 heavy slots, heavy 2D launches "
                       "of ~2e10 flop with <= 2 queued, FP32 (pair state), 20 steps per request, "
                       f"CUDA_DEVICE_MAX_CONNECTIONS={os.environ.get('CUDA_DEVICE_MAX_CONNECTIONS', '8')}"}

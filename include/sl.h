@@ -167,7 +167,7 @@ int sl_preload(int device);
 /* Creates a solver for M samples of order N (N Gauss nodes per direction,  */
 /* 2 <= N <= 16) on `mesh`, evaluates the fields at the nodes and faces and  */
 /* sets every sample to phi0 (Section 5.1).  1D: K <= 2048 elements.         */
-/* 2D: N <= 8 in SL_FP64, N <= 10 in the FP32 modes (SL_ERR_UNSUPPORTED       */
+/* 2D: N <= 11 in SL_FP64, N <= 12 in the FP32 modes (SL_ERR_UNSUPPORTED     */
 /* otherwise); in 2D both FP32 modes run the FP32 Gram solve with one         */
 /* refinement step.                                                           */
 /* The step counter starts at 0.  opt may be NULL (seed 0, SL_FP64).         */

@@ -321,7 +321,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     const int precision = opt ? opt->precision : SL_FP64;
     if (precision != SL_FP64 && precision != SL_MIXED && precision != SL_FP32) return SL_ERR_ARG;
     if (dim == 1 && mesh->K[0] > sl::kMaxThreads1D * sl::kMaxCluster1D) return SL_ERR_UNSUPPORTED;
-    if (dim == 2 && N > (precision == SL_FP64 ? 8 : 10)) return SL_ERR_UNSUPPORTED;
+    if (dim == 2 && N > (precision == SL_FP64 ? 11 : 12)) return SL_ERR_UNSUPPORTED;
     if (opt && (opt->sample0 < 0 || opt->sample0 + M > (1ll << 32))) return SL_ERR_ARG;
     const double bc_w = opt && opt->bc_weight > 0.0 ? opt->bc_weight : 1.0;
     if (opt && std::isnan(opt->bc_weight)) return SL_ERR_ARG;

@@ -83,12 +83,31 @@ struct Vec16<double> {
     __device__ static double2 make(double a, double b, double, double) { return make_double2(a, b); }
 };
 
+// Lanes per Gram row: one while a row of n values fits in a thread's
+// registers (FP32 n <= 81, FP64 n <= 64); above that the row's columns are
+// split over SP adjacent lanes of one warp, which exchange the pivot-column
+// entries by shuffles.  FP32 N = 10 would fit in one lane but runs 1.33x
+// faster on two (more warps per SM); N = 9 runs faster on one.
+template <int N, typename R>
+constexpr int split2d()
+{
+    return std::is_same<R, float>::value ? (N <= 9 ? 1 : (N <= 10 ? 2 : 4)) : (N <= 8 ? 1 : (N <= 10 ? 2 : 4));
+}
+
 template <int N, typename R>
 struct Geo2D {
     static constexpr int n = N * N;
-    static constexpr int GS = (n + 31) / 32 * 32;               // threads per group
+    static constexpr int SP = split2d<N, R>();                  // lanes per row
+    static constexpr int VWg = sizeof(R) == 4 ? 4 : 2;          // values per 16 bytes
+    // columns per lane (SP > 1), widened by one 16-byte vector where a lane's
+    // block would span a multiple of 128 bytes: the lanes of a row then read
+    // a shared row at offsets in different banks
+    static constexpr int NC0 = ((n + SP - 1) / SP + VWg - 1) / VWg * VWg;
+    static constexpr int NC = (NC0 * int(sizeof(R))) % 128 == 0 ? NC0 + VWg : NC0;
+    static constexpr int GS = (SP * n + 31) / 32 * 32;          // threads per group
     static constexpr int GPC = GS >= kGroupThreads2D ? 1 : kGroupThreads2D / GS;  // groups per CTA
-    static constexpr int LD = (n + 3) & ~3;                     // row stride (16-byte rows)
+    static constexpr int kBlock = GPC * GS;                     // threads per CTA
+    static constexpr int LD = (SP == 1 ? n : (n > SP * NC ? n : SP * NC)) + 3 & ~3;  // row stride (16-byte rows)
     static constexpr int P = n + 4 * N;                         // stacked rows
     // per-group shared memory (elements of R)
     static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
@@ -104,11 +123,11 @@ struct Geo2D {
 // BATCH = true: `ninst` instances of the same N, instance i owning groups
 // [prefix[i], prefix[i+1]) (its E*M element-samples).
 template <int N, typename R, int PHASE, bool BATCH>
-__global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::value && N <= 8) ? 2 : 1) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
+__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::value && N <= 8) ? 2 : 1) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
                                                                     const long long *__restrict__ prefix, int ninst, int t)
 {
     using G = Geo2D<N, R>;
-    constexpr int n = G::n, LD = G::LD;
+    constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
     constexpr int P = PHASE == 1 ? n : G::P;  // rows of the system solved in this phase
     using VV = Vec16<R>;
     using VT = typename VV::T;
@@ -123,7 +142,11 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     R *sh0 = slam + N;        // [N] h_i(0)
     R *sh1 = sh0 + N;         // [N] h_i(1)
     const int grp = threadIdx.x / G::GS;
-    const int c = threadIdx.x - grp * G::GS;  // thread's node / row / column index
+    const int tig = threadIdx.x - grp * G::GS;  // thread in the group
+    const int c = tig / SP;                     // thread's node / row / column index
+    const int h = tig - c * SP;                 // column block of the row (SP > 1)
+    const bool lead = h == 0;                   // the row's lane for per-row work
+    const int rowbase = (threadIdx.x & 31) - h; // lane of the row's first thread
     R *gbase = tab + ((G::kTables + 3) & ~3) + grp * G::kGroup;
     R *Vs = gbase;                 // [P][LD] stacked rows
     R *rhs = Vs + G::kRows;        // [P] right-hand side (relative to c)
@@ -170,7 +193,8 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     const int s = group_active ? int(gid / E) : 0;
     const int e = group_active ? int(gid % E) : 0;
     const int kx = e % a.Kx, ky = e / a.Kx;
-    const bool real = group_active && c < n;
+    const bool real = group_active && c < n;     // every lane of a real row
+    const bool real_lead = real && lead;          // its per-row work
     const int bar_id = 1 + grp;
 
     // reference value and own state
@@ -185,7 +209,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
         } else {
             ch = cv;
         }
-        if (real) {
+        if (real_lead) {
             const State qv = Qg[qoff + c];
             if constexpr (kPair) {
                 qh = qv.x;
@@ -198,7 +222,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     const int ip = c % N, jp = c / N;
     R hx[N], hy[N];
     R ph = R(0);
-    if (real) {
+    if (real_lead) {
         const long long V = (long long)E * n;
         const double dWx = a.dW[((long long)t * a.M + s) * 2 + 0];
         const double dWy = a.dW[((long long)t * a.M + s) * 2 + 1];
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     const long long fbase = (long long)s * E;
     if constexpr (PHASE == 2) {
         // face rows of B and the upwinded face values g (Eq. bnd_update)
-        if (group_active && c < 4 * N) {
+        if (group_active && lead && c < 4 * N) {
             const int side = c / N, f = c % N;
             R *row = Vs + (n + c) * LD;
 #pragma unroll
@@ -344,20 +368,33 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     group_sync(bar_id, G::GS);
 
     // Gram row c: G[c][c'] = sum_p S[p][c] S[p][c'], b_c = sum_p S[p][c] rhs_p
-    R gr[n];
+    // (SP > 1: lane h holds the columns c' = h NC + j, j < NC, of row c)
+    constexpr int NG = SP == 1 ? n : NC;
+    const int col0 = h * NC;  // first column of this lane (SP > 1)
+    R gr[NG];
 #pragma unroll
-    for (int q = 0; q < n; ++q) gr[q] = R(0);
+    for (int q = 0; q < NG; ++q) gr[q] = R(0);
     R bc = R(0);
     if (real) {
         for (int p = 0; p < P; ++p) {
             const R vpc = Vs[p * LD + c];
             const R *rowp = Vs + p * LD;
+            if constexpr (SP == 1) {
 #pragma unroll
-            for (int q = 0; q < n; q += VW) {
-                const VT v = *reinterpret_cast<const VT *>(rowp + q);
+                for (int q = 0; q < n; q += VW) {
+                    const VT v = *reinterpret_cast<const VT *>(rowp + q);
 #pragma unroll
-                for (int i = 0; i < VW; ++i)
-                    if (q + i < n) gr[q + i] = fma(vpc, VV::at(v, i), gr[q + i]);
+                    for (int i = 0; i < VW; ++i)
+                        if (q + i < n) gr[q + i] = fma(vpc, VV::at(v, i), gr[q + i]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NC; j += VW) {
+                    const VT v = *reinterpret_cast<const VT *>(rowp + col0 + j);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i)
+                        if (col0 + j + i < n) gr[j + i] = fma(vpc, VV::at(v, i), gr[j + i]);
+                }
             }
             bc = fma(vpc, rhs[p], bc);
         }
@@ -367,46 +404,88 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
     // kept in the eliminated positions for the refinement replay
     R diag = R(1);
     bool bad = false;
+    // entry k of row c, from the lane holding column k (SP > 1: a shuffle
+    // executed by every lane of the warp; k is a compile-time index)
+    auto row_entry = [&](const int k) -> R {
+        if constexpr (SP == 1) {
+            return gr[k];
+        } else {
+            const R mine = h == k / NC ? gr[k % NC] : R(0);
+            return __shfl_sync(0xffffffffu, mine, rowbase + k / NC);
+        }
+    };
 #pragma unroll
     for (int k = 0; k < n; ++k) {
         R *pr = piv + (k & 1) * (LD + 4);
-        if (c == k) {
+        if constexpr (SP == 1) {
+            if (c == k) {
 #pragma unroll
-            for (int q = 0; q < n; q += VW) {
-                R v4[4];
+                for (int q = 0; q < n; q += VW) {
+                    R v4[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
-                *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                    for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
+                    *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                }
+                pr[LD] = bc;
+                pr[LD + 1] = R(1) / gr[k];
+                diag = gr[k];
             }
-            pr[LD] = bc;
-            pr[LD + 1] = R(1) / gr[k];
-            diag = gr[k];
+        } else {
+            if (c == k) {  // every lane of the pivot row publishes its columns
+#pragma unroll
+                for (int j = 0; j < NC; j += VW) {
+                    R v4[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v4[i] = i < VW ? gr[j + i] : R(0);
+                    *reinterpret_cast<VT *>(pr + col0 + j) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                }
+                if (lead) pr[LD] = bc;
+                if (h == k / NC) {
+                    pr[LD + 1] = R(1) / gr[k % NC];
+                    diag = gr[k % NC];
+                }
+            }
         }
         group_sync(bar_id, G::GS);
+        const R gk = row_entry(k);
         if (real && c != k) {
-            const R l = gr[k] * pr[LD + 1];
+            const R l = gk * pr[LD + 1];
             // columns < k hold multipliers (eliminated); only q > k change
+            if constexpr (SP == 1) {
 #pragma unroll
-            for (int q = 0; q < n; q += VW) {
-                if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
-                const VT v = *reinterpret_cast<const VT *>(pr + q);
+                for (int q = 0; q < n; q += VW) {
+                    if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
+                    const VT v = *reinterpret_cast<const VT *>(pr + q);
 #pragma unroll
-                for (int i = 0; i < VW; ++i)
-                    if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+                    for (int i = 0; i < VW; ++i)
+                        if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+                }
+                gr[k] = l;
+            } else {
+#pragma unroll
+                for (int j = 0; j < NC; j += VW) {
+                    const VT v = *reinterpret_cast<const VT *>(pr + col0 + j);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) {
+                        const int q = col0 + j + i;
+                        if (q > k && q < n) gr[j + i] = fma(-l, VV::at(v, i), gr[j + i]);
+                    }
+                }
+                if (h == k / NC) gr[k % NC] = l;
             }
             bc = fma(-l, pr[LD], bc);
-            gr[k] = l;
         }
     }
-    R x = real ? bc / diag : R(0);
-    bad |= real && !(diag > R(0));
+    if constexpr (SP > 1) diag = __shfl_sync(0xffffffffu, diag, rowbase + (c < n ? c : 0) / NC);  // the row's pivot
+    R x = real_lead ? bc / diag : R(0);
+    bad |= real_lead && !(diag > R(0));
 
     if constexpr (kPair) {
         // one step of iterative refinement of the stacked least-squares
         // residual: r = S^T (rhs - S x), G dx = r, x += dx
-        if (c < n) vec[c] = x;  // the group may have more threads than nodes
+        if (c < n && lead) vec[c] = x;  // the group may have more threads than nodes
         group_sync(bar_id, G::GS);
-        if (real) {
+        if (real_lead) {
             // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
             R t2[N];
 #pragma unroll
@@ -423,7 +502,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
             for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
             res[c] = rhs[c] - vx;
         }
-        if (PHASE == 2 && group_active && c < 4 * N) {
+        if (PHASE == 2 && group_active && lead && c < 4 * N) {
             const R *row = Vs + (n + c) * LD;
             R bx = R(0);
 #pragma unroll
@@ -438,7 +517,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
         }
         group_sync(bar_id, G::GS);
         R rc = R(0);
-        if (real)
+        if (real_lead)
             for (int p = 0; p < P; p += VW) {
                 const VT rv = *reinterpret_cast<const VT *>(res + p);
 #pragma unroll
@@ -448,19 +527,20 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             R *pr = piv + (k & 1) * (LD + 4);
-            if (c == k) pr[0] = rc;
+            if (c == k && lead) pr[0] = rc;
             group_sync(bar_id, G::GS);
-            if (real && c != k) rc = fma(-gr[k], pr[0], rc);
+            const R gk = row_entry(k);
+            if (real_lead && c != k) rc = fma(-gk, pr[0], rc);
         }
-        x += real ? rc / diag : R(0);
+        x += real_lead ? rc / diag : R(0);
     }
-    bad |= real && !isfinite(x);
+    bad |= real_lead && !isfinite(x);
 
     if constexpr (PHASE == 1) {
         // face values of the advected interpolant (alpha - c = x) at the 4N face points
-        if (c < n) vec[c] = x;  // the group may have more threads than nodes
+        if (c < n && lead) vec[c] = x;  // the group may have more threads than nodes
         group_sync(bar_id, G::GS);
-        if (group_active && c < 4 * N) {
+        if (group_active && lead && c < 4 * N) {
             const int side = c / N, f = c % N;
             R v = R(0);
             if (side < 2) {
@@ -482,7 +562,7 @@ __global__ void __launch_bounds__(kGroupThreads2D, (std::is_same<R, float>::valu
             faces[(fbase + e) * 4 * N + c] = out;
         }
     } else {
-        if (real) {
+        if (real_lead) {
             if constexpr (kPair) {
                 float hi, lo;
                 two_sum2d(ch, x, hi, lo);
@@ -504,7 +584,7 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
     // a launch covers at most `chunk` groups (a multiple of the groups per CTA)
     const long long chunk =
         a.chunk > 0 ? std::min(groups, (a.chunk + G::GPC - 1) / G::GPC * G::GPC) : groups;
-    const unsigned block = unsigned(G::GPC * G::GS);
+    const unsigned block = unsigned(G::kBlock);
     auto k1 = sl2d_step_kernel<N, R, 1, false>;
     auto k2 = sl2d_step_kernel<N, R, 2, false>;
     Step2DArgs b = a;
@@ -548,7 +628,7 @@ cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
     using G = Geo2D<N, R>;
     const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
     const unsigned grid = unsigned((b.total_groups + G::GPC - 1) / G::GPC);
-    const unsigned block = unsigned(G::GPC * G::GS);
+    const unsigned block = unsigned(G::kBlock);
     auto k1 = sl2d_step_kernel<N, R, 1, true>;
     auto k2 = sl2d_step_kernel<N, R, 2, true>;
     Step2DArgs none = {};

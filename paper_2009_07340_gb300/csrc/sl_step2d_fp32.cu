@@ -1,5 +1,6 @@
 // 2D step kernels in FP32 with float-pair state and one refinement step
-// (see sl_step2d.cuh); N <= 10 (a Gram row of up to 100 floats per thread).
+// (see sl_step2d.cuh); N <= 12 (a Gram row of up to 81 floats per thread,
+// split over two or four lanes above that).
 // Both FP32 modes (SL_MIXED, SL_FP32) run this kernel in 2D: an FP64 Gram
 // factor would cost ~n^3/2 FP64 operations per element-sample, at 1/64 of the
 // FP32 rate on GB300.  The orders are compiled in sl_step2d_fp32_nNN.cu.
@@ -24,6 +25,10 @@ cudaError_t launch_step2d_fp32_n9(const Step2DArgs &a, cudaStream_t st);
 cudaError_t launch_step2d_batch_fp32_n9(const Batch2DLaunch &b, cudaStream_t st);
 cudaError_t launch_step2d_fp32_n10(const Step2DArgs &a, cudaStream_t st);
 cudaError_t launch_step2d_batch_fp32_n10(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n11(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n11(const Batch2DLaunch &b, cudaStream_t st);
+cudaError_t launch_step2d_fp32_n12(const Step2DArgs &a, cudaStream_t st);
+cudaError_t launch_step2d_batch_fp32_n12(const Batch2DLaunch &b, cudaStream_t st);
 
 cudaError_t preload_step2d_fp32_n2();
 cudaError_t preload_step2d_fp32_n3();
@@ -34,6 +39,8 @@ cudaError_t preload_step2d_fp32_n7();
 cudaError_t preload_step2d_fp32_n8();
 cudaError_t preload_step2d_fp32_n9();
 cudaError_t preload_step2d_fp32_n10();
+cudaError_t preload_step2d_fp32_n11();
+cudaError_t preload_step2d_fp32_n12();
 
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
 {
@@ -47,6 +54,8 @@ cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
     case 8: return launch_step2d_fp32_n8(a, st);
     case 9: return launch_step2d_fp32_n9(a, st);
     case 10: return launch_step2d_fp32_n10(a, st);
+    case 11: return launch_step2d_fp32_n11(a, st);
+    case 12: return launch_step2d_fp32_n12(a, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -54,7 +63,7 @@ cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st)
 cudaError_t preload_step2d_fp32()
 {
     cudaError_t e = cudaSuccess;
-    for (auto f : {preload_step2d_fp32_n2, preload_step2d_fp32_n3, preload_step2d_fp32_n4, preload_step2d_fp32_n5, preload_step2d_fp32_n6, preload_step2d_fp32_n7, preload_step2d_fp32_n8, preload_step2d_fp32_n9, preload_step2d_fp32_n10})
+    for (auto f : {preload_step2d_fp32_n2, preload_step2d_fp32_n3, preload_step2d_fp32_n4, preload_step2d_fp32_n5, preload_step2d_fp32_n6, preload_step2d_fp32_n7, preload_step2d_fp32_n8, preload_step2d_fp32_n9, preload_step2d_fp32_n10, preload_step2d_fp32_n11, preload_step2d_fp32_n12})
         if (e == cudaSuccess) e = f();
     return e;
 }
@@ -71,6 +80,8 @@ cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t
     case 8: return launch_step2d_batch_fp32_n8(b, st);
     case 9: return launch_step2d_batch_fp32_n9(b, st);
     case 10: return launch_step2d_batch_fp32_n10(b, st);
+    case 11: return launch_step2d_batch_fp32_n11(b, st);
+    case 12: return launch_step2d_batch_fp32_n12(b, st);
     default: return cudaErrorNotSupported;
     }
 }

@@ -72,10 +72,10 @@ def test_invalid_precision_and_null(sl):
 
 @pytest.mark.parametrize("bad,precision,code", [
     (dict(K=(2049,)), "fp64", -8),                          # 1D beyond the largest cluster (8 x 256 elements)
-    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=9, drift=("const", [0.1, 0.2]),
-          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp64", -8),   # 2D FP64 N > 8
-    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=11, drift=("const", [0.1, 0.2]),
-          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp32", -8),   # 2D FP32 N > 10
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=12, drift=("const", [0.1, 0.2]),
+          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp64", -8),   # 2D FP64 N > 11
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=13, drift=("const", [0.1, 0.2]),
+          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp32", -8),   # 2D FP32 N > 12
 ])
 def test_unsupported_sizes_rejected_before_device(sl, bad, precision, code):
     pb = I.config1()

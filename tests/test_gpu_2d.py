@@ -1,7 +1,8 @@
 """GPU parity of the 2D path (tensor-product elements) against the FP64 CPU
 oracle, through the C ABI.  SL_FP64 within 1e-10 of the oracle; the FP32
 path (float-pair state, FP32 Gram solve, one refinement step) within 1e-5 of
-the FP64 path on the moments."""
+the FP64 path on the moments.  Orders up to 12 (FP32) and 11 (FP64), the
+high ones with each Gram row split over several lanes."""
 
 import numpy as np
 import pytest
@@ -107,19 +108,40 @@ def test_config3_mesh_fp32_vs_fp64_edge_dt(sl, orc):
         assert _rel(s.samples(0, 1)[0], ref) <= FP64_TOL
 
 
-@pytest.mark.parametrize("N", [9, 10])
+@pytest.mark.parametrize("N", [9, 10, 11, 12])
 def test_fp32_high_order_vs_oracle(sl, orc, N):
+    # N = 11, 12: each Gram row split over four lanes
     pb = _rot(K=(3, 3), N=N, M=2, steps=3, orc=orc)
     e_mean, _, e_st = _pair(sl, orc, pb, precision="fp32")
     assert e_mean <= MIXED_TOL and e_st <= MIXED_TOL
 
 
+@pytest.mark.parametrize("N", [9, 10, 11])
+def test_fp64_high_order_vs_oracle(sl, orc, N):
+    # N = 9, 10: each Gram row split over two lanes; N = 11: four
+    pb = _rot(K=(3, 2), N=N, M=3, steps=3, orc=orc)
+    e_mean, e_m2, e_st = _pair(sl, orc, pb)
+    assert e_mean <= FP64_TOL and e_m2 <= FP64_TOL and e_st <= FP64_TOL
+
+
+@pytest.mark.parametrize("N", [10, 11])
+def test_fp32_vs_fp64_high_order(sl, orc, N):
+    pb = _rot(K=(4, 4), N=N, M=16, steps=10, orc=orc)
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        m64, _ = s.moments()
+    with sl.Solver(pb, "fp32") as s:
+        s.step()
+        m32, _ = s.moments()
+    assert _rel(m32, m64) <= MIXED_TOL
+
+
 def test_order_limits(sl, orc):
-    pb = _rot(K=(2, 2), N=9, M=1, steps=1, orc=orc)
+    pb = _rot(K=(2, 2), N=12, M=1, steps=1, orc=orc)
     with pytest.raises(sl.SLError) as e:
         sl.Solver(pb, "fp64")
     assert e.value.code == -8
-    pb = _rot(K=(2, 2), N=11, M=1, steps=1, orc=orc)
+    pb = _rot(K=(2, 2), N=13, M=1, steps=1, orc=orc)
     with pytest.raises(sl.SLError) as e:
         sl.Solver(pb, "fp32")
     assert e.value.code == -8

@@ -76,6 +76,22 @@ def test_batch_equals_alone_2d_and_mixed_dims(sl, orc, precision):
             assert np.array_equal(b.samples(i), _alone(sl, pb, precision, 6)), i
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_high_orders_equal_alone(sl, orc, precision):
+    # 2D orders whose Gram rows are split over several lanes (FP64 N = 9..11,
+    # FP32 N = 11), batched with a one-lane order
+    pbs = []
+    for i, (K, N, M) in enumerate([((2, 2), 9, 3), ((3, 2), 11, 2), ((2, 3), 4, 4)]):
+        pb = I.problem(2, K, (0.0, 0.0), (1.0, 1.0), N, M, 0, 0.0, 300 + i, ("rotation", [2 * np.pi, 0.5, 0.5]),
+                       ("const", [0.004]), ("gauss", [1.0, 0.2, 0.5, 0.5]))
+        pb["dt"] = 0.4 * orc.dt_max(pb)
+        pbs.append(pb)
+    with sl.Batch(pbs, precision) as b:
+        b.step(2)
+        for i, pb in enumerate(pbs):
+            assert np.array_equal(b.samples(i), _alone(sl, pb, precision, 2)), i
+
+
 def test_tuner_restores_state_and_picks_grids(sl, orc):
     pbs = _mix1d(orc)
     with sl.Batch(pbs, "fp32") as b:
