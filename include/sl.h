@@ -141,9 +141,10 @@ typedef struct {
     int components;          /* scalar fields per sample sharing the particles and    */
                              /* so the remap factorization (Section 5.3: its cost     */
                              /* does not grow with the components); 0 or 1: one; 2:   */
-                             /* two (1D, periodic, SL_FP64 or SL_FP32; otherwise     */
+                             /* two (periodic meshes; 1D in SL_FP64 or SL_FP32, 2D   */
+                             /* N <= 8 in any precision; otherwise                   */
                              /* SL_ERR_UNSUPPORTED).  Each sample's state, samples   */
-                             /* and moments are [components][elements][N]; every     */
+                             /* and moments are [components][elements][N^dim]; every */
                              /* component starts from phi0 (set others with          */
                              /* sl_set_samples)                                       */
     int reseed_every;        /* > 0: after every step n with (n + 1) % reseed_every  */

@@ -182,6 +182,7 @@ cudaError_t ensure_loaded()
     if (e == cudaSuccess) e = preload_step1d_fp32();
     if (e == cudaSuccess) e = preload_step2d_fp64();
     if (e == cudaSuccess) e = preload_step2d_fp32();
+    if (e == cudaSuccess) e = preload_step2d_c2();
     if (e == cudaSuccess && !g_pool[dev]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -329,7 +330,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (opt && opt->reseed_every < 0) return SL_ERR_ARG;
     const int ncomp = opt && opt->components > 1 ? opt->components : 1;
     if (opt && (opt->components < 0 || opt->components > 2)) return SL_ERR_UNSUPPORTED;
-    if (ncomp > 1 && (dim != 1 || precision == SL_MIXED || !mesh->periodic[0])) return SL_ERR_UNSUPPORTED;
+    if (ncomp > 1 && (!mesh->periodic[0] || (dim == 1 && precision == SL_MIXED) || (dim == 2 && N > 8)))
+        return SL_ERR_UNSUPPORTED;  // two fields: periodic; 1D FP64 / FP32; 2D N <= 8 (any precision)
 
     if (opt && opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return SL_ERR_CUDA;
     if (sl::ensure_loaded() != cudaSuccess) {
@@ -389,7 +391,7 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
               (dim == 1 || (dalloc(c, &c->faceUhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess &&
                             dalloc(c, &c->faceBhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess));
     if (ok && dim == 2)
-        ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * m.E * 4 * N * c->state_elem) == cudaSuccess;
+        ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * ncomp * m.E * 4 * N * c->state_elem) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         sl_free(c);
@@ -567,7 +569,10 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.faceUhi = c->faceUhi;
             a.faceBhi = c->faceBhi;
             a.throttle = c->launch_chunk > 0 ? &c->throttle : nullptr;
-            e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
+            if (c->ncomp > 1)
+                e = sl::launch_step2d_c2(a, m.N, c->precision == SL_FP64, c->st);
+            else
+                e = c->precision == SL_FP64 ? sl::launch_step2d_fp64(a, m.N, c->st) : sl::launch_step2d_fp32(a, m.N, c->st);
         }
         if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;
         if (e != cudaSuccess) return fail_cuda(c);

@@ -131,6 +131,8 @@ cudaError_t launch_step2d_batch_fp64(const Batch2DLaunch &b, int N, cudaStream_t
 cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st);
+// two fields per sample (Q [M][2][E][n], faces [M][2][E][4N]), N <= 8
+cudaError_t launch_step2d_c2(const Step2DArgs &a, int N, bool fp64, cudaStream_t st);
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
                                const double *phi0_nodal_dev, double *xi, double *nodeU, double *nodeB,
                                double *nodeDiv, double *faceU, double *faceB, void *Q, int M,
@@ -175,6 +177,7 @@ cudaError_t preload_step1d_mixed();
 cudaError_t preload_step1d_fp32();
 cudaError_t preload_step2d_fp64();
 cudaError_t preload_step2d_fp32();
+cudaError_t preload_step2d_c2();
 cudaError_t preload_setup();
 cudaError_t ensure_loaded();
 

@@ -94,7 +94,7 @@ constexpr int split2d()
     return std::is_same<R, float>::value ? (N <= 9 ? 1 : (N <= 10 ? 2 : 4)) : (N <= 8 ? 1 : (N <= 10 ? 2 : 4));
 }
 
-template <int N, typename R>
+template <int N, typename R, int NCOMP = 1>
 struct Geo2D {
     static constexpr int n = N * N;
     static constexpr int SP = split2d<N, R>();                  // lanes per row
@@ -111,7 +111,8 @@ struct Geo2D {
     static constexpr int P = n + 4 * N;                         // stacked rows
     // per-group shared memory (elements of R)
     static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
-    static constexpr int kRows = P * LD, kRhs = P4, kPiv = 2 * (LD + 4), kVec = P4, kRes = P4;
+    // rhs, vec and res hold one P4-long array per field
+    static constexpr int kRows = P * LD, kRhs = NCOMP * P4, kPiv = 2 * (LD + 4), kVec = NCOMP * P4, kRes = NCOMP * P4;
     static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
     // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N]
     static constexpr int kTables = N * N + 3 * N;
@@ -122,11 +123,15 @@ struct Geo2D {
 // BATCH = false: one instance (a0), group g = element-sample g.
 // BATCH = true: `ninst` instances of the same N, instance i owning groups
 // [prefix[i], prefix[i+1]) (its E*M element-samples).
-template <int N, typename R, int PHASE, bool BATCH>
+// NCOMP = 2: two fields per sample ([M][2][E][n]) on the same particles, so
+// one Gram matrix, one elimination and one upwind choice serve both; each
+// field has its own right-hand side, refinement, faces and state.
+template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1>
 __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::value && N <= 8) ? 2 : 1) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
                                                                     const long long *__restrict__ prefix, int ninst, int t)
 {
-    using G = Geo2D<N, R>;
+    using G = Geo2D<N, R, NCOMP>;
+    constexpr int P4 = G::P4;  // stride of the per-field arrays
     constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
     constexpr int P = PHASE == 1 ? n : G::P;  // rows of the system solved in this phase
     using VV = Vec16<R>;
@@ -149,10 +154,10 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
     const int rowbase = (threadIdx.x & 31) - h; // lane of the row's first thread
     R *gbase = tab + ((G::kTables + 3) & ~3) + grp * G::kGroup;
     R *Vs = gbase;                 // [P][LD] stacked rows
-    R *rhs = Vs + G::kRows;        // [P] right-hand side (relative to c)
-    R *piv = rhs + G::kRhs;        // [2][LD + 4] pivot rows
-    R *vec = piv + G::kPiv;        // [P] broadcast vector
-    R *res = vec + G::kVec;        // [P] residual
+    R *rhs = Vs + G::kRows;        // [NCOMP][P4] right-hand sides (relative to c)
+    R *piv = rhs + G::kRhs;        // [2][LD + 4] pivot rows (+ b of field 0 at LD, 1 / pivot, b of field 1)
+    R *vec = piv + G::kPiv;        // [NCOMP][P4] broadcast vectors
+    R *res = vec + G::kVec;        // [NCOMP][P4] residuals
 
     // node tables depend on N only (every instance of a batch class shares them)
     const double *xi = BATCH ? args[0].xi : a0.xi;
@@ -197,31 +202,36 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
     const bool real_lead = real && lead;          // its per-row work
     const int bar_id = 1 + grp;
 
-    // reference value and own state
+    // reference values and own state, per field
     State *Qg = reinterpret_cast<State *>(a.Q);
-    const long long qoff = ((long long)s * E + e) * n;
-    R ch, cl = R(0), qh = R(0), ql = R(0);
-    {
-        const State cv = Qg[qoff + n / 2];
+    long long qoff[NCOMP];
+    R ch[NCOMP], cl[NCOMP], qh[NCOMP], ql[NCOMP];
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) {
+        qoff[cc] = (((long long)s * NCOMP + cc) * E + e) * n;
+        cl[cc] = qh[cc] = ql[cc] = R(0);
+        const State cv = Qg[qoff[cc] + n / 2];
         if constexpr (kPair) {
-            ch = cv.x;
-            cl = cv.y;
+            ch[cc] = cv.x;
+            cl[cc] = cv.y;
         } else {
-            ch = cv;
+            ch[cc] = cv;
         }
         if (real_lead) {
-            const State qv = Qg[qoff + c];
+            const State qv = Qg[qoff[cc] + c];
             if constexpr (kPair) {
-                qh = qv.x;
-                ql = qv.y;
+                qh[cc] = qv.x;
+                ql[cc] = qv.y;
             } else {
-                qh = qv;
+                qh[cc] = qv;
             }
         }
     }
     const int ip = c % N, jp = c / N;
     R hx[N], hy[N];
-    R ph = R(0);
+    R ph[NCOMP];
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) ph[cc] = R(0);
     if (real_lead) {
         const long long V = (long long)E * n;
         const double dWx = a.dW[((long long)t * a.M + s) * 2 + 0];
@@ -233,12 +243,15 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
         const R dx = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx))) / a.hx);
         const R dy = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy))) / a.hy);
         const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
-        R dq = qh - ch;
-        if constexpr (kPair) dq += ql - cl;
-        if constexpr (kPair)
-            ph = dq - __fmul_rn(gam, qh);
-        else
-            ph = dq - __dmul_rn(gam, qh);
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) {
+            R dq = qh[cc] - ch[cc];
+            if constexpr (kPair) dq += ql[cc] - cl[cc];
+            if constexpr (kPair)
+                ph[cc] = dq - __fmul_rn(gam, qh[cc]);
+            else
+                ph[cc] = dq - __dmul_rn(gam, qh[cc]);
+        }
         // Gauss-node basis at the particle: h_i'(x) = lam_i' prod_{m != i'} (x - zeta_m),
         // x - zeta_m = Z[ip][m] + dx (node difference plus displacement)
         R pre = R(1);
@@ -275,12 +288,15 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
             for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? hx[(q + i) % N] * hy[(q + i) / N] : R(0);
             *reinterpret_cast<VT *>(Vs + c * LD + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
         }
-        rhs[c] = ph;
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) rhs[cc * P4 + c] = ph[cc];
     }
 
     using FaceT = typename std::conditional<kPair, float2, double>::type;
     FaceT *faces = reinterpret_cast<FaceT *>(a.faces);
-    const long long fbase = (long long)s * E;
+    long long fbase[NCOMP];  // [M][NCOMP][E][4N]
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) fbase[cc] = ((long long)s * NCOMP + cc) * E;
     if constexpr (PHASE == 2) {
         // face rows of B and the upwinded face values g (Eq. bnd_update)
         if (group_active && lead && c < 4 * N) {
@@ -332,25 +348,28 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
             }
             const bool xface = side < 2;
             // low element's far face (right / top) or high element's near face (left / bottom)
-            FaceT gv;
-            if (from_low && ghost_low)  // left [Ky][N] or bottom [Kx][N] boundary values
-                gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 0 ? (long long)ky * N + f
-                                                                        : 2LL * a.Ky * N + (long long)kx * N + f)]);
-            else if (!from_low && ghost_high)  // right [Ky][N] or top [Kx][N]
-                gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 1 ? (long long)a.Ky * N + (long long)ky * N + f
-                                                                        : 2LL * a.Ky * N + (long long)a.Kx * N +
-                                                                              (long long)kx * N + f)]);
-            else
-                gv = from_low ? faces[(fbase + e_low) * 4 * N + (xface ? N : 3 * N) + f]
-                              : faces[(fbase + e_high) * 4 * N + (xface ? 0 : 2 * N) + f];
-            R gr;
-            if constexpr (kPair)
-                gr = (gv.x - ch) + (gv.y - cl);
-            else
-                gr = gv - ch;
             // the face rows and values carry the boundary weight w (1 by default)
             const R w = R(a.w);
-            rhs[n + c] = w * gr;
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {  // (two fields: periodic meshes only, no ghosts)
+                FaceT gv;
+                if (from_low && ghost_low)  // left [Ky][N] or bottom [Kx][N] boundary values
+                    gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 0 ? (long long)ky * N + f
+                                                                            : 2LL * a.Ky * N + (long long)kx * N + f)]);
+                else if (!from_low && ghost_high)  // right [Ky][N] or top [Kx][N]
+                    gv = ghost_face2d<FaceT>(a.ghost[t * a.ghost_w + (side == 1 ? (long long)a.Ky * N + (long long)ky * N + f
+                                                                            : 2LL * a.Ky * N + (long long)a.Kx * N +
+                                                                                  (long long)kx * N + f)]);
+                else
+                    gv = from_low ? faces[(fbase[cc] + e_low) * 4 * N + (xface ? N : 3 * N) + f]
+                                  : faces[(fbase[cc] + e_high) * 4 * N + (xface ? 0 : 2 * N) + f];
+                R gr;
+                if constexpr (kPair)
+                    gr = (gv.x - ch[cc]) + (gv.y - cl[cc]);
+                else
+                    gr = gv - ch[cc];
+                rhs[cc * P4 + n + c] = w * gr;
+            }
             if (side == 0)
 #pragma unroll
                 for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh0[ii];
@@ -374,7 +393,9 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
     R gr[NG];
 #pragma unroll
     for (int q = 0; q < NG; ++q) gr[q] = R(0);
-    R bc = R(0);
+    R bc[NCOMP];
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = R(0);
     if (real) {
         for (int p = 0; p < P; ++p) {
             const R vpc = Vs[p * LD + c];
@@ -396,7 +417,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
                         if (col0 + j + i < n) gr[j + i] = fma(vpc, VV::at(v, i), gr[j + i]);
                 }
             }
-            bc = fma(vpc, rhs[p], bc);
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = fma(vpc, rhs[cc * P4 + p], bc[cc]);
         }
     }
 
@@ -426,7 +448,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
                     for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
                     *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                 }
-                pr[LD] = bc;
+                pr[LD] = bc[0];
+                if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
                 pr[LD + 1] = R(1) / gr[k];
                 diag = gr[k];
             }
@@ -439,7 +462,10 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
                     for (int i = 0; i < 4; ++i) v4[i] = i < VW ? gr[j + i] : R(0);
                     *reinterpret_cast<VT *>(pr + col0 + j) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                 }
-                if (lead) pr[LD] = bc;
+                if (lead) {
+                    pr[LD] = bc[0];
+                    if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
+                }
                 if (h == k / NC) {
                     pr[LD + 1] = R(1) / gr[k % NC];
                     diag = gr[k % NC];
@@ -473,120 +499,151 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::
                 }
                 if (h == k / NC) gr[k % NC] = l;
             }
-            bc = fma(-l, pr[LD], bc);
+            bc[0] = fma(-l, pr[LD], bc[0]);
+            if constexpr (NCOMP > 1) bc[1] = fma(-l, pr[LD + 2], bc[1]);
         }
     }
     if constexpr (SP > 1) diag = __shfl_sync(0xffffffffu, diag, rowbase + (c < n ? c : 0) / NC);  // the row's pivot
-    R x = real_lead ? bc / diag : R(0);
+    R x[NCOMP];
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) x[cc] = real_lead ? bc[cc] / diag : R(0);
     bad |= real_lead && !(diag > R(0));
 
     if constexpr (kPair) {
         // one step of iterative refinement of the stacked least-squares
-        // residual: r = S^T (rhs - S x), G dx = r, x += dx
-        if (c < n && lead) vec[c] = x;  // the group may have more threads than nodes
+        // residual: r = S^T (rhs - S x), G dx = r, x += dx (per field)
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc)
+            if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
         group_sync(bar_id, G::GS);
         if (real_lead) {
             // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
-            R t2[N];
 #pragma unroll
-            for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                R t2[N];
 #pragma unroll
-            for (int q = 0; q < n; q += VW) {
-                const VT v = *reinterpret_cast<const VT *>(vec + q);
+                for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
 #pragma unroll
-                for (int i = 0; i < VW; ++i)
-                    if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                for (int q = 0; q < n; q += VW) {
+                    const VT v = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i)
+                        if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                }
+                R vx = R(0);
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
+                res[cc * P4 + c] = rhs[cc * P4 + c] - vx;
             }
-            R vx = R(0);
-#pragma unroll
-            for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
-            res[c] = rhs[c] - vx;
         }
         if (PHASE == 2 && group_active && lead && c < 4 * N) {
             const R *row = Vs + (n + c) * LD;
-            R bx = R(0);
 #pragma unroll
-            for (int q = 0; q < n; q += VW) {
-                const VT rv = *reinterpret_cast<const VT *>(row + q);
-                const VT xv = *reinterpret_cast<const VT *>(vec + q);
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                R bx = R(0);
 #pragma unroll
-                for (int i = 0; i < VW; ++i)
-                    if (q + i < n) bx = fma(VV::at(rv, i), VV::at(xv, i), bx);
+                for (int q = 0; q < n; q += VW) {
+                    const VT rv = *reinterpret_cast<const VT *>(row + q);
+                    const VT xv = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i)
+                        if (q + i < n) bx = fma(VV::at(rv, i), VV::at(xv, i), bx);
+                }
+                res[cc * P4 + n + c] = rhs[cc * P4 + n + c] - bx;
             }
-            res[n + c] = rhs[n + c] - bx;
         }
         group_sync(bar_id, G::GS);
-        R rc = R(0);
+        R rc[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = R(0);
         if (real_lead)
             for (int p = 0; p < P; p += VW) {
-                const VT rv = *reinterpret_cast<const VT *>(res + p);
 #pragma unroll
-                for (int i = 0; i < VW; ++i)
-                    if (p + i < P) rc = fma(Vs[(p + i) * LD + c], VV::at(rv, i), rc);
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    const VT rv = *reinterpret_cast<const VT *>(res + cc * P4 + p);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i)
+                        if (p + i < P) rc[cc] = fma(Vs[(p + i) * LD + c], VV::at(rv, i), rc[cc]);
+                }
             }
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             R *pr = piv + (k & 1) * (LD + 4);
-            if (c == k && lead) pr[0] = rc;
+            if (c == k && lead)
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) pr[cc] = rc[cc];
             group_sync(bar_id, G::GS);
             const R gk = row_entry(k);
-            if (real_lead && c != k) rc = fma(-gk, pr[0], rc);
+            if (real_lead && c != k)
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = fma(-gk, pr[cc], rc[cc]);
         }
-        x += real_lead ? rc / diag : R(0);
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) x[cc] += real_lead ? rc[cc] / diag : R(0);
     }
-    bad |= real_lead && !isfinite(x);
+#pragma unroll
+    for (int cc = 0; cc < NCOMP; ++cc) bad |= real_lead && !isfinite(x[cc]);
 
     if constexpr (PHASE == 1) {
         // face values of the advected interpolant (alpha - c = x) at the 4N face points
-        if (c < n && lead) vec[c] = x;  // the group may have more threads than nodes
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc)
+            if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
         group_sync(bar_id, G::GS);
         if (group_active && lead && c < 4 * N) {
             const int side = c / N, f = c % N;
-            R v = R(0);
-            if (side < 2) {
-                const R *h = side == 0 ? sh0 : sh1;
 #pragma unroll
-                for (int ii = 0; ii < N; ++ii) v = fma(h[ii], vec[f * N + ii], v);
-            } else {
-                const R *h = side == 2 ? sh0 : sh1;
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                const R *vc = vec + cc * P4;
+                R v = R(0);
+                if (side < 2) {
+                    const R *h = side == 0 ? sh0 : sh1;
 #pragma unroll
-                for (int jj = 0; jj < N; ++jj) v = fma(h[jj], vec[jj * N + f], v);
+                    for (int ii = 0; ii < N; ++ii) v = fma(h[ii], vc[f * N + ii], v);
+                } else {
+                    const R *h = side == 2 ? sh0 : sh1;
+#pragma unroll
+                    for (int jj = 0; jj < N; ++jj) v = fma(h[jj], vc[jj * N + f], v);
+                }
+                FaceT out;
+                if constexpr (kPair) {
+                    two_sum2d(ch[cc], v, out.x, out.y);
+                    out.y += cl[cc];
+                } else {
+                    out = ch[cc] + v;
+                }
+                faces[(fbase[cc] + e) * 4 * N + c] = out;
             }
-            FaceT out;
-            if constexpr (kPair) {
-                two_sum2d(ch, v, out.x, out.y);
-                out.y += cl;
-            } else {
-                out = ch + v;
-            }
-            faces[(fbase + e) * 4 * N + c] = out;
         }
     } else {
         if (real_lead) {
-            if constexpr (kPair) {
-                float hi, lo;
-                two_sum2d(ch, x, hi, lo);
-                Qg[qoff + c] = make_float2(hi, lo + cl);
-            } else {
-                Qg[qoff + c] = ch + x;
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                if constexpr (kPair) {
+                    float hi, lo;
+                    two_sum2d(ch[cc], x[cc], hi, lo);
+                    Qg[qoff[cc] + c] = make_float2(hi, lo + cl[cc]);
+                } else {
+                    Qg[qoff[cc] + c] = ch[cc] + x[cc];
+                }
             }
         }
     }
     if (bad) atomicOr(a.err, 1);
 }
 
-template <int N, typename R>
+template <int N, typename R, int NCOMP = 1>
 cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
 {
-    using G = Geo2D<N, R>;
+    using G = Geo2D<N, R, NCOMP>;
     const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
     const long long groups = (long long)a.Kx * a.Ky * a.M;
     // a launch covers at most `chunk` groups (a multiple of the groups per CTA)
     const long long chunk =
         a.chunk > 0 ? std::min(groups, (a.chunk + G::GPC - 1) / G::GPC * G::GPC) : groups;
     const unsigned block = unsigned(G::kBlock);
-    auto k1 = sl2d_step_kernel<N, R, 1, false>;
-    auto k2 = sl2d_step_kernel<N, R, 2, false>;
+    auto k1 = sl2d_step_kernel<N, R, 1, false, NCOMP>;
+    auto k2 = sl2d_step_kernel<N, R, 2, false, NCOMP>;
     Step2DArgs b = a;
     LaunchThrottle *th = a.chunk > 0 ? a.throttle : nullptr;
     for (int t = 0; t < a.nsteps; ++t) {
@@ -608,6 +665,15 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
             }
     }
     return cudaGetLastError();
+}
+
+// Prepares the two single-instance kernels of one order for two fields.
+template <int N, typename R>
+cudaError_t preload_step2d_c2_n()
+{
+    cudaError_t e = prepare_kernel(sl2d_step_kernel<N, R, 1, false, 2>);
+    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, false, 2>);
+    return e;
 }
 
 // Prepares the four kernels of one order (two phases, single and batched).
