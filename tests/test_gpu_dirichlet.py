@@ -175,6 +175,27 @@ def test_2d_inflow_advection_vs_oracle_and_exact(sl, orc):
         assert np.abs(s.samples() - st50).max() / np.abs(st50).max() <= MIXED_TOL
 
 
+@pytest.mark.parametrize("N,precision", [(10, "fp64"), (11, "fp64"), (11, "fp32"), (12, "fp32")])
+def test_2d_inflow_high_orders_vs_oracle(sl, orc, N, precision):
+    """Dirichlet ghosts at the orders whose Gram rows are split over lanes."""
+    u, v, L, K, steps = 0.6, -0.4, 0.8, 2, 6
+
+    def phi(x, y, t):
+        return 1.0 + 0.5 * np.sin(2 * np.pi * (x - u * t)) * np.sin(2 * np.pi * (y - v * t))
+
+    pb = I.problem(2, (K, K), (0.0, 0.0), (L, L), N, 2, steps, 0.0, 3, ("const", [u, v]), ("const", [0.001]),
+                   ("sinsin", [1.0, 0.5, 1.0]))
+    pb["periodic"] = False
+    pb["dt"] = dt = 0.5 * orc.dt_edge(pb)
+    pb["ghost"] = _ghost_2d(orc, K, N, L, phi, dt * np.arange(1, steps + 1))
+    ref = orc.run(pb, ns=2, want_states=True)["states"]
+    with sl.Solver(pb, precision) as s:
+        s.step()
+        st = s.samples()
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    assert np.abs(st - ref).max() / np.abs(ref).max() <= tol
+
+
 def test_2d_sine_diffusion_with_reseeding_vs_oracle(sl, orc):
     K, N, M, dt, steps = 2, 5, 12, 1e-5, 30
 
