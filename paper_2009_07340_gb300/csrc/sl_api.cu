@@ -305,6 +305,7 @@ void sl_free(sl_ctx *c)
 int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *drift, const sl_field *diffusion,
             const sl_field *phi0, const sl_options *opt)
 {
+    sl::TraceRange trace("sl_init");
     if (!out) return SL_ERR_ARG;
     *out = nullptr;
     if (!mesh || (mesh->dim != 1 && mesh->dim != 2)) return SL_ERR_ARG;
@@ -462,6 +463,7 @@ int sl_set_step_count(sl_ctx *c, long long n)
 
 int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
 {
+    sl::TraceRange trace("sl_set_fields");
     if (!c) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     const int dim = c->m.dim;
@@ -477,6 +479,7 @@ int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
 
 int sl_step(sl_ctx *c, double dt, int steps)
 {
+    sl::TraceRange trace("sl_step");
     if (!c) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     if (!(dt > 0.0) || !std::isfinite(dt) || steps < 0) return SL_ERR_ARG;
@@ -589,6 +592,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
 
 int sl_reseed(sl_ctx *c)
 {
+    sl::TraceRange trace("sl_reseed");
     if (!c) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     const long long V = c->vals;  // values per sample (components x nodes)
@@ -645,6 +649,7 @@ static int check_device_error(sl_ctx *c)
 
 int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2)
 {
+    sl::TraceRange trace("sl_moments");
     if (!c || !d_mean) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     const long long V = c->vals;  // values per sample (components x nodes)

@@ -391,6 +391,7 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
 
 int sl_batch_step(sl_batch *b, int steps)
 {
+    sl::TraceRange trace("sl_batch_step");
     if (!b || steps < 0) return SL_ERR_ARG;
     if (b->poisoned) return SL_ERR_STATE;
     if (steps == 0) return SL_OK;

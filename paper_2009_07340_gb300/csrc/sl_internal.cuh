@@ -8,9 +8,21 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sl.h"
 
 namespace sl {
+
+// NVTX range over a host API call: the solver's entry points appear as named
+// ranges in Nsight tools (ncu --nvtx filters on them); without a tool
+// attached a push / pop is a cheap no-op.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr int kMaxN = 16;           // nodes per direction per element
 constexpr int kMaxThreads1D = 256;  // elements (threads) per CTA in the 1D kernel

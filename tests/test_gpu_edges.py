@@ -84,3 +84,28 @@ def test_single_sample_moments(sl, orc):
         q = s.samples()[0]
     assert np.array_equal(mean, q)
     np.testing.assert_allclose(m2, q * q, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("dim,precision", [(1, "fp64"), (1, "fp32"), (1, "mixed"), (2, "fp64"), (2, "fp32")])
+def test_nonfinite_remap_reports_singular_and_poisons(sl, orc, dim, precision):
+    """A non-finite value in the state makes that element's remap non-finite:
+    the step reports SL_ERR_SINGULAR (-5) at the next synchronising call
+    instead of returning NaN moments, and the context then refuses further
+    calls with SL_ERR_STATE (-7)."""
+    if dim == 1:
+        pb = I.config2(N=6, M=3, steps=2, K=8)
+        pb["dt"] = 0.5 * orc.dt_max(pb)
+    else:
+        pb = I.problem(2, (2, 2), (0.0, 0.0), (1.0, 1.0), 4, 3, 2, 0.0, 5, ("const", [0.3, -0.2]),
+                       ("const", [0.004]), ("gauss", [1.0, 0.2, 0.5, 0.5]))
+        pb["dt"] = 0.5 * orc.dt_edge(pb)
+    q = orc.init_state(pb)
+    q[1, 2] = np.nan
+    with sl.Solver(pb, precision, phi0_nodal=q) as s:
+        s.step()
+        with pytest.raises(sl.SLError) as e:
+            s.moments()
+        assert e.value.code == -5
+        with pytest.raises(sl.SLError) as e:
+            s.step()
+        assert e.value.code == -7
