@@ -86,12 +86,14 @@ struct Vec16<double> {
 // Lanes per Gram row: one while a row of n values fits in a thread's
 // registers (FP32 n <= 81, FP64 n <= 64); above that the row's columns are
 // split over SP adjacent lanes of one warp, which exchange the pivot-column
-// entries by shuffles.  FP32 N = 10 would fit in one lane but runs 1.33x
-// faster on two (more warps per SM); N = 9 runs faster on one.
+// entries by shuffles.  FP32 N = 10 would fit in one lane but runs faster on
+// two (more warps per SM); N = 9 runs faster on one.  FP32 N = 12 on two
+// lanes at two CTAs per SM keeps its row in local memory (7.5x slower), so
+// it takes four lanes and one CTA.
 template <int N, typename R>
 constexpr int split2d()
 {
-    return std::is_same<R, float>::value ? (N <= 9 ? 1 : (N <= 10 ? 2 : 4)) : (N <= 8 ? 1 : (N <= 10 ? 2 : 4));
+    return std::is_same<R, float>::value ? (N <= 9 ? 1 : (N <= 11 ? 2 : 4)) : (N <= 8 ? 1 : (N <= 10 ? 2 : 4));
 }
 
 template <int N, typename R, int NCOMP = 1>
@@ -118,8 +120,16 @@ struct Geo2D {
     static constexpr int kTables = N * N + 3 * N;
 };
 
-// FP32 kernels up to N = 8 are held to two CTAs per SM (their shared memory
-// allows it; 128 registers per thread), the rest to one.
+// CTAs per SM the register budget is sized for: two where shared memory
+// allows two and the row still fits (FP32 N <= 11, FP64 N = 9), one otherwise.
+// At one CTA the high orders ran one element-sample group per SM: two made
+// FP32 N = 9 1.66x, N = 10 1.73x, N = 11 2.2x and FP64 N = 9 1.10x faster.
+template <int N, typename R>
+constexpr int min_ctas2d()
+{
+    return std::is_same<R, float>::value ? (N <= 11 ? 2 : 1) : (N == 9 ? 2 : 1);
+}
+
 // BATCH = false: one instance (a0), group g = element-sample g.
 // BATCH = true: `ninst` instances of the same N, instance i owning groups
 // [prefix[i], prefix[i+1]) (its E*M element-samples).
@@ -127,7 +137,7 @@ struct Geo2D {
 // one Gram matrix, one elimination and one upwind choice serve both; each
 // field has its own right-hand side, refinement, faces and state.
 template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1>
-__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, (std::is_same<R, float>::value && N <= 8) ? 2 : 1) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
+__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
                                                                     const long long *__restrict__ prefix, int ninst, int t)
 {
     using G = Geo2D<N, R, NCOMP>;
