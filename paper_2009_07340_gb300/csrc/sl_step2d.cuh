@@ -120,14 +120,16 @@ struct Geo2D {
     static constexpr int kTables = N * N + 3 * N;
 };
 
-// CTAs per SM the register budget is sized for: two where shared memory
-// allows two and the row still fits (FP32 N <= 11, FP64 N = 9), one otherwise.
-// At one CTA the high orders ran one element-sample group per SM: two made
-// FP32 N = 9 1.66x, N = 10 1.73x, N = 11 2.2x and FP64 N = 9 1.10x faster.
+// CTAs per SM the register budget is sized for: three for FP32 N <= 6
+// (1.14-1.31x over two), two where shared memory allows two and the row
+// still fits (FP32 N <= 11, FP64 N = 9), one otherwise.  At one CTA the high
+// orders ran one element-sample group per SM: two made FP32 N = 9 1.66x,
+// N = 10 1.73x, N = 11 2.2x and FP64 N = 9 1.10x faster.  FP64 N <= 6 gained
+// nothing from two (FP64-pipe bound).
 template <int N, typename R>
 constexpr int min_ctas2d()
 {
-    return std::is_same<R, float>::value ? (N <= 11 ? 2 : 1) : (N == 9 ? 2 : 1);
+    return std::is_same<R, float>::value ? (N <= 6 ? 3 : (N <= 11 ? 2 : 1)) : (N == 9 ? 2 : 1);
 }
 
 // BATCH = false: one instance (a0), group g = element-sample g.
