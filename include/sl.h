@@ -183,6 +183,18 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
 /* Stream-ordered after earlier steps; synchronises the context's stream.   */
 int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion);
 
+/* As sl_set_fields for a field solver that runs on the same GPU: stream-     */
+/* ordered on the context's stream, with no copy and no synchronisation.     */
+/* The tables of SL_U_NODAL / SL_D_NODAL (same layouts) are DEVICE pointers,  */
+/* read in place by kernels on the context's stream: they must hold their    */
+/* values when those kernels run (e.g. written before on the same stream)    */
+/* and stay allocated until then.  A D below 0 (or NaN) in a nodal table is  */
+/* found on the device and reported as SL_ERR_ARG by the next synchronising  */
+/* call (sl_moments, sl_get_samples), which poisons the context.  The time-  */
+/* step bounds are recomputed when next needed (sl_dt_max, sl_dt_edge, or    */
+/* sl_step with strict_dt), which synchronises then.                         */
+int sl_set_fields_device(sl_ctx *c, const sl_field *drift, const sl_field *diffusion);
+
 /* Dirichlet boundary values (1D, periodic[0] = 0), Section 5.3: at a domain */
 /* boundary the given value is the ghost solution that takes the place of   */
 /* the missing neighbour in the upwind rule (Eq. bnd_update).  values: host */

@@ -93,6 +93,7 @@ def lib():
         L.sl_set_boundary.argtypes = [vp, C.c_int, _dp]
         L.sl_reseed.argtypes = [vp]
         L.sl_set_fields.argtypes = [vp, C.POINTER(sl_field), C.POINTER(sl_field)]
+        L.sl_set_fields_device.argtypes = [vp, C.POINTER(sl_field), C.POINTER(sl_field)]
         L.sl_pdf.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_uint32)]
         L.sl_pdf_device.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
         L.sl_moments.argtypes = [vp, _dp, _dp]
@@ -516,6 +517,31 @@ class Solver:
         """New drift and diffusion (problem-dict form, e.g. ("sin", [...])) for the following steps."""
         u, D = _field(_U, drift), _field(_D, diffusion)
         _check(lib().sl_set_fields(C.c_void_p(self.ctx), C.byref(u), C.byref(D)), "sl_set_fields")
+        self.pb = dict(self.pb, drift=drift, diffusion=diffusion)
+
+    def set_fields_device(self, drift, diffusion):
+        """New drift and diffusion from device memory (sl_set_fields_device):
+        ("nodal", tensor[, tensor]) with contiguous float64 CUDA tensors (or
+        an analytic form).  Stream-ordered, no copy; the tensors must stay
+        alive and unchanged until the next step has run."""
+        import torch
+
+        def dev_field(kind_map, spec):
+            if spec[0] != "nodal":
+                return _field(kind_map, spec)
+            f = sl_field()
+            f.kind = kind_map["nodal"]
+            tabs = [t for t in spec[1:3] if t is not None]
+            for t in tabs:
+                if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                    raise TypeError("nodal tables must be contiguous float64 CUDA tensors")
+            f.nodal = C.cast(C.c_void_p(tabs[0].data_ptr()), _dp)
+            if len(tabs) > 1:
+                f.face = C.cast(C.c_void_p(tabs[1].data_ptr()), _dp)
+            return f
+
+        u, D = dev_field(_U, drift), dev_field(_D, diffusion)
+        _check(lib().sl_set_fields_device(C.c_void_p(self.ctx), C.byref(u), C.byref(D)), "sl_set_fields_device")
         self.pb = dict(self.pb, drift=drift, diffusion=diffusion)
 
     def reseed(self):

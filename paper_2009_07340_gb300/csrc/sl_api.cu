@@ -113,20 +113,31 @@ void unstage_nodal(const sl_ctx *c, sl::FieldDev &d)
 // Node and face coefficients of the current drift and diffusion (the setup
 // kernels), nodal tables staged for the duration.
 cudaError_t set_coefficients(sl_ctx *c, const sl_field *drift, const sl_field *diffusion, const sl_field *phi0,
-                             const double *phi0_nodal_dev, bool write_state)
+                             const double *phi0_nodal_dev, bool write_state, bool device_tables = false)
 {
     const sl::Mesh &m = c->m;
     const long long V = (long long)m.E * m.n, nif = n_iface(m.dim, m.K[0], m.K[1], m.N);
     sl::FieldDev du = to_dev(drift), dD = to_dev(diffusion);
-    cudaError_t e = stage_nodal(c, drift, m.dim * V, nif, du);
-    if (e == cudaSuccess) e = stage_nodal(c, diffusion, V, nif, dD);
+    cudaError_t e = cudaSuccess;
+    if (device_tables) {  // the caller's device tables, read in place by the kernels below
+        du.nodal = drift->nodal;
+        du.face = drift->face;
+        dD.nodal = diffusion->nodal;
+        dD.face = diffusion->face;
+        dD.err = c->err;
+    } else {
+        e = stage_nodal(c, drift, m.dim * V, nif, du);
+        if (e == cudaSuccess) e = stage_nodal(c, diffusion, V, nif, dD);
+    }
     if (e == cudaSuccess)
         e = sl::launch_init_fields(m, du, dD, to_dev(phi0), phi0_nodal_dev, c->xi, c->nodeU, c->nodeB, c->nodeDiv,
                                    c->faceU, c->faceB, write_state ? c->Q : nullptr, c->M * c->ncomp,
                                    c->precision == SL_FP64, c->st);  // [M][ncomp] fields of E n values
     if (e == cudaSuccess && m.dim == 2) e = sl::launch_init_faces_hi(m, du, dD, c->faceUhi, c->faceBhi, c->st);
-    unstage_nodal(c, du);
-    unstage_nodal(c, dD);
+    if (!device_tables) {
+        unstage_nodal(c, du);
+        unstage_nodal(c, dD);
+    }
     return e;
 }
 
@@ -432,9 +443,23 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     return SL_OK;
 }
 
+// Bounds after sl_set_fields_device are recomputed on first use (this
+// synchronises the context's stream); the context object itself is not const.
+static int current_bounds(const sl_ctx *cc)
+{
+    sl_ctx *c = const_cast<sl_ctx *>(cc);
+    if (!c->bounds_stale) return SL_OK;
+    if (c->poisoned) return SL_ERR_STATE;
+    if (refresh_bounds(c) != SL_OK) return fail_cuda(c);
+    c->bounds_stale = 0;
+    return SL_OK;
+}
+
 int sl_dt_max(const sl_ctx *c, double *dt)
 {
     if (!c || !dt) return SL_ERR_ARG;
+    const int rc = current_bounds(c);
+    if (rc != SL_OK) return rc;
     *dt = c->dtmax;
     return SL_OK;
 }
@@ -442,6 +467,8 @@ int sl_dt_max(const sl_ctx *c, double *dt)
 int sl_dt_edge(const sl_ctx *c, double *dt)
 {
     if (!c || !dt) return SL_ERR_ARG;
+    const int rc = current_bounds(c);
+    if (rc != SL_OK) return rc;
     *dt = c->dtedge;
     return SL_OK;
 }
@@ -474,6 +501,25 @@ int sl_set_fields(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
     none.kind = SL_PHI_GAUSS;  // no state is written
     const cudaError_t e = set_coefficients(c, drift, diffusion, &none, nullptr, false);
     if (e != cudaSuccess || refresh_bounds(c) != SL_OK) return fail_cuda(c);
+    c->bounds_stale = 0;
+    return SL_OK;
+}
+
+int sl_set_fields_device(sl_ctx *c, const sl_field *drift, const sl_field *diffusion)
+{
+    sl::TraceRange trace("sl_set_fields_device");
+    if (!c) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    const int dim = c->m.dim;
+    if (!valid_kind(dim, 0, drift) || !valid_kind(dim, 1, diffusion)) return SL_ERR_ARG;
+    // analytic parameters are checked here, nodal values on the device
+    if (diffusion->kind != SL_D_NODAL && !diffusion_ok(diffusion, dim, c->m.K[0], c->m.K[1], c->m.N, c->periodic != 0))
+        return SL_ERR_ARG;
+    sl_field none;
+    std::memset(&none, 0, sizeof(none));
+    none.kind = SL_PHI_GAUSS;  // no state is written
+    if (set_coefficients(c, drift, diffusion, &none, nullptr, false, true) != cudaSuccess) return fail_cuda(c);
+    c->bounds_stale = 1;
     return SL_OK;
 }
 
@@ -483,6 +529,10 @@ int sl_step(sl_ctx *c, double dt, int steps)
     if (!c) return SL_ERR_ARG;
     if (c->poisoned) return SL_ERR_STATE;
     if (!(dt > 0.0) || !std::isfinite(dt) || steps < 0) return SL_ERR_ARG;
+    if (c->strict_dt && c->bounds_stale) {
+        if (refresh_bounds(c) != SL_OK) return fail_cuda(c);
+        c->bounds_stale = 0;
+    }
     if (c->strict_dt && dt > c->dtmax * (1.0 + 1e-12)) return SL_ERR_DT;
     if (steps == 0) return SL_OK;
     if (!c->periodic && (c->step < c->ghost_base || c->step + steps > c->ghost_base + c->ghost_count))
@@ -636,6 +686,10 @@ static int check_device_error(sl_ctx *c)
     if (cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
         cudaStreamSynchronize(c->st) != cudaSuccess)
         return fail_cuda(c);
+    if (h & 4) {  // a negative D in tables read in place (sl_set_fields_device); the cause
+        c->poisoned = 1;  // of any non-finite remap that followed, so reported first
+        return SL_ERR_ARG;
+    }
     if (h & 1) {
         c->poisoned = 1;
         return SL_ERR_SINGULAR;

@@ -34,6 +34,7 @@ struct FieldDev {
     double p[40];
     const double *nodal;  // nodal drift / diffusion: device copy of the node values
     const double *face;   // and of the interface table (nullptr: derived from the traces)
+    int *err;             // diffusion tables read in place: D < 0 sets bit 4 here (else null)
 };
 
 struct Mesh {
@@ -207,6 +208,7 @@ struct sl_ctx {
     int device = 0;
     long long step = 0;
     int poisoned = 0;
+    int bounds_stale = 0; // fields changed on the device: dtmax / dtedge recomputed when asked
     double dtmax = 0.0;   // Eq. (1d_timestep) with the smallest node gap
     double dtedge = 0.0;  // the same with the first node's distance to the element face
     // device memory owned by the context

@@ -130,8 +130,13 @@ __device__ void face_fields(const FieldDev &fu, const FieldDev &fD, const Mesh &
         un = dir == 0 ? ux : uy;
     }
     double D;
-    if (fD.kind == SL_D_NODAL) D = fmax(iface_nodal(m, fD.nodal, fD.face, dir, line, idx, pt), 0.0);
-    else D = diffusion_at(fD, x, y);
+    if (fD.kind == SL_D_NODAL) {
+        D = iface_nodal(m, fD.nodal, fD.face, dir, line, idx, pt);
+        if (fD.face && fD.err && !(D >= 0.0)) atomicOr(fD.err, 4);  // a given value below 0
+        D = fmax(D, 0.0);  // a derived trace may undershoot
+    } else {
+        D = diffusion_at(fD, x, y);
+    }
     b = sqrt(2.0 * D);
 }
 
@@ -202,7 +207,9 @@ __global__ void init_nodes_kernel(Mesh m, FieldDev fu, FieldDev fD, FieldDev fph
     node_drift(fu, m, v, x, y, ux, uy);
     nodeU[v] = ux;
     if (m.dim == 2) nodeU[V + v] = uy;
-    nodeB[v] = sqrt(2.0 * node_diffusion(fD, v, x, y));
+    const double Dv = node_diffusion(fD, v, x, y);
+    if (fD.err && !(Dv >= 0.0)) atomicOr(fD.err, 4);  // tables read in place are checked here
+    nodeB[v] = sqrt(2.0 * Dv);
     // divergence
     const long long ve = (long long)e * m.n;
     double dx = 0.0, dy = 0.0;

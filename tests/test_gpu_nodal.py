@@ -1,8 +1,9 @@
 """Nodal drift and diffusion on the GPU (node values handed over by a field
 solver, Section 5.2), through the C ABI, against the FP64 oracle: interface
 tables given or derived from the neighbouring traces, periodic and Dirichlet
-meshes, 1D and 2D, fields switched between steps, batched instances and
-served requests (whose tables the server must copy)."""
+meshes, 1D and 2D, fields switched between steps (from host or device
+memory), batched instances and served requests (whose tables the server must
+copy)."""
 
 import numpy as np
 import pytest
@@ -189,3 +190,48 @@ def test_server_copies_the_nodal_tables(sl, orc):
         state, (mean, _, _) = srv.poll(t)
     assert state == 2
     assert np.array_equal(mean, want.ravel())
+
+
+@pytest.mark.parametrize("table", [False, True])
+def test_device_tables_equal_host_tables(sl, orc, table):
+    """sl_set_fields_device reads the nodal tables in place from device
+    memory: the same steps, bit for bit, as sl_set_fields with the same values
+    from the host; the time-step bounds follow when next asked for."""
+    import torch
+
+    pb = I.config2(N=8, M=4, steps=0, K=16)
+    u, D = _nodal_1d(orc, pb, 21, table)
+    q = I.with_(pb, drift=u, diffusion=D)
+    dt = 0.4 * orc.dt_max(q)
+    with sl.Solver(pb, "fp64") as s:
+        s.step(dt, 3)
+        s.set_fields(u, D)
+        s.step(dt, 4)
+        want = s.samples()
+    dev = lambda spec: (spec[0],) + tuple(None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
+                                          for a in spec[1:])  # noqa: E731
+    with sl.Solver(pb, "fp64") as s:
+        s.step(dt, 3)
+        s.set_fields_device(dev(u), dev(D))
+        assert s.dt_max == pytest.approx(orc.dt_max(q), rel=1e-12)
+        s.step(dt, 4)
+        got = s.samples()
+    assert np.array_equal(got, want)
+
+
+def test_device_tables_negative_diffusion_is_reported(sl, orc):
+    import torch
+
+    pb = I.config2(N=6, M=2, steps=0, K=8)
+    u, D = _nodal_1d(orc, pb, 22, False)
+    bad = torch.tensor(D[1], dtype=torch.float64, device="cuda")
+    bad[3, 2] = -1e-3
+    with sl.Solver(pb, "fp64") as s:
+        s.set_fields_device(("nodal", torch.tensor(u[1], device="cuda")), ("nodal", bad))
+        s.step(1e-5, 1)
+        with pytest.raises(sl.SLError) as e:
+            s.moments()
+        assert e.value.code == -1
+        with pytest.raises(sl.SLError) as e:
+            s.step(1e-5, 1)
+        assert e.value.code == -7
