@@ -192,17 +192,23 @@ def test_server_copies_the_nodal_tables(sl, orc):
     assert np.array_equal(mean, want.ravel())
 
 
+@pytest.mark.parametrize("dim", [1, 2])
 @pytest.mark.parametrize("table", [False, True])
-def test_device_tables_equal_host_tables(sl, orc, table):
+def test_device_tables_equal_host_tables(sl, orc, dim, table):
     """sl_set_fields_device reads the nodal tables in place from device
     memory: the same steps, bit for bit, as sl_set_fields with the same values
     from the host; the time-step bounds follow when next asked for."""
     import torch
 
-    pb = I.config2(N=8, M=4, steps=0, K=16)
-    u, D = _nodal_1d(orc, pb, 21, table)
+    if dim == 1:
+        pb = I.config2(N=8, M=4, steps=0, K=16)
+        u, D = _nodal_1d(orc, pb, 21, table)
+    else:
+        pb = I.problem(2, (3, 4), (0.0, 0.0), (1.0, 1.0), 5, 3, 0, 0.0, 8, ("rotation", [2 * np.pi, 0.5, 0.5]),
+                       ("const", [0.004]), ("gauss", [1.0, 0.2, 0.5, 0.5]))
+        u, D = _nodal_2d(orc, pb, 23, table)
     q = I.with_(pb, drift=u, diffusion=D)
-    dt = 0.4 * orc.dt_max(q)
+    dt = 0.4 * (orc.dt_max(q) if dim == 1 else orc.dt_edge(q))
     with sl.Solver(pb, "fp64") as s:
         s.step(dt, 3)
         s.set_fields(u, D)
