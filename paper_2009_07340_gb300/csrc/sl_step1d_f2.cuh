@@ -51,6 +51,14 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
     float2 *sF = sng + NH * T;                                            // [N] (0 - zeta_m, 4 - zeta_m)
     float *sfa = reinterpret_cast<float *>(sF + N);                       // [T + 1] u dt at interfaces
     float *sfb = sfa + (T + 1);                                           // [T + 1] sqrt(2 D)
+    // node tables as compile-time constants (see NodeTab1D): rows of Z padded
+    // with zeros past N, face pairs (0 - zeta_m, 4 - zeta_m)
+    constexpr NodeTab1D<N> kTab{};
+    auto zrow = [&](int j, float (&zr)[NP]) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) zr[m] = m < N ? kTab.z[j][m] : 0.f;
+    };
+    auto Fp = [&](int m) { return make_float2(kTab.f0[m], kTab.f1[m]); };
 
     cg::cluster_group cluster = cg::this_cluster();
     const int C = a.C;
@@ -167,7 +175,7 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             float zr[NP];
-            load_row<NP>(sZ + j * NP, zr);
+            zrow(j, zr);
             const float dj = lane_rt(dl[j >> 1], j & 1);
             float2 acc = make_float2(1.f, 1.f);
 #pragma unroll
@@ -202,12 +210,12 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
             pre[0] = make_float2(1.f, 1.f);
 #pragma unroll
             for (int m = 1; m < N; ++m)
-                pre[m] = mul2(pre[m - 1], add2(sF[m - 1], bc2(lane_rt(ndl[(m - 1) >> 1], (m - 1) & 1))));
+                pre[m] = mul2(pre[m - 1], add2(Fp(m - 1), bc2(lane_rt(ndl[(m - 1) >> 1], (m - 1) & 1))));
             float2 suf = make_float2(1.f, 1.f);
 #pragma unroll
             for (int j = N - 1; j >= 0; --j) {
                 E[j] = mul2(mul2(bc2(w[j]), pre[j]), suf);
-                if (j > 0) suf = mul2(suf, add2(sF[j], bc2(lane_rt(ndl[j >> 1], j & 1))));
+                if (j > 0) suf = mul2(suf, add2(Fp(j), bc2(lane_rt(ndl[j >> 1], j & 1))));
             }
 #pragma unroll
             for (int j = 0; j < N; ++j) e = fma2(bc2(lane_rt(ph[j >> 1], j & 1)), E[j], e);
@@ -283,7 +291,7 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
         float2 A[NH], P[NH];
         {
             float zr[NP];
-            load_row<NP>(sZ, zr);
+            zrow(0, zr);
             const float d0 = lane_rt(dl[0], 0);
 #pragma unroll
             for (int p = 0; p < NH; ++p) {
@@ -294,7 +302,7 @@ __device__ __forceinline__ void step1d_f2_body(const Step1DArgs &a, const int sl
 #pragma unroll
         for (int k = 1; k < N; ++k) {
             float zr[NP];
-            load_row<NP>(sZ + k * NP, zr);
+            zrow(k, zr);
             const float2 dk = bc2(lane_rt(dl[k >> 1], k & 1));
             const float2 rk = bc2(rw[k]);
 #pragma unroll
