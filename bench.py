@@ -163,9 +163,18 @@ def _cpu_baseline(seconds=15.0):
         oracle.run(I.config2(N=N, M=ms, steps=steps), ns=ms, nthreads=cores, want_sums=True)
     t = time.perf_counter() - t0
     esu = len(ORDERS) * K_ELEM * ms * steps
+    # the same oracle on one thread: 2 samples, a fifth of the time
+    s1 = max(1, int(steps * (seconds / 5.0) / max(t * cores / ms * 2.0, 1e-3)))
+    t0 = time.perf_counter()
+    for N in ORDERS:
+        oracle.run(I.config2(N=N, M=2, steps=s1), ns=2, nthreads=1, want_sums=True)
+    t1 = time.perf_counter() - t0
+    esu1 = len(ORDERS) * K_ELEM * 2 * s1
     return {"value": esu / t, "unit": "ESU/s", "cores": cores, "kind": "oracle",
             "sample": f"K=256, M={ms}, {steps} steps at each N in {{4,8,12,16}} ({esu:.3g} ESU, {t:.1f} s, "
-                      f"FP64 C oracle, samples split over {cores} threads)"}
+                      f"FP64 C oracle, samples split over {cores} threads)",
+            "single_core": {"value": esu1 / t1, "unit": "ESU/s", "cores": 1,
+                            "sample": f"K=256, M=2, {s1} steps at each N ({esu1:.3g} ESU, {t1:.1f} s, one thread)"}}
 
 
 def flops_per_esu_2d(N):
