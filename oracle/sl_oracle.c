@@ -21,6 +21,10 @@
  *     authors' earlier deterministic paper).
  *   - The Wiener increment is drawn from Philox4x32-10 with a Box-Muller
  *     transform built on the own ln / sincospi below (the paper names no RNG).
+ *   - Nodal drift and diffusion (the field solver's values at the Gauss
+ *     nodes, Section 5.2): interface values given, else the mean of the two
+ *     neighbouring elements' traces (the inside trace at a Dirichlet
+ *     boundary, a derived D clipped at 0).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread sl_oracle.c -lm
  * (contraction off: fma() is used only where written explicitly).
