@@ -10,7 +10,9 @@ method (Sections 2, 5 and 6 of the paper):
 * the paper's 1D sine diffusion test (Section 6.1) and its mass conservation;
 * conservation of the element-integrated mean for the divergence form with
   non-constant drift;
-* the time-step condition (Eq. 1d_timestep) and the moment bookkeeping.
+* the time-step condition (Eq. 1d_timestep) and the moment bookkeeping;
+* the Ornstein-Uhlenbeck density (a linear drift given as nodal values):
+  mass, mean and variance of the averaged density against the closed form.
 """
 
 import math
@@ -396,3 +398,54 @@ def test_dirichlet_2d_sine_diffusion_within_standard_error(orc):
     se = np.sqrt(np.maximum(m2 - mean ** 2, 0.0) / (M - 1)).max()
     x, y = orc.node_coords(pb)
     assert np.abs(mean - mean_exact(x, y, steps * dt)).max() <= 4.0 * se + 1e-3
+
+
+def test_ornstein_uhlenbeck_density(orc):
+    """The paper's Ornstein-Uhlenbeck test (Section 6): with the linear drift
+    u = -theta (x - mu) and constant D = sigma^2 / 2, the transported density
+    obeys the OU Fokker-Planck equation, under which a Gaussian stays
+    Gaussian with mean mu + (m0 - mu) e^(-theta t) and variance
+    s0^2 e^(-2 theta t) + D / theta (1 - e^(-2 theta t)).  The drift is given
+    as nodal values (exact for a linear field: exact traces at the faces,
+    spectral divergence -theta).  Dirichlet boundaries far out carry the exact
+    density.  Checked: mass, the first two moments of the averaged density
+    within their standard errors, and the density pointwise."""
+    th, D, m0, s0, L, K, N, M, T = 1.0, 0.05, 0.5, 0.2, 2.0, 16, 8, 2000, 0.25
+
+    def dens(x, t):
+        m = m0 * math.exp(-th * t)
+        s2 = s0 ** 2 * math.exp(-2 * th * t) + D / th * (1 - math.exp(-2 * th * t))
+        return np.exp(-(x - m) ** 2 / (2 * s2)) / math.sqrt(2 * math.pi * s2), m, s2
+
+    pb = I.problem(1, (K,), (-L,), (L,), N, M, 0, 0.0, 17, ("const", [0.0, 0.0]), ("const", [D]),
+                   ("gauss", [1.0, 0.2, 0.0, 0.0]))
+    pb["periodic"] = False
+    x, _ = orc.node_coords(pb)
+    pb = I.with_(pb, drift=("nodal", -th * x))
+    steps = int(round(T / (0.5 * orc.dt_max(pb))))
+    dt = T / steps
+    pb = I.with_(pb, dt=dt, steps=steps)
+    pb["ghost"] = np.array([[dens(-L, (k + 1) * dt)[0], dens(L, (k + 1) * dt)[0]] for k in range(steps)])
+    r = orc.run(pb, nthreads=8, state_in=np.stack([dens(x, 0.0)[0]] * M), want_states=True)
+    st = r["states"]
+    mean, m2 = r["sum"] / M, r["sumsq"] / M
+    exact, m_T, s2_T = dens(x, T)
+    w = orc.quad_weights(N)
+    h = 2 * L / K
+    # mass (divergence form; the compositional update keeps it)
+    mass = float((mean @ w).sum() * h)
+    assert abs(mass - 1.0) <= 1e-3
+    # moments of the averaged density against their sampling errors
+    ms = (st @ w).sum(axis=1) * h
+    m1s = ((st * x) @ w).sum(axis=1) * h / ms
+    m1 = float(((mean * x) @ w).sum() * h) / mass
+    var = float(((mean * x * x) @ w).sum() * h) / mass - m1 ** 2
+    se_m1 = m1s.std(ddof=1) / math.sqrt(M)
+    se_var = m1s.var(ddof=1) * math.sqrt(2.0 / M)
+    assert abs(m1 - m_T) <= 4.0 * se_m1 + 1e-3
+    assert abs(var - s2_T) <= 4.0 * se_var + 1e-3
+    # pointwise, where the density is
+    se = np.sqrt(np.maximum(m2 - mean * mean, 0.0) / (M - 1))
+    assert np.all(np.abs(mean - exact) <= 4.5 * se + 5e-3)
+    on = exact > 1e-2
+    assert on.sum() >= 10 and np.mean(np.abs((mean - exact)[on] / se[on]) < 2.5) > 0.8
