@@ -40,6 +40,8 @@
 #ifndef SL_H
 #define SL_H
 
+#include <stddef.h> /* size_t */
+
 #ifdef __cplusplus
 extern "C" {
 #endif

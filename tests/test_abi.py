@@ -143,3 +143,34 @@ def test_nodal_fields_are_checked_before_device(sl):
     assert _nodal_init_rc(sl, pb, u, sl._field(sl._D, ("nodal", good, face))) != -1
     dirichlet = I.with_(pb, periodic=False)  # ... but read at a Dirichlet boundary
     assert _nodal_init_rc(sl, dirichlet, u, sl._field(sl._D, ("nodal", good, face))) == -1
+
+
+def test_header_is_self_contained_c_and_matches_the_binding(sl, tmp_path):
+    """include/sl.h compiles as plain C99 on its own, and every struct of the
+    C ABI has the same size and field offsets in C as in the ctypes binding."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [sl.sl_field, sl.sl_mesh, sl.sl_options, sl.sl_instance, sl.sl_server_config, sl.sl_server_stats]
+    lines = ['#include "sl.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    got = {tuple(l.split()[:-1]): int(l.split()[-1]) for l in out}
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == C.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
