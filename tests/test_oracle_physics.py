@@ -11,8 +11,9 @@ method (Sections 2, 5 and 6 of the paper):
 * conservation of the element-integrated mean for the divergence form with
   non-constant drift;
 * the time-step condition (Eq. 1d_timestep) and the moment bookkeeping;
-* the Ornstein-Uhlenbeck density (a linear drift given as nodal values):
-  mass, mean and variance of the averaged density against the closed form.
+* the Ornstein-Uhlenbeck density, 1D and 2D (a linear drift given as nodal
+  values): mass, mean and variance of the averaged density against the
+  closed form.
 """
 
 import math
@@ -449,3 +450,50 @@ def test_ornstein_uhlenbeck_density(orc):
     assert np.all(np.abs(mean - exact) <= 4.5 * se + 5e-3)
     on = exact > 1e-2
     assert on.sum() >= 10 and np.mean(np.abs((mean - exact)[on] / se[on]) < 2.5) > 0.8
+
+
+def test_ornstein_uhlenbeck_density_2d(orc):
+    """2D: u = -theta (x, y) separates into two independent OU processes, so
+    a product of Gaussians stays one, with each axis's mean and variance as in
+    1D.  The drift is given as nodal values (divergence -2 theta), D constant,
+    Dirichlet boundaries with the exact density, half the particle-gap dt.
+    Checked: mass and both axes' means and variances of the averaged density
+    against the closed form, within their standard errors plus the
+    discretisation error of this coarse mesh (N = 6, ~2 elements per sigma)."""
+    th, D, m0, s0, L, K, N, M, T = 1.0, 0.02, (0.3, -0.2), 0.25, 2.0, 8, 6, 200, 0.15
+
+    def axis(z, t, mz):
+        m = mz * math.exp(-th * t)
+        s2 = s0 ** 2 * math.exp(-2 * th * t) + D / th * (1 - math.exp(-2 * th * t))
+        return np.exp(-(z - m) ** 2 / (2 * s2)) / math.sqrt(2 * math.pi * s2), m, s2
+
+    def dens(x, y, t):
+        return axis(x, t, m0[0])[0] * axis(y, t, m0[1])[0]
+
+    pb = I.problem(2, (K, K), (-L, -L), (L, L), N, M, 0, 0.0, 19, ("const", [0.0, 0.0]), ("const", [D]),
+                   ("gauss", [1.0, 0.2, 0.0, 0.0]))
+    pb["periodic"] = False
+    x, y = orc.node_coords(pb)
+    pb = I.with_(pb, drift=("nodal", np.stack([-th * x, -th * y])))
+    steps = int(round(T / (0.5 * orc.dt_max(pb))))
+    dt = T / steps
+    pb = I.with_(pb, dt=dt, steps=steps)
+    pts = (np.arange(K)[:, None] + orc.nodes(N)[None, :]).ravel() * (2 * L / K) - L
+    lo, hi = -L + 0 * pts, L + 0 * pts
+    pb["ghost"] = np.array([np.concatenate([dens(lo, pts, t), dens(hi, pts, t), dens(pts, lo, t), dens(pts, hi, t)])
+                            for t in dt * np.arange(1, steps + 1)])
+    r = orc.run(pb, nthreads=8, state_in=np.stack([dens(x, y, 0.0)] * M), want_states=True)
+    st, mean = r["states"], r["sum"] / M
+    w = orc.quad_weights(N)
+    W = np.outer(w, w).ravel()
+    area = (2 * L / K) ** 2
+    mass = float((mean @ W).sum() * area)
+    assert abs(mass - 1.0) <= 1e-2
+    ms = (st @ W).sum(axis=1) * area
+    for z, mz in ((x, m0[0]), (y, m0[1])):
+        _, m_T, s2_T = axis(0.0, T, mz)
+        zs = ((st * z) @ W).sum(axis=1) * area / ms
+        m1 = float(((mean * z) @ W).sum() * area) / mass
+        var = float(((mean * z * z) @ W).sum() * area) / mass - m1 ** 2
+        assert abs(m1 - m_T) <= 4.0 * zs.std(ddof=1) / math.sqrt(M) + 1e-3
+        assert abs(var - s2_T) <= 4.0 * zs.var(ddof=1) * math.sqrt(2.0 / M) + 2e-3
