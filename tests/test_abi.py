@@ -76,6 +76,12 @@ def test_invalid_precision_and_null(sl):
           diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp64", -8),   # 2D FP64 N > 11
     (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=13, drift=("const", [0.1, 0.2]),
           diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp32", -8),   # 2D FP32 N > 12
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=9, components=2, drift=("const", [0.1, 0.2]),
+          diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])), "fp32", -8),   # 2D two fields N > 8
+    (dict(dim=2, K=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), N=4, components=2, periodic=False,
+          drift=("const", [0.1, 0.2]), diffusion=("const", [0.01]), phi0=("gauss", [1.0, 0.2, 0.5, 0.5])),
+     "fp64", -8),                                                                          # two fields: periodic only
+    (dict(components=2), "mixed", -8),                                                     # 1D two fields: not mixed
 ])
 def test_unsupported_sizes_rejected_before_device(sl, bad, precision, code):
     pb = I.config1()
