@@ -761,7 +761,9 @@ static int orc_elem_on_line(const orc_coeffs *cf, int dir, int line, int k)
 }
 
 /* Trace of element e's nodal interpolant of `vals` ([E][n]) on its face     */
-/* xi_dir = side (0 or 1), at the face's Gauss point pt (2D; 0 in 1D).       */
+/* xi_dir = side (0 or 1), at the face's Gauss point pt (2D; 0 in 1D): the   */
+/* Lagrange expansion of the element's nodal values (Section 3) evaluated at */
+/* the face.                                                                 */
 static double orc_trace(const orc_coeffs *cf, const double *vals, int e, int dir, int side, int pt)
 {
     int N = cf->N;
@@ -777,6 +779,10 @@ static double orc_trace(const orc_coeffs *cf, const double *vals, int e, int dir
 /* grid line `line`: the caller's interface table if given, else the mean of */
 /* the traces of the elements on both sides (the one inside trace at a       */
 /* Dirichlet boundary).  On a periodic mesh interface K is interface 0.      */
+/* Reading: Section 5.2 takes the fields from the DSEM solver and the upwind */
+/* rule (Eq. bnd_update) needs them at the interface points; the paper does  */
+/* not say how, and the mean of the two traces is the central value of a     */
+/* discontinuous spectral element method.                                    */
 static double orc_iface_nodal(const orc_problem *pb, const orc_coeffs *cf, const double *vals,
                               const double *face, int dir, int line, int idx, int pt)
 {
@@ -796,9 +802,10 @@ static double orc_iface_nodal(const orc_problem *pb, const orc_coeffs *cf, const
     return have_left ? left : right;
 }
 
-/* Normal drift u_dir and D at an interface point.  Analytic kinds are       */
-/* evaluated at (x, y); nodal ones by orc_iface_nodal, D clipped at 0 where  */
-/* a derived trace undershoots (D >= 0 on the nodes does not bound the       */
+/* Normal drift u_dir and D at an interface point, the quantities of the     */
+/* upwind test sigma = u dt + sqrt(2 D) dW (Eq. bnd_update).  Analytic kinds */
+/* are evaluated at (x, y); nodal ones by orc_iface_nodal, D clipped at 0    */
+/* where a derived trace undershoots (D >= 0 on the nodes does not bound the */
 /* interpolant between them).  Returns -1 for a negative given value.        */
 static int orc_face_fields(const orc_problem *pb, const orc_coeffs *cf, int dir, int line, int idx,
                            int pt, double x, double y, double *un, double *D)
