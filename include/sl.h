@@ -232,6 +232,34 @@ int sl_moments(sl_ctx *c, double *mean, double *m2);
 /* context's stream (no synchronisation, no error check of earlier steps).  */
 int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2);
 
+/* Partial sums of the sample moments, for combining contexts that hold     */
+/* disjoint sample ranges (one per GPU or process): the samples are          */
+/* independent (Section 5.2: one Wiener increment per sample), so the moments */
+/* of Eq. (averaged) over all of them are sums of per-range sums.            */
+/*   d_psum  device, FP64 [nchunks][elements * N^dim (* components)]: row c    */
+/*           = sum of the context's samples [64c, 64c + 64) (the last chunk   */
+/*           may be shorter), in the same fixed order as sl_moments            */
+/*   d_psq   device, FP64, same layout: sums of squares                       */
+/* nchunks = ceil(M / 64) (sl_moment_chunk gives 64).  Caller-owned,          */
+/* asynchronous on the context's stream.  Adding the chunk rows of all       */
+/* contexts in ascending global sample order and dividing by the total       */
+/* sample count reproduces sl_moments of one context holding every sample,  */
+/* bit for bit, when every context's sample0 is a multiple of 64.            */
+int sl_moments_partial(sl_ctx *c, double *d_psum, double *d_psq);
+
+/* Samples per chunk of sl_moments_partial (64). */
+int sl_moment_chunk(void);
+
+/* Moments from chunk partial sums gathered from several contexts (the last */
+/* pass of sl_moments): mean[v] = (sum_c psum[c][v]) / M_total and m2[v] =   */
+/* (sum_c psq[c][v]) / M_total, the chunks added in ascending c, FP64.       */
+/*   d_psum, d_psq  device [nchunks][V], caller-owned, read only             */
+/*   d_mean         device [V]; d_m2 device [V] or NULL                       */
+/*   stream         cudaStream_t or NULL; asynchronous on it                  */
+/* SL_ERR_ARG for nchunks < 1, V < 1, M_total < 1 or a NULL input.           */
+int sl_moments_combine(const double *d_psum, const double *d_psq, int nchunks, long long V, long long M_total,
+                       double *d_mean, double *d_m2, void *stream);
+
 /* The PDF at every node recovered by binning the samples (Section 5.4):    */
 /* counts [elements][N^dim][nbins] (uint32) of the M samples in nbins equal */
 /* bins over [lo, hi]: bin b = floor((x - lo) * (nbins / (hi - lo))) in    */

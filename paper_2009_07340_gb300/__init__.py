@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_init", "sl_step",
            "sl_moments", "sl_moments_device", "sl_dt_max", "sl_step_count", "sl_get_samples",
            "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_dt_edge", "sl_profile", "sl_profile_read",
-           "sl_moments_static", "sl_free", "sl_strerror"]
+           "sl_moments_static", "sl_moments_partial", "sl_moment_chunk", "sl_moments_combine", "sl_free",
+           "sl_strerror"]
 
 SL_FP64, SL_MIXED, SL_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": SL_FP64, "mixed": SL_MIXED, "fp32": SL_FP32}
@@ -108,6 +109,9 @@ def lib():
         L.sl_profile.argtypes = [vp, C.c_int]
         L.sl_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
         L.sl_moments_static.argtypes = [vp, C.c_int, C.c_longlong, vp, vp, vp]
+        L.sl_moments_partial.argtypes = [vp, vp, vp]
+        L.sl_moment_chunk.argtypes = []
+        L.sl_moments_combine.argtypes = [vp, vp, C.c_int, C.c_longlong, C.c_longlong, vp, vp, vp]
         L.sl_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(sl_instance), C.POINTER(sl_options)]
         L.sl_batch_step.argtypes = [vp, C.c_int]
         L.sl_batch_tune.argtypes = [vp, C.c_int, _dp]
@@ -227,6 +231,24 @@ def sl_moments(ctx, V, want_m2=True):
 def sl_moments_device(ctx, d_mean_ptr, d_m2_ptr=None):
     _check(lib().sl_moments_device(C.c_void_p(ctx), C.c_void_p(d_mean_ptr),
                                    C.c_void_p(d_m2_ptr) if d_m2_ptr else None), "sl_moments_device")
+
+
+def sl_moments_partial(ctx, d_psum_ptr, d_psq_ptr):
+    """Chunk partial sums [ceil(M/64)][V] into caller-owned device memory."""
+    _check(lib().sl_moments_partial(C.c_void_p(ctx), C.c_void_p(d_psum_ptr), C.c_void_p(d_psq_ptr)),
+           "sl_moments_partial")
+
+
+def sl_moment_chunk():
+    return int(lib().sl_moment_chunk())
+
+
+def sl_moments_combine(d_psum_ptr, d_psq_ptr, nchunks, V, M_total, d_mean_ptr, d_m2_ptr=None, stream=None):
+    """Moments from gathered chunk partials (device pointers), asynchronous on `stream`."""
+    _check(lib().sl_moments_combine(C.c_void_p(d_psum_ptr), C.c_void_p(d_psq_ptr), int(nchunks), int(V),
+                                    int(M_total), C.c_void_p(d_mean_ptr),
+                                    C.c_void_p(d_m2_ptr) if d_m2_ptr else None,
+                                    C.c_void_p(stream) if stream else None), "sl_moments_combine")
 
 
 def sl_dt_max(ctx):
@@ -557,6 +579,16 @@ class Solver:
 
     def moments_device(self, mean_t, m2_t=None):
         sl_moments_device(self.ctx, mean_t.data_ptr(), m2_t.data_ptr() if m2_t is not None else None)
+
+    def moments_partial(self, psum_t, psq_t):
+        """Chunk partial sums into float64 CUDA tensors [ceil(M/64)][V]
+        (sl_moments_partial), asynchronous on the solver's stream."""
+        nc = -(-self.M // 64)
+        for t in (psum_t, psq_t):
+            if tuple(t.shape) != (nc, self.V) or not t.is_contiguous() or str(t.dtype) != "torch.float64" \
+                    or not t.is_cuda:
+                raise ValueError(f"need contiguous float64 CUDA tensors of shape ({nc}, {self.V})")
+        sl_moments_partial(self.ctx, psum_t.data_ptr(), psq_t.data_ptr())
 
     def samples(self, s0=0, count=None):
         count = self.M - s0 if count is None else count

@@ -713,6 +713,31 @@ int sl_moments_device(sl_ctx *c, double *d_mean, double *d_m2)
     return SL_OK;
 }
 
+int sl_moments_partial(sl_ctx *c, double *d_psum, double *d_psq)
+{
+    sl::TraceRange trace("sl_moments_partial");
+    if (!c || !d_psum || !d_psq) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    if (sl::launch_moment_partials(c->Q, c->precision == SL_FP64, c->M, c->vals, c->mom_chunk, d_psum, d_psq,
+                                   c->st) != cudaSuccess)
+        return fail_cuda(c);
+    return SL_OK;
+}
+
+int sl_moment_chunk(void) { return 64; }
+
+int sl_moments_combine(const double *d_psum, const double *d_psq, int nchunks, long long V, long long M_total,
+                       double *d_mean, double *d_m2, void *stream)
+{
+    sl::TraceRange trace("sl_moments_combine");
+    if (!d_psum || !d_psq || !d_mean || nchunks < 1 || V < 1 || M_total < 1) return SL_ERR_ARG;
+    if (sl::ensure_loaded() != cudaSuccess) return SL_ERR_CUDA;
+    return sl::launch_moments_combine(d_psum, d_psq, nchunks, V, M_total, d_mean, d_m2,
+                                      static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? SL_OK
+               : SL_ERR_CUDA;
+}
+
 int sl_pdf_device(sl_ctx *c, int nbins, double lo, double hi, unsigned int *d_counts)
 {
     if (!c || !d_counts || nbins < 1 || nbins > 4096 || !std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo))

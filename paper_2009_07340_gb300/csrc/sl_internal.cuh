@@ -154,6 +154,12 @@ cudaError_t launch_wiener(unsigned long long seed, long long step0, long long sa
                           double sqrt_dt, double *out, cudaStream_t st);
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk,
                            double *psum, double *psq, double *mean, double *m2, cudaStream_t st);
+// The first pass alone: per-chunk sums and sums of squares [ceil(M/chunk)][V].
+cudaError_t launch_moment_partials(const void *Q, int state_is_double, int M, long long V, int chunk,
+                                   double *psum, double *psq, cudaStream_t st);
+// The second pass alone: chunk partials [nc][V] added in ascending c, / M.
+cudaError_t launch_moments_combine(const double *psum, const double *psq, int nc, long long V, long long M,
+                                   double *mean, double *m2, cudaStream_t st);
 // Per-node histogram of the samples into B bins over [lo, hi] (device [V][B]).
 cudaError_t launch_pdf(const void *Q, int state_is_double, int M, long long V, int B, double lo, double hi,
                        unsigned int *counts, cudaStream_t st);

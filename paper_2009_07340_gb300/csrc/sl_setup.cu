@@ -340,29 +340,51 @@ cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_
     return cudaGetLastError();
 }
 
-// Moments, Eq. (averaged), in a fixed summation order: chunk c of `chunk`
-// consecutive samples is summed in ascending sample order into partials
-// [c][V]; the partials are then added in ascending c.  FP64 throughout.
+// Moments, Eq. (averaged), in a fixed summation order.  A block owns 32
+// consecutive nodes (one per lane: every warp load is 32 adjacent values,
+// 256 bytes) and one chunk c of `chunk` consecutive samples.  Warp w of the
+// block's kMomWarps sums the chunk's samples s0 + w, s0 + w + kMomWarps, ...
+// in ascending order; the warps' partials are then added in ascending w
+// through shared memory into psum/psq [c][V].  The final pass adds the chunk
+// partials in ascending c.  FP64 throughout.
+constexpr int kMomWarps = 8;
+
 template <typename State>
-__global__ void moments_partial_kernel(const State *__restrict__ Q, int M, long long V, int chunk,
-                                       double *__restrict__ psum, double *__restrict__ psq)
+__global__ void __launch_bounds__(32 * kMomWarps) moments_partial_kernel(const State *__restrict__ Q, int M, long long V,
+                                                                         int chunk, double *__restrict__ psum,
+                                                                         double *__restrict__ psq)
 {
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
+    __shared__ double sa[kMomWarps][32], sb[kMomWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long v = (long long)blockIdx.x * 32 + lane;
     const int c = blockIdx.y;
-    const int s0 = c * chunk, s1 = min(M, s0 + chunk);
+    const long long s0 = (long long)c * chunk, s1 = min((long long)M, s0 + chunk);
     double a = 0.0, b = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const double x = load_state(Q, (long long)s * V + v);
-        a += x;
-        b = fma(x, x, b);
+    if (v < V) {
+#pragma unroll 4
+        for (long long s = s0 + w; s < s1; s += kMomWarps) {
+            const double x = load_state(Q, s * V + v);
+            a += x;
+            b = fma(x, x, b);
+        }
     }
-    psum[(long long)c * V + v] = a;
-    psq[(long long)c * V + v] = b;
+    sa[w][lane] = a;
+    sb[w][lane] = b;
+    __syncthreads();
+    if (w == 0 && v < V) {
+        double ta = sa[0][lane], tb = sb[0][lane];
+#pragma unroll
+        for (int k = 1; k < kMomWarps; ++k) {
+            ta += sa[k][lane];
+            tb += sb[k][lane];
+        }
+        psum[(long long)c * V + v] = ta;
+        psq[(long long)c * V + v] = tb;
+    }
 }
 
 __global__ void moments_final_kernel(const double *__restrict__ psum, const double *__restrict__ psq, int nc,
-                                     long long V, int M, double *__restrict__ mean, double *__restrict__ m2)
+                                     long long V, double M, double *__restrict__ mean, double *__restrict__ m2)
 {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -465,19 +487,37 @@ cudaError_t launch_reseed(void *Q, int state_is_double, int M, long long V, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_moment_partials(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
+                                   double *psq, cudaStream_t st)
+{
+    const int nc = (M + chunk - 1) / chunk;
+    if (nc > 65535) return cudaErrorInvalidValue;  // chunks are the grid's y dimension
+    dim3 g1(unsigned((V + 31) / 32), unsigned(nc));
+    if (state_is_double)
+        moments_partial_kernel<double><<<g1, 32 * kMomWarps, 0, st>>>(static_cast<const double *>(Q), M, V, chunk,
+                                                                      psum, psq);
+    else
+        moments_partial_kernel<float2><<<g1, 32 * kMomWarps, 0, st>>>(static_cast<const float2 *>(Q), M, V, chunk,
+                                                                      psum, psq);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
                            double *psq, double *mean, double *m2, cudaStream_t st)
 {
     const int tb = 256;
     const int nc = (M + chunk - 1) / chunk;
-    dim3 g1(unsigned((V + tb - 1) / tb), unsigned(nc));
-    if (state_is_double)
-        moments_partial_kernel<double><<<g1, tb, 0, st>>>(static_cast<const double *>(Q), M, V, chunk, psum, psq);
-    else
-        moments_partial_kernel<float2><<<g1, tb, 0, st>>>(static_cast<const float2 *>(Q), M, V, chunk, psum, psq);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_moment_partials(Q, state_is_double, M, V, chunk, psum, psq, st);
     if (e != cudaSuccess) return e;
-    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, M, mean, m2);
+    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, double(M), mean, m2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_combine(const double *psum, const double *psq, int nc, long long V, long long M,
+                                   double *mean, double *m2, cudaStream_t st)
+{
+    const int tb = 256;
+    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, double(M), mean, m2);
     return cudaGetLastError();
 }
 

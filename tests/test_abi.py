@@ -68,6 +68,9 @@ def test_invalid_precision_and_null(sl):
     assert L.sl_step(None, 1e-3, 1) == -1
     assert L.sl_moments(None, None, None) == -1
     L.sl_free(None)  # no-op
+    assert L.sl_moments_partial(None, None, None) == -1
+    assert L.sl_moments_combine(None, None, 1, 4, 4, None, None, None) == -1
+    assert L.sl_moment_chunk() == 64
 
 
 @pytest.mark.parametrize("bad,precision,code", [

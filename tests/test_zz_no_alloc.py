@@ -79,3 +79,24 @@ def test_long_chunks_and_size_limit(env):
     with pytest.raises(sl.SLError) as e:
         sl.sl_moments_static(x.data_ptr(), 1, (1 << 20) + 1, mean.data_ptr())
     assert e.value.code == -1
+
+
+def test_calls_allocate_no_device_memory(env):
+    # after a first call (which looks up the scratch array's address), further
+    # calls must leave the device's free memory and torch's allocator untouched
+    torch, sl = env
+    M, V = 500, 4096
+    x = torch.rand((M, V), dtype=torch.float64, device="cuda")
+    mean = torch.empty(V, dtype=torch.float64, device="cuda")
+    m2 = torch.empty(V, dtype=torch.float64, device="cuda")
+    sl.sl_moments_static(x.data_ptr(), M, V, mean.data_ptr(), m2.data_ptr())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        sl.sl_moments_static(x.data_ptr(), M, V, mean.data_ptr(), m2.data_ptr())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == (alloc0, reserved0)
+    assert _rel(mean.cpu().numpy(), x.mean(0).cpu().numpy()) <= TOL
