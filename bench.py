@@ -222,34 +222,50 @@ def _timed(fn):
     return time.perf_counter() - t0
 
 
-def leg_2d(sl, stream):
-    """Config 3 mesh (64x64 elements, N=8): FP32 at M=1024, FP64 at M=64."""
-    out = {"workload": "2D periodic [0,1]^2, 64x64 elements, N=8, rotation drift, "
-                       "D=0.005(1+0.3 sin 2pi x sin 2pi y), dt=1.618e-6 (edge-distance bound; at the "
-                       "node-gap dt 6.93e-5 the 2D interpolation matrix reaches cond ~3e3 at one sigma)"}
+def leg_2d(sl, stream, horizon=500, acc_samples=16):
+    """Config 3 (64x64 elements, N=8, rotation drift): rates in FP32 (M=1024)
+    and FP64 (M=128) at two time steps, and FP32 against FP64 over the full
+    500-step horizon at the larger one.
+
+    The stated dt (the Eq. 1d_timestep particle-gap bound, 6.93e-5) is not
+    used: there the 2D step amplifies a perturbation ~12 % per step (x5.8e6
+    over 120 steps, measured on the FP64 oracle), so no two implementations
+    agree after a few hundred steps.  Half of it (3.465e-5) is stable; the
+    edge-distance bound (1.618e-6) keeps every particle inside its element."""
+    out = {"workload": "2D periodic [0,1]^2, 64x64 elements, N=8, rotation drift, D=0.005(1+0.3 sin 2pi x "
+                       "sin 2pi y), Gaussian blob; dt: half the particle-gap bound (3.465e-5; the bound itself, "
+                       "6.93e-5, is unstable in 2D) and the edge-distance bound (1.618e-6)"}
+    for name, dt in (("half_node_gap_dt", I.DT_CFG3_HALF), ("edge_dt", I.DT_CFG3_EDGE)):
+        leg = {"dt": dt}
+        for mode, M, steps in (("fp32", 1024, 3), ("fp64", 128, 2)):
+            pb = I.config3(M=M, steps=steps, dt=dt)
+            s = sl.Solver(pb, mode, stream=stream.cuda_stream)
+            s.step(pb["dt"], 1)
+            s.profile(True)
+            s.step(pb["dt"], steps)
+            ms, _ = s.profile_read()
+            s.close()
+            leg[mode] = {"value": 64 * 64 * M * steps / (ms * 1e-3), "unit": "ESU/s", "M": M, "steps": steps}
+        ach = leg["fp32"]["value"] * flops_per_esu_2d(8) / 1e12
+        leg["roofline_fp32"] = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach / PEAK_FP32_TFLOPS, "flops_per_esu": flops_per_esu_2d(8),
+                                "what": "the dense direct solve's flops (the method's work count) per second"}
+        out[name] = leg
+    # FP32 against FP64 over the whole horizon, same seeds
+    pb = I.config3(M=acc_samples, steps=horizon, dt=I.DT_CFG3_HALF)
     means = {}
-    for mode, M, steps in (("fp32", 1024, 3), ("fp64", 64, 2)):
-        pb = I.config3(M=M, steps=steps, dt=I.DT_CFG3_EDGE)
-        s = sl.Solver(pb, mode, stream=stream.cuda_stream)
-        s.step(pb["dt"], 1)
-        s.profile(True)
-        s.step(pb["dt"], steps)
-        ms, _ = s.profile_read()
-        s.close()
-        esu = 64 * 64 * M * steps
-        out[mode] = {"value": esu / (ms * 1e-3), "unit": "ESU/s", "M": M, "steps": steps}
-    ach = out["fp32"]["value"] * flops_per_esu_2d(8) / 1e12
-    out["roofline_fp32"] = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / PEAK_FP32_TFLOPS, "flops_per_esu": flops_per_esu_2d(8)}
     for mode in ("fp64", "fp32"):
-        pb = I.config3(M=32, steps=20, dt=I.DT_CFG3_EDGE)
         with sl.Solver(pb, mode, stream=stream.cuda_stream) as s:
             s.step()
             means[mode] = s.moments()[0]
-    out["error_fp32_vs_fp64"] = float(np.abs(means["fp32"] - means["fp64"]).max() / np.abs(means["fp64"]).max())
-    out["error_what"] = "max rel. difference of the mean, M=32, 20 steps, same seeds"
-    out["summary"] = {"fp32_esu_per_s": out["fp32"]["value"], "fp64_esu_per_s": out["fp64"]["value"],
-                      "fp32_frac": out["roofline_fp32"]["frac"], "error_fp32_vs_fp64": out["error_fp32_vs_fp64"]}
+    err = float(np.abs(means["fp32"] - means["fp64"]).max() / np.abs(means["fp64"]).max())
+    out["accuracy"] = {"dt": I.DT_CFG3_HALF, "steps": horizon, "M": acc_samples, "error_fp32_vs_fp64": err,
+                       "tolerance": 1e-5, "met": err <= 1e-5,
+                       "what": "max |mean_fp32 - mean_fp64| / max |mean_fp64| after the full horizon"}
+    out["summary"] = {"fp32_esu_per_s": {k: out[k]["fp32"]["value"] for k in ("half_node_gap_dt", "edge_dt")},
+                      "fp64_esu_per_s": {k: out[k]["fp64"]["value"] for k in ("half_node_gap_dt", "edge_dt")},
+                      "fp32_frac": {k: out[k]["roofline_fp32"]["frac"] for k in ("half_node_gap_dt", "edge_dt")},
+                      "error_fp32_vs_fp64_500_steps": err}
     return out
 
 
@@ -464,10 +480,14 @@ def _moments_bandwidth(sl, stream, reps=20):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            s.moments_device(d_mean, d_m2)
-        e1.record(stream)
+        with torch.cuda.stream(stream):
+            # hold the stream while the calls are queued, so that the events
+            # time the kernels and not the host's launch rate
+            torch.cuda._sleep(20_000_000)
+            e0.record(stream)
+            for _ in range(reps):
+                s.moments_device(d_mean, d_m2)
+            e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
     nc = -(-M_SAMPLES // 64)

@@ -113,11 +113,23 @@ struct Geo2D {
     static constexpr int P = n + 4 * N;                         // stacked rows
     // per-group shared memory (elements of R)
     static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
+    static constexpr int HXS = (2 * N + 3) & ~3;                // stride of the particles' basis-value table
+    // the tensor-preconditioned fast path (one lane per row, N <= 8, one field)
+    static constexpr bool kFast = SP == 1 && N <= 8 && NCOMP == 1;
+    __host__ __device__ static constexpr int r4(int v) { return (v + 3) & ~3; }
+    // its buffers after the basis-value table: hxT, hyT [N][n]; Wx, WxT, Wy, WyT [N][N];
+    // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [n]; u4, mu4 [4N]; two pivot rows [4N + 4];
+    // convergence slots [2][GS / 32][2]
+    static constexpr int kFastBuf = kFast ? 2 * N * r4(n) + 4 * r4(N * N) + 6 * r4(N) + 2 * r4(n) + 2 * r4(4 * N) +
+                                                2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1)
+                                          : 0;
     // rhs, vec and res hold one P4-long array per field
-    static constexpr int kRows = P * LD, kRhs = NCOMP * P4, kPiv = 2 * (LD + 4), kVec = NCOMP * P4, kRes = NCOMP * P4;
+    static constexpr int kRows0 = P * LD;
+    static constexpr int kRows = kFast && n * HXS + kFastBuf > kRows0 ? r4(n * HXS + kFastBuf) : kRows0;
+    static constexpr int kRhs = NCOMP * P4, kPiv = 2 * (LD + 4), kVec = NCOMP * P4, kRes = NCOMP * P4;
     static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
-    // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N]
-    static constexpr int kTables = N * N + 3 * N;
+    // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N], -4 xi [N], 4 (1 - xi) [N]
+    static constexpr int kTables = N * N + 5 * N;
 };
 
 // CTAs per SM the register budget is sized for: three for FP32 N <= 6
@@ -145,6 +157,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     using G = Geo2D<N, R, NCOMP>;
     constexpr int P4 = G::P4;  // stride of the per-field arrays
     constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
+    constexpr int HXS = G::HXS;  // stride of the phase-2 basis-value table (16-byte rows)
+    static_assert(n * HXS <= G::kRows, "basis-value table fits in the rows' space");
     constexpr int P = PHASE == 1 ? n : G::P;  // rows of the system solved in this phase
     using VV = Vec16<R>;
     using VT = typename VV::T;
@@ -158,6 +172,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     R *slam = sZ + N * N;     // [N] barycentric weights of the (scaled) Gauss nodes
     R *sh0 = slam + N;        // [N] h_i(0)
     R *sh1 = sh0 + N;         // [N] h_i(1)
+    R *sX0 = sh1 + N;         // [N] -4 xi_m (scaled face x = 0 minus node m)
+    R *sX1 = sX0 + N;         // [N] 4 (1 - xi_m)
     const int grp = threadIdx.x / G::GS;
     const int tig = threadIdx.x - grp * G::GS;  // thread in the group
     const int c = tig / SP;                     // thread's node / row / column index
@@ -189,6 +205,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
         slam[j] = R(lam);
         sh0[j] = R(l0);
         sh1[j] = R(l1);
+        sX0[j] = R(-4.0 * xi[j]);
+        sX1[j] = R(4.0 * (1.0 - xi[j]));
     }
     __syncthreads();
 
@@ -241,6 +259,7 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     }
     const int ip = c % N, jp = c / N;
     R hx[N], hy[N];
+    R dxp = R(0), dyp = R(0);  // the particle's displacement in scaled element units (4 / h)
     R ph[NCOMP];
 #pragma unroll
     for (int cc = 0; cc < NCOMP; ++cc) ph[cc] = R(0);
@@ -254,6 +273,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
         // differently in the batched and single kernels
         const R dx = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx))) / a.hx);
         const R dy = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy))) / a.hy);
+        dxp = dx;
+        dyp = dy;
         const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
 #pragma unroll
         for (int cc = 0; cc < NCOMP; ++cc) {
@@ -290,15 +311,27 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
             hy[m] *= suf * slam[m];
             suf *= sZ[jp * N + m] + dy;
         }
-        // row c of V and its right-hand side
-        // (row c of V: entry q = jj N + ii is hx[ii] hy[jj]; 16-byte stores,
-        // the padding past n is never read)
+        if constexpr (SP > 1) {
+            // row c of V (entry q = jj N + ii is hx[ii] hy[jj]) for the lanes
+            // of the row; 16-byte stores, the padding past n is never read
 #pragma unroll
-        for (int q = 0; q < n; q += VW) {
-            R v4[4];
+            for (int q = 0; q < n; q += VW) {
+                R v4[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? hx[(q + i) % N] * hy[(q + i) / N] : R(0);
-            *reinterpret_cast<VT *>(Vs + c * LD + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? hx[(q + i) % N] * hy[(q + i) / N] : R(0);
+                *reinterpret_cast<VT *>(Vs + c * LD + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+            }
+        } else if constexpr (PHASE == 2) {
+            // the particle's basis values, hx then hy ([n][HXS] table at Vs):
+            // the Gram matrix is formed from them in tensor form
+#pragma unroll
+            for (int q = 0; q < 2 * N; q += VW) {
+                R v4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v4[i] = (i < VW && q + i < 2 * N) ? (q + i < N ? hx[q + i] : hy[q + i - N]) : R(0);
+                *reinterpret_cast<VT *>(Vs + c * HXS + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+            }
         }
 #pragma unroll
         for (int cc = 0; cc < NCOMP; ++cc) rhs[cc * P4 + c] = ph[cc];
@@ -314,8 +347,9 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
         if (group_active && lead && c < 4 * N) {
             const int side = c / N, f = c % N;
             R *row = Vs + (n + c) * LD;
+            if constexpr (SP > 1)
 #pragma unroll
-            for (int q = 0; q < n; q += VW) *reinterpret_cast<VT *>(row + q) = VV::make(R(0), R(0), R(0), R(0));
+                for (int q = 0; q < n; q += VW) *reinterpret_cast<VT *>(row + q) = VV::make(R(0), R(0), R(0), R(0));
             const double dW = a.dW[((long long)t * a.M + s) * 2 + (side < 2 ? 0 : 1)];
             int e_face;  // element whose low face is this interface
             if (side == 0) e_face = e;
@@ -382,226 +416,935 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                     gr = gv - ch[cc];
                 rhs[cc * P4 + n + c] = w * gr;
             }
-            if (side == 0)
+            if constexpr (SP > 1) {
+                if (side == 0)
 #pragma unroll
-                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh0[ii];
-            else if (side == 1)
+                    for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh0[ii];
+                else if (side == 1)
 #pragma unroll
-                for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh1[ii];
-            else if (side == 2)
+                    for (int ii = 0; ii < N; ++ii) row[f * N + ii] = w * sh1[ii];
+                else if (side == 2)
 #pragma unroll
-                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh0[jj];
-            else
+                    for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh0[jj];
+                else
 #pragma unroll
-                for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh1[jj];
+                    for (int jj = 0; jj < N; ++jj) row[jj * N + f] = w * sh1[jj];
+            }
         }
     }
     group_sync(bar_id, G::GS);
 
-    // Gram row c: G[c][c'] = sum_p S[p][c] S[p][c'], b_c = sum_p S[p][c] rhs_p
-    // (SP > 1: lane h holds the columns c' = h NC + j, j < NC, of row c)
-    constexpr int NG = SP == 1 ? n : NC;
-    const int col0 = h * NC;  // first column of this lane (SP > 1)
-    R gr[NG];
-#pragma unroll
-    for (int q = 0; q < NG; ++q) gr[q] = R(0);
-    R bc[NCOMP];
-#pragma unroll
-    for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = R(0);
-    if (real) {
-        for (int p = 0; p < P; ++p) {
-            const R vpc = Vs[p * LD + c];
-            const R *rowp = Vs + p * LD;
-            if constexpr (SP == 1) {
-#pragma unroll
-                for (int q = 0; q < n; q += VW) {
-                    const VT v = *reinterpret_cast<const VT *>(rowp + q);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (q + i < n) gr[q + i] = fma(vpc, VV::at(v, i), gr[q + i]);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < NC; j += VW) {
-                    const VT v = *reinterpret_cast<const VT *>(rowp + col0 + j);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (col0 + j + i < n) gr[j + i] = fma(vpc, VV::at(v, i), gr[j + i]);
-                }
-            }
-#pragma unroll
-            for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = fma(vpc, rhs[cc * P4 + p], bc[cc]);
-        }
-    }
-
-    // Gauss-Jordan elimination without pivoting (G is SPD); multipliers are
-    // kept in the eliminated positions for the refinement replay
-    R diag = R(1);
     bool bad = false;
-    // entry k of row c, from the lane holding column k (SP > 1: a shuffle
-    // executed by every lane of the warp; k is a compile-time index)
-    auto row_entry = [&](const int k) -> R {
-        if constexpr (SP == 1) {
-            return gr[k];
-        } else {
-            const R mine = h == k / NC ? gr[k % NC] : R(0);
-            return __shfl_sync(0xffffffffu, mine, rowbase + k / NC);
-        }
-    };
+    constexpr int NG = SP == 1 ? n : NC;  // row entries a lane holds
+    const int col0 = h * NC;  // first column of this lane (SP > 1)
+    // ---------------------------------------------------------------- fast path
+    // Within an element the particles of a sample move almost alike (one
+    // Wiener increment per sample, fields that vary little across an
+    // element), so V is close to a tensor product V0 of two 1D advected-basis
+    // matrices: with x~_a the mean x of particle column a and y~_b the mean y
+    // of particle row b, V0[(b,a)][(j,i)] = h_i(x~_a) h_j(y~_b).  Its inverse
+    // is the tensor product of the 1D interpolation matrices Wx[i][a] =
+    // l~_a(xi_i) (the Lagrange basis on the x~, evaluated at the nodes) and Wy.
+    // Phase 1 iterates alpha += V0^{-1} (phi* - V alpha).  Phase 2 iterates
+    // q += G0^{-1} S^T (rhs - S q) on the stacked system S = [V; w B], with
+    // G0 = V0^T (I + w^2 E0^T E0) V0, E0 = B V0^{-1}, applied in the stable
+    // order V0^{-1} (I - E0^T C^{-1} E0) V0^{-T}, C = w^{-2} I + E0 E0^T
+    // (4N x 4N, assembled from 1D products and inverted by one warp).  Both
+    // converge to the direct solution.  A group whose tensor factors are
+    // ill-conditioned (||Wx|| ||Wy|| above kFastCond: particles far outside
+    // the element) or whose iteration has not converged after kFastIters
+    // takes the direct path below, which is unchanged by this one.
+    bool done = false;
+    if constexpr (G::kFast) {
+        constexpr int NW = G::GS / 32;
+        constexpr int NT = G::r4(n), R4N = G::r4(N);
+        constexpr float kFastCond = 64.0f;
+        constexpr int kFastIters = kPair ? 8 : 16;
+        const float kFastTol = kPair ? 1e-6f : 1e-13f;
+        R *hxT = Vs + n * HXS;          // [N][NT]: hx_p[i] at [i][p]
+        R *hyT = hxT + N * NT;          // [N][NT]
+        R *Wx = hyT + N * NT;           // [N][N]: Wx[i][a]
+        R *WxT = Wx + G::r4(N * N);     // [N][N]: Wx transposed
+        R *Wy = WxT + G::r4(N * N);
+        R *WyT = Wy + G::r4(N * N);
+        R *gx0 = WyT + G::r4(N * N);    // [N] l~_a(0); then l~_a(1), and the same in y
+        R *gx1 = gx0 + R4N;
+        R *gy0 = gx1 + R4N;
+        R *gy1 = gy0 + R4N;
+        R *dbx = gy1 + R4N;             // [N] mean x displacement of particle column a
+        R *dby = dbx + R4N;             // [N] mean y displacement of particle row b
+        R *tA = dby + R4N;              // [NT] work vectors
+        R *tB = tA + NT;
+        R *u4 = tB + NT;                // [4N]
+        R *mu4 = u4 + G::r4(4 * N);     // [4N]
+        R *prow = mu4 + G::r4(4 * N);   // [2][4N + 4] pivot rows of the inversion of C
+        unsigned *red = reinterpret_cast<unsigned *>(prow + 2 * G::r4(4 * N + 4));  // [2][NW][2] maxima, [1] decision
+        static_assert(n * HXS + G::kFastBuf <= G::kRows, "fast-path buffers fit in the rows' space");
+        const int lane = threadIdx.x & 31, wig = tig >> 5;
+        const R cref = R(fabs(double(ch[0])));
+
+        // displacements (and, in phase 2, the particles' basis values) to shared memory
+        if (c < n) {
+            tA[c] = dxp;
+            tB[c] = dyp;
+            if constexpr (PHASE == 2) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-        R *pr = piv + (k & 1) * (LD + 4);
-        if constexpr (SP == 1) {
-            if (c == k) {
-#pragma unroll
-                for (int q = 0; q < n; q += VW) {
-                    R v4[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
-                    *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
-                }
-                pr[LD] = bc[0];
-                if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
-                pr[LD + 1] = R(1) / gr[k];
-                diag = gr[k];
-            }
-        } else {
-            if (c == k) {  // every lane of the pivot row publishes its columns
-#pragma unroll
-                for (int j = 0; j < NC; j += VW) {
-                    R v4[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) v4[i] = i < VW ? gr[j + i] : R(0);
-                    *reinterpret_cast<VT *>(pr + col0 + j) = VV::make(v4[0], v4[1], v4[2], v4[3]);
-                }
-                if (lead) {
-                    pr[LD] = bc[0];
-                    if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
-                }
-                if (h == k / NC) {
-                    pr[LD + 1] = R(1) / gr[k % NC];
-                    diag = gr[k % NC];
+                for (int i = 0; i < N; ++i) {
+                    hxT[i * NT + c] = hx[i];
+                    hyT[i * NT + c] = hy[i];
                 }
             }
         }
         group_sync(bar_id, G::GS);
-        const R gk = row_entry(k);
-        if (real && c != k) {
-            const R l = gk * pr[LD + 1];
-            // columns < k hold multipliers (eliminated); only q > k change
-            if constexpr (SP == 1) {
+        if (c < N) {
+            R sx = R(0);
 #pragma unroll
-                for (int q = 0; q < n; q += VW) {
-                    if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
-                    const VT v = *reinterpret_cast<const VT *>(pr + q);
+            for (int b = 0; b < N; ++b) sx += tA[b * N + c];
+            dbx[c] = sx / R(N);
+        } else if (c < 2 * N) {
+            R sy = R(0);
 #pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+            for (int a2 = 0; a2 < N; ++a2) sy += tB[(c - N) * N + a2];
+            dby[c - N] = sy / R(N);
+        }
+        group_sync(bar_id, G::GS);
+        // the 1D inverse factors and the tilde basis at the faces; every
+        // difference is a node difference plus a displacement difference
+        if (c < n) {
+            const int i = c / N, a2 = c % N;
+            R nx = R(1), dx_ = R(1), ny = R(1), dy_ = R(1);
+#pragma unroll
+            for (int m = 0; m < N; ++m)
+                if (m != a2) {
+                    nx *= sZ[i * N + m] - dbx[m];
+                    dx_ *= sZ[a2 * N + m] + (dbx[a2] - dbx[m]);
+                    ny *= sZ[i * N + m] - dby[m];
+                    dy_ *= sZ[a2 * N + m] + (dby[a2] - dby[m]);
                 }
-                gr[k] = l;
-            } else {
+            const R wx = nx / dx_, wy = ny / dy_;
+            Wx[i * N + a2] = wx;
+            WxT[a2 * N + i] = wx;
+            Wy[i * N + a2] = wy;
+            WyT[a2 * N + i] = wy;
+        }
+        if (c < 4 * N) {
+            const int s2 = c / N, a2 = c % N;
+            const R *db = s2 < 2 ? dbx : dby;
+            const R *X = (s2 & 1) ? sX1 : sX0;
+            R num = R(1), den = R(1);
 #pragma unroll
-                for (int j = 0; j < NC; j += VW) {
-                    const VT v = *reinterpret_cast<const VT *>(pr + col0 + j);
+            for (int m = 0; m < N; ++m)
+                if (m != a2) {
+                    num *= X[m] - db[m];
+                    den *= sZ[a2 * N + m] + (db[a2] - db[m]);
+                }
+            gx0[s2 * R4N + a2] = num / den;
+        }
+        group_sync(bar_id, G::GS);
+        {
+            // conditioning of the tensor factors: ||Wx||_inf ||Wy||_inf
+            R sx = R(0), sy = R(0);
+            if (c < N) {
 #pragma unroll
-                    for (int i = 0; i < VW; ++i) {
-                        const int q = col0 + j + i;
-                        if (q > k && q < n) gr[j + i] = fma(-l, VV::at(v, i), gr[j + i]);
+                for (int a2 = 0; a2 < N; ++a2) {
+                    sx += fabs(Wx[c * N + a2]);
+                    sy += fabs(Wy[c * N + a2]);
+                }
+            }
+            const unsigned kx = __reduce_max_sync(0xffffffffu, __float_as_uint(float(sx)));
+            const unsigned ky = __reduce_max_sync(0xffffffffu, __float_as_uint(float(sy)));
+            if (tig == 0) red[4 * NW] = __uint_as_float(kx) * __uint_as_float(ky) <= kFastCond ? 1u : 0u;
+        }
+        group_sync(bar_id, G::GS);
+        if (red[4 * NW] != 0u) {
+            // group maxima of |d| and |x| of one iteration, through the slots of buffer it & 1
+            auto publish_maxima = [&](const int it, const R d, const R x) {
+                const unsigned kd = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(float(d))));
+                const unsigned kxm = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(float(x))));
+                if (lane == 0) {
+                    red[(it & 1) * 2 * NW + 2 * wig] = kd;
+                    red[(it & 1) * 2 * NW + 2 * wig + 1] = kxm;
+                }
+            };
+            auto converged = [&](const int it) -> bool {  // read after a group barrier
+                unsigned md = 0u, mx = 0u;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    md = max(md, red[(it & 1) * 2 * NW + 2 * w]);
+                    mx = max(mx, red[(it & 1) * 2 * NW + 2 * w + 1]);
+                }
+                return __uint_as_float(md) <= kFastTol * (__uint_as_float(mx) + float(cref));
+            };
+            if constexpr (PHASE == 1) {
+                R x = R(0);                        // alpha - c at node c
+                R r = real ? rhs[c] : R(0);        // phi* - V alpha at particle c
+                for (int it = 0; it < kFastIters; ++it) {
+                    if (c < n) res[c] = r;
+                    group_sync(bar_id, G::GS);
+                    // V0^{-1} r: [(b, i)] = sum_a Wx[i][a] r[(b, a)] (stored at [i][b]), then sum_b Wy[j][b] [(b, i)]
+                    if (c < n) {
+                        const int i = c % N, b = c / N;
+                        R t = R(0);
+#pragma unroll
+                        for (int a2 = 0; a2 < N; ++a2) t = fma(Wx[i * N + a2], res[b * N + a2], t);
+                        tA[i * N + b] = t;
+                    }
+                    group_sync(bar_id, G::GS);
+                    R d = R(0);
+                    if (c < n) {
+                        const int i = c % N, j = c / N;
+#pragma unroll
+                        for (int b = 0; b < N; ++b) d = fma(Wy[j * N + b], tA[i * N + b], d);
+                        x += d;
+                        vec[c] = x;
+                    }
+                    publish_maxima(it, d, x);
+                    group_sync(bar_id, G::GS);
+                    if (converged(it)) {
+                        done = true;
+                        break;
+                    }
+                    if (real) {  // the new residual at particle c, from every node's x
+                        R t2[N];
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+                        for (int q = 0; q < n; q += VW) {
+                            const VT v = *reinterpret_cast<const VT *>(vec + q);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i)
+                                if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                        }
+                        R vx = R(0);
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
+                        r = rhs[c] - vx;
                     }
                 }
-                if (h == k / NC) gr[k % NC] = l;
+            } else {
+                const R wb = R(a.w), wi2 = R(1) / (wb * wb);
+                // products for C: Wx Wx^T at tA, Wy Wy^T at tB, and
+                // hvx[s][i] = sum_a Wx[i][a] gx_s[a] at u4[s N + i], hvy[s][j] = sum_b Wy[j][b] gy_s[b] at u4[(2 + s) N + j]
+                if (c < n) {
+                    const int i = c / N, i2 = c % N;
+                    R sxx = R(0), syy = R(0);
+#pragma unroll
+                    for (int a2 = 0; a2 < N; ++a2) {
+                        sxx = fma(Wx[i * N + a2], Wx[i2 * N + a2], sxx);
+                        syy = fma(Wy[i * N + a2], Wy[i2 * N + a2], syy);
+                    }
+                    tA[c] = sxx;
+                    tB[c] = syy;
+                }
+                if (c < 4 * N) {
+                    const int s2 = c / N, k = c % N;
+                    const R *W = s2 < 2 ? Wx : Wy;
+                    const R *g = gx0 + s2 * R4N;
+                    R v = R(0);
+#pragma unroll
+                    for (int m = 0; m < N; ++m) v = fma(W[k * N + m], g[m], v);
+                    u4[c] = v;
+                }
+                group_sync(bar_id, G::GS);
+                // lane f of warp 0 assembles row f of C and, with the other lanes, inverts C in place
+                // (Gauss-Jordan without pivoting: C is symmetric positive definite, eigenvalues >= w^-2)
+                R creg[4 * N];
+#pragma unroll
+                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = R(0);
+                if (wig == 0) {
+                    if (lane < 4 * N) {
+                        const int f = lane;
+                        const bool fx = f < 2 * N;
+                        const int s = (f / N) & 1, k = f % N;
+                        const R *g = fx ? gx0 + s * R4N : gy0 + s * R4N;
+                        const R *g0 = fx ? gx0 : gy0;
+                        const R *g1 = fx ? gx1 : gy1;
+                        R gg0 = R(0), gg1 = R(0);
+#pragma unroll
+                        for (int m = 0; m < N; ++m) {
+                            gg0 = fma(g[m], g0[m], gg0);
+                            gg1 = fma(g[m], g1[m], gg1);
+                        }
+                        const R *Mw = fx ? tB : tA;  // Wy Wy^T along x faces, Wx Wx^T along y faces
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; ++f2) {
+                            const bool f2x = f2 < 2 * N;
+                            const int s2 = (f2 / N) & 1, k2 = f2 % N;
+                            R v;
+                            if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
+                            else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
+                            else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
+                            creg[f2] = f2 == f ? v + wi2 : v;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4 * N; ++k) {
+                        R *pr = prow + (k & 1) * G::r4(4 * N + 4);
+                        if (lane == k)
+#pragma unroll
+                            for (int f2 = 0; f2 < 4 * N; ++f2) pr[f2] = creg[f2];
+                        __syncwarp();
+                        if (lane < 4 * N) {
+                            const R pinv = R(1) / pr[k];
+                            if (lane == k) {
+#pragma unroll
+                                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
+                            } else {
+                                const R l = creg[k];
+#pragma unroll
+                                for (int f2 = 0; f2 < 4 * N; ++f2)
+                                    creg[f2] = f2 == k ? -l * pinv : fma(-l, pr[f2] * pinv, creg[f2]);
+                            }
+                        }
+                    }
+                }
+                R q = R(0);  // q - c at node c
+                bool conv = false;
+                for (int it = 0; it <= kFastIters; ++it) {
+                    if (c < n) vec[c] = q;
+                    group_sync(bar_id, G::GS);
+                    if (it > 0 && converged(it - 1)) {
+                        conv = true;
+                        break;
+                    }
+                    if (it == kFastIters) break;
+                    // stacked residual: particles phi* - V q, face points w (g - c) - w B q
+                    if (real) {
+                        R t2[N];
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+                        for (int qq = 0; qq < n; qq += VW) {
+                            const VT v = *reinterpret_cast<const VT *>(vec + qq);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i)
+                                if (qq + i < n) t2[(qq + i) / N] = fma(hx[(qq + i) % N], VV::at(v, i), t2[(qq + i) / N]);
+                        }
+                        R vq = R(0);
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) vq = fma(hy[jj], t2[jj], vq);
+                        res[c] = rhs[c] - vq;
+                    }
+                    if (group_active && c < 4 * N) {
+                        const int side = c / N, f = c % N;
+                        R bq = R(0);
+                        if (side < 2) {
+                            const R *hf = side == 0 ? sh0 : sh1;
+#pragma unroll
+                            for (int ii = 0; ii < N; ++ii) bq = fma(hf[ii], vec[f * N + ii], bq);
+                        } else {
+                            const R *hf = side == 2 ? sh0 : sh1;
+#pragma unroll
+                            for (int jj = 0; jj < N; ++jj) bq = fma(hf[jj], vec[jj * N + f], bq);
+                        }
+                        res[n + c] = rhs[n + c] - wb * bq;
+                    }
+                    group_sync(bar_id, G::GS);
+                    // z = S^T res at node c = (i, j)
+                    if (c < n) {
+                        const int i = c % N, j = c / N;
+                        R z = R(0);
+#pragma unroll
+                        for (int p2 = 0; p2 < n; p2 += VW) {
+                            const VT xv = *reinterpret_cast<const VT *>(hxT + i * NT + p2);
+                            const VT yv = *reinterpret_cast<const VT *>(hyT + j * NT + p2);
+                            const VT rv = *reinterpret_cast<const VT *>(res + p2);
+#pragma unroll
+                            for (int e2 = 0; e2 < VW; ++e2)
+                                if (p2 + e2 < n) z = fma(VV::at(xv, e2) * VV::at(yv, e2), VV::at(rv, e2), z);
+                        }
+                        z = fma(wb * sh0[i], res[n + j], z);
+                        z = fma(wb * sh1[i], res[n + N + j], z);
+                        z = fma(wb * sh0[j], res[n + 2 * N + i], z);
+                        z = fma(wb * sh1[j], res[n + 3 * N + i], z);
+                        tA[c] = z;
+                    }
+                    group_sync(bar_id, G::GS);
+                    // V0^{-T} z: [(j, a)] = sum_i Wx[i][a] z[(j, i)] (stored at [a][j]), then sum_j Wy[j][b] [(j, a)]
+                    if (c < n) {
+                        const int a2 = c % N, j = c / N;
+                        R t = R(0);
+#pragma unroll
+                        for (int i = 0; i < N; ++i) t = fma(WxT[a2 * N + i], tA[j * N + i], t);
+                        tB[a2 * N + j] = t;
+                    }
+                    group_sync(bar_id, G::GS);
+                    R tv = R(0);
+                    if (c < n) {
+                        const int a2 = c % N, b = c / N;
+#pragma unroll
+                        for (int j = 0; j < N; ++j) tv = fma(WyT[b * N + j], tB[a2 * N + j], tv);
+                        tA[c] = tv;
+                    }
+                    group_sync(bar_id, G::GS);
+                    // u = E0 t: x faces sum_b Wy[k][b] sum_a gx_s[a] t[(b, a)]; y faces sum_a Wx[k][a] sum_b gy_s[b] t[(b, a)]
+                    if (c < 4 * N) {
+                        const int s2 = (c / N) & 1, k = c % N;
+                        R uv = R(0);
+                        if (c < 2 * N) {
+                            const R *g = gx0 + s2 * R4N;
+#pragma unroll
+                            for (int b = 0; b < N; ++b) {
+                                R inner = R(0);
+#pragma unroll
+                                for (int a2 = 0; a2 < N; ++a2) inner = fma(g[a2], tA[b * N + a2], inner);
+                                uv = fma(Wy[k * N + b], inner, uv);
+                            }
+                        } else {
+                            const R *g = gy0 + s2 * R4N;
+#pragma unroll
+                            for (int a2 = 0; a2 < N; ++a2) {
+                                R inner = R(0);
+#pragma unroll
+                                for (int b = 0; b < N; ++b) inner = fma(g[b], tA[b * N + a2], inner);
+                                uv = fma(Wx[k * N + a2], inner, uv);
+                            }
+                        }
+                        u4[c] = uv;
+                    }
+                    group_sync(bar_id, G::GS);
+                    if (wig == 0 && lane < 4 * N) {  // mu = C^{-1} u
+                        R m = R(0);
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; ++f2) m = fma(creg[f2], u4[f2], m);
+                        mu4[lane] = m;
+                    }
+                    group_sync(bar_id, G::GS);
+                    // t - E0^T mu at particle (a, b)
+                    if (c < n) {
+                        const int a2 = c % N, b = c / N;
+                        R sx0 = R(0), sx1 = R(0), sy0 = R(0), sy1 = R(0);
+#pragma unroll
+                        for (int j = 0; j < N; ++j) {
+                            sx0 = fma(WyT[b * N + j], mu4[j], sx0);
+                            sx1 = fma(WyT[b * N + j], mu4[N + j], sx1);
+                            sy0 = fma(WxT[a2 * N + j], mu4[2 * N + j], sy0);
+                            sy1 = fma(WxT[a2 * N + j], mu4[3 * N + j], sy1);
+                        }
+                        R corr = gx0[a2] * sx0;
+                        corr = fma(gx1[a2], sx1, corr);
+                        corr = fma(gy0[b], sy0, corr);
+                        corr = fma(gy1[b], sy1, corr);
+                        tA[c] = tv - corr;
+                    }
+                    group_sync(bar_id, G::GS);
+                    // V0^{-1}: [(b, i)] = sum_a Wx[i][a] t[(b, a)] (stored at [i][b]), then sum_b Wy[j][b] [(b, i)]
+                    if (c < n) {
+                        const int i = c % N, b = c / N;
+                        R t = R(0);
+#pragma unroll
+                        for (int a2 = 0; a2 < N; ++a2) t = fma(Wx[i * N + a2], tA[b * N + a2], t);
+                        tB[i * N + b] = t;
+                    }
+                    group_sync(bar_id, G::GS);
+                    R d = R(0);
+                    if (c < n) {
+                        const int i = c % N, j = c / N;
+#pragma unroll
+                        for (int b = 0; b < N; ++b) d = fma(Wy[j * N + b], tB[i * N + b], d);
+                        q += d;
+                    }
+                    publish_maxima(it, d, q);
+                }
+                if (conv) {
+                    done = true;
+                    if (real) {
+                        if constexpr (kPair) {
+                            float hi, lo;
+                            two_sum2d(ch[0], q, hi, lo);
+                            Qg[qoff[0] + c] = make_float2(hi, lo + cl[0]);
+                        } else {
+                            Qg[qoff[0] + c] = ch[0] + q;
+                        }
+                    }
+                }
             }
-            bc[0] = fma(-l, pr[LD], bc[0]);
-            if constexpr (NCOMP > 1) bc[1] = fma(-l, pr[LD + 2], bc[1]);
         }
     }
-    if constexpr (SP > 1) diag = __shfl_sync(0xffffffffu, diag, rowbase + (c < n ? c : 0) / NC);  // the row's pivot
-    R x[NCOMP];
+    // ---------------------------------------------------------------- direct path
+    if (!done) {
+    if constexpr (PHASE == 1 && SP == 1) {
+        // Phase 1: alpha = V^{-1} phi* by Gauss-Jordan elimination of the
+        // square advected-basis matrix V itself, with partial (row) pivoting.
+        // Row c (particle c) lives in the registers of its lanes.  At step k
+        // every warp nominates its not yet pivoted row of largest |V[.][k]| (a
+        // warp max-reduction of the magnitudes' bit patterns) and publishes
+        // it; after one group barrier every thread takes the nominee of
+        // largest magnitude (the lowest warp on ties) as the pivot row.  Every
+        // other row eliminates column k and keeps its multiplier there.  Node
+        // k's alpha is its pivot row's right-hand side over the pivot.
+        constexpr int NW = G::GS / 32;  // warps per group
+        static_assert(2 * NW * (LD + 4) + 2 * NW <= 4 * N * LD, "pivot nominees fit in the face rows' space");
+        R *cnd = Vs + n * LD;                                                     // [2][NW][LD + 4] nominated rows
+        unsigned *mags = reinterpret_cast<unsigned *>(cnd + 2 * NW * (LD + 4));  // [2][NW] their keys
+        const int wig = tig >> 5, lane = threadIdx.x & 31;
+        R gr[NG];
+        if constexpr (SP == 1) {  // row c of V from the particle's own basis values
 #pragma unroll
-    for (int cc = 0; cc < NCOMP; ++cc) x[cc] = real_lead ? bc[cc] / diag : R(0);
-    bad |= real_lead && !(diag > R(0));
+            for (int q = 0; q < n; ++q) gr[q] = real ? hx[q % N] * hy[q / N] : R(0);
+        } else {  // this lane's columns of row c, staged by the row's first lane
+#pragma unroll
+            for (int q = 0; q < NG; q += VW) {
+                VT v = VV::make(R(0), R(0), R(0), R(0));
+                if (real) v = *reinterpret_cast<const VT *>(Vs + c * LD + col0 + q);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+                    if (q + i < NG) gr[q + i] = col0 + q + i < n ? VV::at(v, i) : R(0);
+            }
+        }
+        R bc[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = real ? rhs[cc * P4 + c] : R(0);
+        int mypiv = -1;  // the column this row pivots, once chosen
+        R diag = R(1);
+        // entry k of this thread's row, from the lane holding column k (SP > 1:
+        // a shuffle executed by every lane of the warp; k is a compile-time index)
+        auto row_entry = [&](const int k) -> R {
+            if constexpr (SP == 1) {
+                return gr[k];
+            } else {
+                const R mine = h == k / NC ? gr[k % NC] : R(0);
+                return __shfl_sync(0xffffffffu, mine, rowbase + k / NC);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            const int buf = k & 1;
+            const int hk = SP == 1 ? 0 : k / NC;  // lane of a row holding column k
+            const int jk = SP == 1 ? k : k % NC;  // its register
+            unsigned key = 0u;                    // 0: no candidate
+            if (real && mypiv < 0 && h == hk) key = __float_as_uint(fabsf(float(gr[jk]))) + 1u;
+            const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+            const unsigned ball = __ballot_sync(0xffffffffu, key != 0u && key == kmax);
+            const int wl = __ffs(ball) - 1;  // the lowest lane holding the warp's largest entry
+            const bool nominee = ball != 0u && lane - h == wl - hk;  // a lane of the warp's nominated row
+            R *slot = cnd + (buf * NW + wig) * (LD + 4);
+            if (nominee) {
+#pragma unroll
+                for (int q = 0; q < NG; q += VW) {
+                    R v4[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < NG) ? gr[q + i] : R(0);
+                    *reinterpret_cast<VT *>(slot + col0 + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                }
+                if (lead) {
+                    slot[LD] = bc[0];
+                    if constexpr (NCOMP > 1) slot[LD + 2] = bc[1];
+                }
+                if (h == hk) slot[LD + 1] = R(1) / gr[jk];
+            }
+            if (lane == 0) mags[buf * NW + wig] = kmax;
+            group_sync(bar_id, G::GS);
+            int wstar = 0;
+            unsigned best = mags[buf * NW];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) {
+                const unsigned m = mags[buf * NW + w];
+                if (m > best) {
+                    best = m;
+                    wstar = w;
+                }
+            }
+            const R *pr = cnd + (buf * NW + wstar) * (LD + 4);
+            const bool is_piv = nominee && wig == wstar;
+            if (is_piv) {
+                mypiv = k;
+                if (h == hk) diag = gr[jk];
+            }
+            bad |= real_lead && best == 0u;  // no non-zero entry left in column k: V is singular
+            const R gk = row_entry(k);
+            if (real && !is_piv) {
+                const R l = gk * pr[LD + 1];
+                // columns < k hold multipliers (or this row's pivot); only q > k change
+                if constexpr (SP == 1) {
+#pragma unroll
+                    for (int q = 0; q < n; q += VW) {
+                        if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
+                        const VT v = *reinterpret_cast<const VT *>(pr + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+                    }
+                    gr[k] = l;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; j += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(pr + col0 + j);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i) {
+                            const int q = col0 + j + i;
+                            if (q > k && q < n) gr[j + i] = fma(-l, VV::at(v, i), gr[j + i]);
+                        }
+                    }
+                    if (h == hk) gr[jk] = l;
+                }
+                bc[0] = fma(-l, pr[LD], bc[0]);
+                if constexpr (NCOMP > 1) bc[1] = fma(-l, pr[LD + 2], bc[1]);
+            }
+        }
+        if constexpr (SP > 1) diag = __shfl_sync(0xffffffffu, diag, rowbase + (mypiv >= 0 ? mypiv : 0) / NC);
+        const bool has = real_lead && mypiv >= 0;
+        bad |= real_lead && mypiv < 0;
+        R x[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) x[cc] = has ? bc[cc] / diag : R(0);
 
-    if constexpr (kPair) {
-        // one step of iterative refinement of the stacked least-squares
-        // residual: r = S^T (rhs - S x), G dx = r, x += dx (per field)
+        if constexpr (kPair) {
+            // one step of iterative refinement: r = phi* - V x from the
+            // particle's basis values, V dx = r by replaying the elimination's
+            // multipliers (pivot rows in the same order), x += dx
 #pragma unroll
-        for (int cc = 0; cc < NCOMP; ++cc)
-            if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
-        group_sync(bar_id, G::GS);
-        if (real_lead) {
-            // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
+            for (int cc = 0; cc < NCOMP; ++cc)
+                if (has) vec[cc * P4 + mypiv] = x[cc];
+            group_sync(bar_id, G::GS);
+            R rc[NCOMP];
 #pragma unroll
-            for (int cc = 0; cc < NCOMP; ++cc) {
-                R t2[N];
-#pragma unroll
-                for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
-#pragma unroll
-                for (int q = 0; q < n; q += VW) {
-                    const VT v = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
-                }
-                R vx = R(0);
-#pragma unroll
-                for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
-                res[cc * P4 + c] = rhs[cc * P4 + c] - vx;
-            }
-        }
-        if (PHASE == 2 && group_active && lead && c < 4 * N) {
-            const R *row = Vs + (n + c) * LD;
-#pragma unroll
-            for (int cc = 0; cc < NCOMP; ++cc) {
-                R bx = R(0);
-#pragma unroll
-                for (int q = 0; q < n; q += VW) {
-                    const VT rv = *reinterpret_cast<const VT *>(row + q);
-                    const VT xv = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (q + i < n) bx = fma(VV::at(rv, i), VV::at(xv, i), bx);
-                }
-                res[cc * P4 + n + c] = rhs[cc * P4 + n + c] - bx;
-            }
-        }
-        group_sync(bar_id, G::GS);
-        R rc[NCOMP];
-#pragma unroll
-        for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = R(0);
-        if (real_lead)
-            for (int p = 0; p < P; p += VW) {
+            for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = R(0);
+            if (real_lead) {
 #pragma unroll
                 for (int cc = 0; cc < NCOMP; ++cc) {
-                    const VT rv = *reinterpret_cast<const VT *>(res + cc * P4 + p);
+                    R t2[N];
 #pragma unroll
-                    for (int i = 0; i < VW; ++i)
-                        if (p + i < P) rc[cc] = fma(Vs[(p + i) * LD + c], VV::at(rv, i), rc[cc]);
+                    for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+                    for (int q = 0; q < n; q += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                    }
+                    R vx = R(0);
+#pragma unroll
+                    for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
+                    rc[cc] = rhs[cc * P4 + c] - vx;
                 }
             }
+#pragma unroll
+            for (int k = 0; k < n; ++k) {
+                R *pr = piv + (k & 1) * (LD + 4);
+                if (lead && mypiv == k)
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) pr[cc] = rc[cc];
+                group_sync(bar_id, G::GS);
+                const R gk = row_entry(k);
+                if (real_lead && mypiv != k)
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = fma(-gk, pr[cc], rc[cc]);
+            }
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) x[cc] += has ? rc[cc] / diag : R(0);
+        }
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) bad |= real_lead && !isfinite(x[cc]);
+        // face values of the advected interpolant (alpha - c = x, node-indexed) at the 4N face points
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc)
+            if (has) vec[cc * P4 + mypiv] = x[cc];
+        group_sync(bar_id, G::GS);
+    } else {
+        // Gram row c: G[c][c'] = sum_p S[p][c] S[p][c'], b_c = sum_p S[p][c] rhs_p
+        // (SP > 1: lane h holds the columns c' = h NC + j, j < NC, of row c)
+        R gr[NG];
+#pragma unroll
+        for (int q = 0; q < NG; ++q) gr[q] = R(0);
+        R bc[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = R(0);
+        const int ic = c % N, jc = c / N;  // node (i, j) of row c
+        // face-row weight w and the Gauss-node basis at the faces
+        const R wb = R(a.w);
+        if (SP == 1 && real) {
+            // G = V^T V + B^T B in tensor form.  V[p][(i',j')] = hx_p[i'] hy_p[j'], so
+            // row c = (i, j) of V^T V is sum_p V[p][c] (hx_p (x) hy_p), and B's rows
+            // (w h_i'(0 or 1) along one face) give w^2 (h0[i] h0[i'] + h1[i] h1[i'])
+            // on the entries (i', j) and the same in y on (i, j').
+            for (int p = 0; p < n; ++p) {
+                const R *hp = Vs + p * HXS;
+                R hxp[N], hyp[N];
+#pragma unroll
+                for (int q = 0; q < 2 * N; q += VW) {
+                    const VT v = *reinterpret_cast<const VT *>(hp + q);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) {
+                        if (q + i < N) hxp[q + i] = VV::at(v, i);
+                        else if (q + i < 2 * N) hyp[q + i - N] = VV::at(v, i);
+                    }
+                }
+                const R vpc = hp[ic] * hp[N + jc];
+                R u[N];
+#pragma unroll
+                for (int ii = 0; ii < N; ++ii) u[ii] = vpc * hxp[ii];
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj)
+#pragma unroll
+                    for (int ii = 0; ii < N; ++ii) gr[jj * N + ii] = fma(u[ii], hyp[jj], gr[jj * N + ii]);
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = fma(vpc, rhs[cc * P4 + p], bc[cc]);
+            }
+            const R w2 = wb * wb;
+            const R x0 = w2 * sh0[ic], x1 = w2 * sh1[ic], y0 = w2 * sh0[jc], y1 = w2 * sh1[jc];
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj)
+                if (jj == jc)
+#pragma unroll
+                    for (int ii = 0; ii < N; ++ii) gr[jj * N + ii] = fma(x1, sh1[ii], fma(x0, sh0[ii], gr[jj * N + ii]));
+#pragma unroll
+            for (int ii = 0; ii < N; ++ii)
+                if (ii == ic)
+#pragma unroll
+                    for (int jj = 0; jj < N; ++jj) gr[jj * N + ii] = fma(y1, sh1[jj], fma(y0, sh0[jj], gr[jj * N + ii]));
+            const R b0x = wb * sh0[ic], b1x = wb * sh1[ic], b0y = wb * sh0[jc], b1y = wb * sh1[jc];
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) {
+                const R *rf = rhs + cc * P4 + n;  // w (g - c) per face point: sides x=0, x=1, y=0, y=1
+                bc[cc] = fma(b0x, rf[jc], bc[cc]);
+                bc[cc] = fma(b1x, rf[N + jc], bc[cc]);
+                bc[cc] = fma(b0y, rf[2 * N + ic], bc[cc]);
+                bc[cc] = fma(b1y, rf[3 * N + ic], bc[cc]);
+            }
+        } else if (real) {
+            for (int p = 0; p < P; ++p) {
+                const R vpc = Vs[p * LD + c];
+                const R *rowp = Vs + p * LD;
+                if constexpr (SP == 1) {
+#pragma unroll
+                    for (int q = 0; q < n; q += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(rowp + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i < n) gr[q + i] = fma(vpc, VV::at(v, i), gr[q + i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; j += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(rowp + col0 + j);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (col0 + j + i < n) gr[j + i] = fma(vpc, VV::at(v, i), gr[j + i]);
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) bc[cc] = fma(vpc, rhs[cc * P4 + p], bc[cc]);
+            }
+        }
+
+        // Gauss-Jordan elimination without pivoting (G is SPD); multipliers are
+        // kept in the eliminated positions for the refinement replay
+        R diag = R(1);
+        // entry k of row c, from the lane holding column k (SP > 1: a shuffle
+        // executed by every lane of the warp; k is a compile-time index)
+        auto row_entry = [&](const int k) -> R {
+            if constexpr (SP == 1) {
+                return gr[k];
+            } else {
+                const R mine = h == k / NC ? gr[k % NC] : R(0);
+                return __shfl_sync(0xffffffffu, mine, rowbase + k / NC);
+            }
+        };
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             R *pr = piv + (k & 1) * (LD + 4);
-            if (c == k && lead)
+            if constexpr (SP == 1) {
+                if (c == k) {
 #pragma unroll
-                for (int cc = 0; cc < NCOMP; ++cc) pr[cc] = rc[cc];
+                    for (int q = 0; q < n; q += VW) {
+                        R v4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) v4[i] = (i < VW && q + i < n) ? gr[q + i] : R(0);
+                        *reinterpret_cast<VT *>(pr + q) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                    }
+                    pr[LD] = bc[0];
+                    if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
+                    pr[LD + 1] = R(1) / gr[k];
+                    diag = gr[k];
+                }
+            } else {
+                if (c == k) {  // every lane of the pivot row publishes its columns
+#pragma unroll
+                    for (int j = 0; j < NC; j += VW) {
+                        R v4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) v4[i] = i < VW ? gr[j + i] : R(0);
+                        *reinterpret_cast<VT *>(pr + col0 + j) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                    }
+                    if (lead) {
+                        pr[LD] = bc[0];
+                        if constexpr (NCOMP > 1) pr[LD + 2] = bc[1];
+                    }
+                    if (h == k / NC) {
+                        pr[LD + 1] = R(1) / gr[k % NC];
+                        diag = gr[k % NC];
+                    }
+                }
+            }
             group_sync(bar_id, G::GS);
             const R gk = row_entry(k);
-            if (real_lead && c != k)
+            if (real && c != k) {
+                const R l = gk * pr[LD + 1];
+                // columns < k hold multipliers (eliminated); only q > k change
+                if constexpr (SP == 1) {
 #pragma unroll
-                for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = fma(-gk, pr[cc], rc[cc]);
+                    for (int q = 0; q < n; q += VW) {
+                        if (q + VW <= k + 1) continue;  // chunk entirely at or before the pivot column
+                        const VT v = *reinterpret_cast<const VT *>(pr + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i > k && q + i < n) gr[q + i] = fma(-l, VV::at(v, i), gr[q + i]);
+                    }
+                    gr[k] = l;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; j += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(pr + col0 + j);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i) {
+                            const int q = col0 + j + i;
+                            if (q > k && q < n) gr[j + i] = fma(-l, VV::at(v, i), gr[j + i]);
+                        }
+                    }
+                    if (h == k / NC) gr[k % NC] = l;
+                }
+                bc[0] = fma(-l, pr[LD], bc[0]);
+                if constexpr (NCOMP > 1) bc[1] = fma(-l, pr[LD + 2], bc[1]);
+            }
+        }
+        if constexpr (SP > 1) diag = __shfl_sync(0xffffffffu, diag, rowbase + (c < n ? c : 0) / NC);  // the row's pivot
+        R x[NCOMP];
+#pragma unroll
+        for (int cc = 0; cc < NCOMP; ++cc) x[cc] = real_lead ? bc[cc] / diag : R(0);
+        bad |= real_lead && !(diag > R(0));
+
+        if constexpr (kPair) {
+            // one step of iterative refinement of the stacked least-squares
+            // residual: r = S^T (rhs - S x), G dx = r, x += dx (per field)
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc)
+                if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
+            group_sync(bar_id, G::GS);
+            if (real_lead) {
+                // (V x)_c from the particle's basis values: sum_j' hy_j' sum_i' hx_i' x[j'N + i']
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    R t2[N];
+#pragma unroll
+                    for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+                    for (int q = 0; q < n; q += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                    }
+                    R vx = R(0);
+#pragma unroll
+                    for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
+                    res[cc * P4 + c] = rhs[cc * P4 + c] - vx;
+                }
+            }
+            if (PHASE == 2 && SP == 1 && group_active && lead && c < 4 * N) {
+                // (B x) at face point c: w times the trace of x along the face
+                const int side = c / N, f = c % N;
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    const R *vc = vec + cc * P4;
+                    R bx = R(0);
+                    if (side < 2) {
+                        const R *hf = side == 0 ? sh0 : sh1;
+#pragma unroll
+                        for (int ii = 0; ii < N; ++ii) bx = fma(hf[ii], vc[f * N + ii], bx);
+                    } else {
+                        const R *hf = side == 2 ? sh0 : sh1;
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) bx = fma(hf[jj], vc[jj * N + f], bx);
+                    }
+                    res[cc * P4 + n + c] = rhs[cc * P4 + n + c] - wb * bx;
+                }
+            } else if (PHASE == 2 && SP > 1 && group_active && lead && c < 4 * N) {
+                const R *row = Vs + (n + c) * LD;
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    R bx = R(0);
+#pragma unroll
+                    for (int q = 0; q < n; q += VW) {
+                        const VT rv = *reinterpret_cast<const VT *>(row + q);
+                        const VT xv = *reinterpret_cast<const VT *>(vec + cc * P4 + q);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (q + i < n) bx = fma(VV::at(rv, i), VV::at(xv, i), bx);
+                    }
+                    res[cc * P4 + n + c] = rhs[cc * P4 + n + c] - bx;
+                }
+            }
+            group_sync(bar_id, G::GS);
+            R rc[NCOMP];
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = R(0);
+            if (SP == 1 && real_lead) {
+                // S^T r for row c = (i, j): sum_p V[p][c] r_p, then the four face terms
+                for (int p = 0; p < n; ++p) {
+                    const R vpc = Vs[p * HXS + ic] * Vs[p * HXS + N + jc];
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = fma(vpc, res[cc * P4 + p], rc[cc]);
+                }
+                const R b0x = wb * sh0[ic], b1x = wb * sh1[ic], b0y = wb * sh0[jc], b1y = wb * sh1[jc];
+#pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    const R *rf = res + cc * P4 + n;
+                    rc[cc] = fma(b0x, rf[jc], rc[cc]);
+                    rc[cc] = fma(b1x, rf[N + jc], rc[cc]);
+                    rc[cc] = fma(b0y, rf[2 * N + ic], rc[cc]);
+                    rc[cc] = fma(b1y, rf[3 * N + ic], rc[cc]);
+                }
+            } else if (real_lead)
+                for (int p = 0; p < P; p += VW) {
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) {
+                        const VT rv = *reinterpret_cast<const VT *>(res + cc * P4 + p);
+#pragma unroll
+                        for (int i = 0; i < VW; ++i)
+                            if (p + i < P) rc[cc] = fma(Vs[(p + i) * LD + c], VV::at(rv, i), rc[cc]);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < n; ++k) {
+                R *pr = piv + (k & 1) * (LD + 4);
+                if (c == k && lead)
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) pr[cc] = rc[cc];
+                group_sync(bar_id, G::GS);
+                const R gk = row_entry(k);
+                if (real_lead && c != k)
+#pragma unroll
+                    for (int cc = 0; cc < NCOMP; ++cc) rc[cc] = fma(-gk, pr[cc], rc[cc]);
+            }
+#pragma unroll
+            for (int cc = 0; cc < NCOMP; ++cc) x[cc] += real_lead ? rc[cc] / diag : R(0);
         }
 #pragma unroll
-        for (int cc = 0; cc < NCOMP; ++cc) x[cc] += real_lead ? rc[cc] / diag : R(0);
-    }
-#pragma unroll
-    for (int cc = 0; cc < NCOMP; ++cc) bad |= real_lead && !isfinite(x[cc]);
+        for (int cc = 0; cc < NCOMP; ++cc) bad |= real_lead && !isfinite(x[cc]);
 
-    if constexpr (PHASE == 1) {
-        // face values of the advected interpolant (alpha - c = x) at the 4N face points
+        if constexpr (PHASE == 1) {
 #pragma unroll
-        for (int cc = 0; cc < NCOMP; ++cc)
-            if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
-        group_sync(bar_id, G::GS);
+            for (int cc = 0; cc < NCOMP; ++cc)
+                if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
+            group_sync(bar_id, G::GS);
+        } else {
+            if (real_lead) {
+    #pragma unroll
+                for (int cc = 0; cc < NCOMP; ++cc) {
+                    if constexpr (kPair) {
+                        float hi, lo;
+                        two_sum2d(ch[cc], x[cc], hi, lo);
+                        Qg[qoff[cc] + c] = make_float2(hi, lo + cl[cc]);
+                    } else {
+                        Qg[qoff[cc] + c] = ch[cc] + x[cc];
+                    }
+                }
+            }
+        }
+    }
+    }  // direct path
+    if constexpr (PHASE == 1) {
         if (group_active && lead && c < 4 * N) {
             const int side = c / N, f = c % N;
 #pragma unroll
@@ -625,19 +1368,6 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                     out = ch[cc] + v;
                 }
                 faces[(fbase[cc] + e) * 4 * N + c] = out;
-            }
-        }
-    } else {
-        if (real_lead) {
-#pragma unroll
-            for (int cc = 0; cc < NCOMP; ++cc) {
-                if constexpr (kPair) {
-                    float hi, lo;
-                    two_sum2d(ch[cc], x[cc], hi, lo);
-                    Qg[qoff[cc] + c] = make_float2(hi, lo + cl[cc]);
-                } else {
-                    Qg[qoff[cc] + c] = ch[cc] + x[cc];
-                }
             }
         }
     }

@@ -44,6 +44,7 @@ DT_CFG1 = 6.510e-4  # K=8, N=6, u=1, D=0.01, edge gap: particles stay in-element
 DT_CFG2 = 7.33e-7   # K=256, N=16 node gap, |u|max=1.5, Dmax=0.015 (used for every N)
 DT_CFG2_HALF = 3.665e-7  # half of it: at DT_CFG2 itself the N=16 step amplifies perturbations
 DT_CFG3 = 6.93e-5   # 64x64, N=8 node gap, |u_j|max=pi, Dmax=0.0065
+DT_CFG3_HALF = 3.465e-5  # half of it: at DT_CFG3 itself the 2D step amplifies perturbations ~12 %/step
 DT_CFG3_EDGE = 1.618e-6  # the same with the first node's distance to the face (particles stay inside)
 
 

@@ -122,6 +122,9 @@ def test_config2_full_size_fp64_sampled(sl, orc, N, frac, steps, tol):
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
 @pytest.mark.parametrize("N,frac", [(16, 0.5), (12, 1.0), (8, 1.0), (4, 1.0)])
 def test_config2_full_size_mixed_vs_fp64(sl, orc, precision, N, frac):
+    # the full workload in the benchmark's launch configuration: the moments
+    # against the FP64 GPU path (itself pinned to the oracle above), and the
+    # first and last samples against the oracle recomputing them one by one
     pb = I.config2(N=N)
     pb["dt"] = frac * I.DT_CFG2
     with sl.Solver(pb, "fp64") as s:
@@ -130,7 +133,12 @@ def test_config2_full_size_mixed_vs_fp64(sl, orc, precision, N, frac):
     with sl.Solver(pb, precision) as s:
         s.step()
         mlo, _ = s.moments()
+        first, last = s.samples(0, 1)[0], s.samples(pb["M"] - 1, 1)[0]
     assert _rel(mlo, m64) <= MIXED_TOL
+    scale = np.abs(m64).max()
+    for sidx, got in ((0, first), (pb["M"] - 1, last)):
+        ref = orc.run(pb, s0=sidx, ns=1, want_states=True)["states"][0]
+        assert _rel(got, ref, scale) <= MIXED_TOL
 
 
 def test_restart_and_checkpoint_bitwise(sl):

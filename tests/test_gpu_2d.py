@@ -108,6 +108,29 @@ def test_config3_mesh_fp32_vs_fp64_edge_dt(sl, orc):
         assert _rel(s.samples(0, 1)[0], ref) <= FP64_TOL
 
 
+def test_config3_full_mesh_fp32_vs_oracle(sl, orc):
+    # the full 64x64, N=8 mesh at the edge-distance dt: 16 samples, 6 steps,
+    # FP32 moments and states against the oracle
+    pb = I.config3(M=16, steps=6, dt=I.DT_CFG3_EDGE)
+    e_mean, e_m2, e_st = _pair(sl, orc, pb, precision="fp32", states=16)
+    assert e_mean <= MIXED_TOL and e_m2 <= MIXED_TOL and e_st <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,N", [("fp32", 9), ("fp32", 10), ("fp32", 11), ("fp32", 12),
+                                         ("fp64", 9), ("fp64", 10), ("fp64", 11)])
+def test_high_order_launch_geometry_vs_oracle(sl, orc, precision, N):
+    # an 8x8 mesh with 8 samples: 512 element-sample groups, more CTAs than
+    # SMs at every order, several groups per CTA where the order allows it
+    # (FP32 per-sample states at half the edge-distance bound: at the node-gap
+    # bound a sample with a large increment leaves FP32 far less accurate)
+    pb = _rot(K=(8, 8), N=N, M=8, steps=3, orc=orc)
+    if precision == "fp32":
+        pb["dt"] = 0.5 * orc.dt_edge(pb)
+    e_mean, e_m2, e_st = _pair(sl, orc, pb, precision=precision, states=8)
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    assert e_mean <= tol and e_m2 <= tol and e_st <= tol
+
+
 @pytest.mark.parametrize("N", [9, 10, 11, 12])
 def test_fp32_high_order_vs_oracle(sl, orc, N):
     # N = 11, 12: each Gram row split over four lanes
