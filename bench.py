@@ -269,15 +269,17 @@ def leg_2d(sl, stream, horizon=500, acc_samples=16):
     return out
 
 
-def leg_batch(sl, stream):
-    """Batched uneven instances (one graph launch per call) vs the same
-    instances stepped one by one."""
+def leg_batch(sl, stream, m_div=32):
+    """Batched uneven instances (one graph launch per call, order classes on
+    tuned parallel branches) vs the same instances stepped one by one:
+    config 4 (all 512 drawn 2D instances, each with M/m_div samples, one
+    step; the full configuration is m_div x 100 times this work), 32 1D
+    draws of config 5, and 256 small 1D instances."""
     import torch
 
     out = {}
     draws = I.batch_instances(512)
-    two_d = [pb for pb in draws if pb["N"] <= 8][:12]
-    high = [dict(pb, M=64) for pb in draws if pb["N"] >= 9][:4]  # Gram rows split over lanes at N >= 11
+    cfg4 = [dict(pb, M=max(8, pb["M"] // m_div)) for pb in draws]
     one_d = []
     rng = np.random.default_rng(45)
     for i in range(32):
@@ -285,14 +287,14 @@ def leg_batch(sl, stream):
         pb["seed"] = 7000 + i
         one_d.append(pb)
     small = I.small_instances_1d()
-    for name, pbs, steps in (("config4_sample_2d", two_d, 1), ("config4_high_orders", high, 1),
-                             ("config5_1d_mix", one_d, 20), ("small_1d_uneven", small, 20)):
+    for name, pbs, steps in (("config4_all_512", cfg4, 1), ("config5_1d_mix", one_d, 20),
+                             ("small_1d_uneven", small, 20)):
         for pb in pbs:  # half of each instance's particle bound (2D: edge distance)
             pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
         esu = sum(int(np.prod(pb["K"])) * pb["M"] for pb in pbs) * steps
         with sl.Batch(pbs, "fp32") as b:
-            tune_ms = b.tune(2)
-            grids = b.grids()
+            tune_ms = b.tune(1)
+            grids, lanes = b.grids(), b.lanes()
             b.step(steps)  # capture
             t_batch = _timed(lambda: b.step(steps))
         solvers = [sl.Solver(pb, "fp32", stream=stream.cuda_stream) for pb in pbs]
@@ -309,18 +311,22 @@ def leg_batch(sl, stream):
             s.close()
         torch.cuda.synchronize()
         out[name] = {"instances": len(pbs), "steps": steps, "esu": esu,
-                     "batched": {"value": esu / t_batch, "unit": "ESU/s"},
-                     "one_by_one": {"value": esu / t_seq, "unit": "ESU/s"},
-                     "speedup": t_seq / t_batch, "tuned_grids": grids, "tune_ms": tune_ms}
+                     "batched": {"value": esu / t_batch, "unit": "ESU/s", "seconds": t_batch},
+                     "one_by_one": {"value": esu / t_seq, "unit": "ESU/s", "seconds": t_seq},
+                     "speedup": t_seq / t_batch, "tuned_grids_1d": grids, "tuned_branches": lanes,
+                     "tune_ms": tune_ms}
+    c4 = out["config4_all_512"]
+    full = sum(int(np.prod(pb["K"])) * pb["M"] for pb in draws) * 100
+    c4["what"] = (f"all 512 config-4 draws (K ~ U{{16..64}}, N ~ U{{4..12}}, constant or rotating drift) with "
+                  f"M/{m_div} samples each, one step, FP32; the configuration as drawn (full M, 100 steps) is "
+                  f"{full:.3g} ESU, {full / c4['esu']:.0f}x this")
+    c4["full_config_extrapolated_s"] = full / c4["batched"]["value"]
     out["small_1d_uneven"]["what"] = ("256 instances, K ~ U{8..64}, N ~ U{4..8}, M ~ U{16..128}: each alone is "
                                       "far from filling the GPU, so one-by-one stepping is launch-bound")
-    out["config4_high_orders"]["what"] = ("the first 4 config-4 draws with N >= 9, M reduced to 64, one step "
-                                          "(orders 11 and 12 split each Gram row over four lanes)")
-    out["summary"] = {k: {"batched_esu_per_s": v["batched"]["value"], "speedup": v["speedup"]}
+    out["summary"] = {k: {"batched_esu_per_s": v["batched"]["value"], "speedup": v["speedup"],
+                          "branches": v["tuned_branches"]}
                       for k, v in out.items() if isinstance(v, dict) and "batched" in v}
-    out["note"] = ("config 4 as drawn (512 instances, N up to 12, 100 steps, ~8.8e10 ESU) is not run: the 2D path "
-                   "runs at ~1e7 ESU/s at N=8 and the cost grows as N^6; the first 12 draws with N<=8 and the "
-                   "first 4 with N>=9 (M=64) are timed for one step")
+    out["summary"]["config4_full_extrapolated_s"] = c4["full_config_extrapolated_s"]
     return out
 
 

@@ -343,12 +343,18 @@ int sl_batch_step(sl_batch *b, int steps);
 
 /* Autotuner: for each 1D order, times the persistent kernel on the real    */
 /* instances for `probe_steps` steps with 1..4 CTAs per SM and keeps the     */
-/* fastest; every instance's state and step counter are restored afterwards. */
-/* best_ms (may be NULL) receives the sum of the best probe times.           */
+/* fastest; then times whole steps with the order classes spread over 1, 2  */
+/* or 4 parallel graph branches and keeps the fastest.  Every instance's    */
+/* state and step counter are restored afterwards.  best_ms (may be NULL)  */
+/* receives the best whole-step probe time.                                  */
 int sl_batch_tune(sl_batch *b, int probe_steps, double *best_ms);
 
 /* Persistent grid chosen for 1D class `cls` (order N, CTAs, instances).     */
 int sl_batch_grid(const sl_batch *b, int cls, int *N, int *grid, int *instances);
+
+/* Parallel graph branches a step's order classes are spread over (1 until  */
+/* sl_batch_tune chooses).                                                   */
+int sl_batch_lanes(const sl_batch *b, int *lanes);
 
 /* Moments / samples of instance i (as sl_moments / sl_get_samples).         */
 int sl_batch_moments(sl_batch *b, int i, double *mean, double *m2);

@@ -116,6 +116,7 @@ def lib():
         L.sl_batch_step.argtypes = [vp, C.c_int]
         L.sl_batch_tune.argtypes = [vp, C.c_int, _dp]
         L.sl_batch_grid.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sl_batch_lanes.argtypes = [vp, C.POINTER(C.c_int)]
         L.sl_batch_moments.argtypes = [vp, C.c_int, _dp, _dp]
         L.sl_batch_samples.argtypes = [vp, C.c_int, C.c_int, C.c_int, _dp]
         L.sl_batch_free.argtypes = [vp]
@@ -364,6 +365,12 @@ def sl_batch_grid(b, cls):
     return None if rc != 0 else (N.value, g.value, k.value)
 
 
+def sl_batch_lanes(b):
+    v = C.c_int()
+    _check(lib().sl_batch_lanes(C.c_void_p(b), C.byref(v)), "sl_batch_lanes")
+    return v.value
+
+
 def sl_batch_moments(b, i, V):
     mean, m2 = np.zeros(V), np.zeros(V)
     _check(lib().sl_batch_moments(C.c_void_p(b), int(i), _f64p(mean), _f64p(m2)), "sl_batch_moments")
@@ -403,6 +410,10 @@ class Batch:
                 return out
             out.append(g)
             c += 1
+
+    def lanes(self):
+        """Parallel graph branches of a step (chosen by tune())."""
+        return sl_batch_lanes(self.h)
 
     def moments(self, i):
         pb = self.problems[i]

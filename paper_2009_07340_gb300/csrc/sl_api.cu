@@ -310,6 +310,8 @@ void sl_free(sl_ctx *c)
     sl::ctx_free(c, c->m2_tmp);
     sl::ctx_free(c, c->err);
     sl::ctx_free(c, c->faces2d);
+    sl::ctx_free(c, c->tab2d);
+    sl::ctx_free(c, c->fb2d);
     delete c;
 }
 
@@ -403,7 +405,9 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
               (dim == 1 || (dalloc(c, &c->faceUhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess &&
                             dalloc(c, &c->faceBhi, size_t(m.K[0] + m.K[1]) * N) == cudaSuccess));
     if (ok && dim == 2)
-        ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * ncomp * m.E * 4 * N * c->state_elem) == cudaSuccess;
+        ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * ncomp * m.E * 4 * N * c->state_elem) == cudaSuccess &&
+             dalloc(c, &c->tab2d, size_t(N) * N + 5 * N) == cudaSuccess &&
+             sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fb2d), size_t(M) * m.E) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         sl_free(c);
@@ -425,6 +429,23 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
         cudaGetLastError();
         sl_free(c);
         return SL_ERR_CUDA;
+    }
+    if (dim == 2) {  // the order's node tables, from the device's own nodes
+        std::vector<double> xh(N), tab(size_t(N) * N + 5 * N);
+        if (cudaMemcpyAsync(xh.data(), c->xi, N * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess) {
+            cudaGetLastError();
+            sl_free(c);
+            return SL_ERR_CUDA;
+        }
+        sl::node_tables2d(N, xh.data(), tab.data());
+        if (cudaMemcpyAsync(c->tab2d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess) {
+            cudaGetLastError();
+            sl_free(c);
+            return SL_ERR_CUDA;
+        }
     }
 
     if (dim == 1) {
@@ -603,7 +624,11 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.dt = dt;
             a.hx = m.h[0];
             a.hy = m.h[1];
+            a.s4x = 4.0 / m.h[0];
+            a.s4y = 4.0 / m.h[1];
             a.xi = c->xi;
+            a.tab = c->tab2d;
+            a.fb = c->fb2d;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
             a.nodeDiv = c->nodeDiv;

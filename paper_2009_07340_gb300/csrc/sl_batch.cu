@@ -12,8 +12,13 @@
 //   3. per 2D class, two launches per step over the element-sample groups of
 //      all instances of the class;
 //   4. one kernel advancing the step counters.
-// The persistent grid of each 1D class is chosen by sl_batch_tune, which
-// times the candidate grids on the real instances and restores their state.
+// Steps 2 and 3 of different classes are independent (disjoint instances):
+// they are spread over `lanes` streams forked from and joined back to the
+// batch stream, so in the captured graph they are parallel branches and a
+// small class can run beside a large one instead of after it.
+// sl_batch_tune times, on the real instances, the persistent grid of each 1D
+// class and then the number of branches (1, 2 or 4), restoring every
+// instance's state afterwards.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +69,10 @@ struct sl_batch {
     int poisoned = 0;
     int nsm = 0;
     bool own_stream = false;  // graphs cannot be captured on the legacy default stream
+    static constexpr int kMaxLanes = 4;
+    int lanes = 1;                              // parallel branches of a step (sl_batch_tune)
+    cudaStream_t lane_st[kMaxLanes] = {};       // branch streams (lane 0 is the batch stream itself)
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxLanes] = {};
 };
 
 namespace {
@@ -149,7 +158,11 @@ sl::Step2DArgs args2d(const sl_ctx *c, double dt, int steps)
     a.dt = dt;
     a.hx = c->m.h[0];
     a.hy = c->m.h[1];
+    a.s4x = 4.0 / c->m.h[0];
+    a.s4y = 4.0 / c->m.h[1];
     a.xi = c->xi;
+    a.tab = c->tab2d;
+    a.fb = c->fb2d;
     a.nodeU = c->nodeU;
     a.nodeB = c->nodeB;
     a.nodeDiv = c->nodeDiv;
@@ -183,11 +196,11 @@ T *upload(const std::vector<T> &v, std::vector<void *> &keep)
     return d;
 }
 
-cudaError_t launch_1d_class(const sl_batch *b, const Class1D &k, const sl::Batch1DLaunch &l)
+cudaError_t launch_1d_class(const sl_batch *b, const Class1D &k, const sl::Batch1DLaunch &l, cudaStream_t st)
 {
-    if (b->precision == SL_FP64) return sl::launch_step1d_batch_fp64(l, k.N, b->st);
-    if (b->precision == SL_MIXED) return sl::launch_step1d_batch_mixed(l, k.N, b->st);
-    return sl::launch_step1d_batch_fp32(l, k.N, b->st);
+    if (b->precision == SL_FP64) return sl::launch_step1d_batch_fp64(l, k.N, st);
+    if (b->precision == SL_MIXED) return sl::launch_step1d_batch_mixed(l, k.N, st);
+    return sl::launch_step1d_batch_fp32(l, k.N, st);
 }
 
 size_t smem_1d(int precision, int N, int S, int T)
@@ -250,29 +263,73 @@ int prepare_step(sl_batch *b, int steps, StepTables &t, std::vector<void *> &kee
     return SL_OK;
 }
 
-// Enqueues the step on b->st: kernel launches and one memset only, so it can
-// be captured into a graph.
+// Enqueues the step on b->st: kernel launches, events and stream waits only,
+// so it can be captured into a graph.  The classes' launches go to b->lanes
+// branch streams forked from b->st after the Wiener kernel and joined back
+// before the counters advance; each class goes to the branch with the least
+// estimated work so far, in decreasing order of work.
 int enqueue_step(sl_batch *b, int steps, const StepTables &t)
 {
     const int n = int(b->inst.size());
     if (sl::launch_wiener_batch(b->d_jobs, t.jprefix, n, steps, b->d_steps, t.jtotal, b->st) != cudaSuccess)
         return SL_ERR_CUDA;
-    for (size_t i = 0; i < b->c1.size(); ++i)
-        if (launch_1d_class(b, b->c1[i], t.l1[i]) != cudaSuccess) return SL_ERR_CUDA;
-    for (int id : b->solo) {
-        const sl::Step1DArgs a = args1d(b->inst[id], b->dt[id], steps);
-        cudaError_t e;
-        if (b->precision == SL_FP64) e = sl::launch_step1d_fp64(a, b->inst[id]->m.N, b->st);
-        else if (b->precision == SL_MIXED) e = sl::launch_step1d_mixed(a, b->inst[id]->m.N, b->st);
-        else e = sl::launch_step1d_fp32(a, b->inst[id]->m.N, b->st);
-        if (e != cudaSuccess) return SL_ERR_CUDA;
+    const int L = std::max(1, std::min(b->lanes, sl_batch::kMaxLanes));
+    b->lane_st[0] = b->st;
+    if (L > 1) {
+        if (cudaEventRecord(b->fork_ev, b->st) != cudaSuccess) return SL_ERR_CUDA;
+        for (int l = 1; l < L; ++l)
+            if (cudaStreamWaitEvent(b->lane_st[l], b->fork_ev, 0) != cudaSuccess) return SL_ERR_CUDA;
     }
+    // work items: (estimated element-sample-node work, kind, index)
+    struct Item {
+        double work;
+        int kind, idx;
+    };
+    std::vector<Item> items;
+    auto work_of = [&](int id) {
+        const sl_ctx *c = b->inst[id];
+        const double nn = double(c->m.n);
+        return double(c->m.E) * c->M * (c->m.dim == 1 ? nn * nn : nn * nn * nn);
+    };
+    for (size_t i = 0; i < b->c1.size(); ++i) {
+        double w = 0.0;
+        for (int id : b->c1[i].ids) w += work_of(id);
+        items.push_back({w, 1, int(i)});
+    }
+    for (int id : b->solo) items.push_back({work_of(id), 0, id});
     for (size_t i = 0; i < b->c2.size(); ++i) {
-        const cudaError_t e = b->precision == SL_FP64 ? sl::launch_step2d_batch_fp64(t.l2[i], b->c2[i].N, b->st)
-                                                      : sl::launch_step2d_batch_fp32(t.l2[i], b->c2[i].N, b->st);
-        if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;
+        double w = 0.0;
+        for (int id : b->c2[i].ids) w += work_of(id);
+        items.push_back({w, 2, int(i)});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.work > y.work; });
+    double load[sl_batch::kMaxLanes] = {};
+    for (const Item &it : items) {
+        int l = 0;
+        for (int k = 1; k < L; ++k)
+            if (load[k] < load[l]) l = k;
+        load[l] += it.work;
+        cudaStream_t st = b->lane_st[l];
+        cudaError_t e = cudaSuccess;
+        if (it.kind == 1) {
+            e = launch_1d_class(b, b->c1[it.idx], t.l1[it.idx], st);
+        } else if (it.kind == 0) {
+            const int id = it.idx;
+            const sl::Step1DArgs a = args1d(b->inst[id], b->dt[id], steps);
+            if (b->precision == SL_FP64) e = sl::launch_step1d_fp64(a, b->inst[id]->m.N, st);
+            else if (b->precision == SL_MIXED) e = sl::launch_step1d_mixed(a, b->inst[id]->m.N, st);
+            else e = sl::launch_step1d_fp32(a, b->inst[id]->m.N, st);
+        } else {
+            e = b->precision == SL_FP64 ? sl::launch_step2d_batch_fp64(t.l2[it.idx], b->c2[it.idx].N, st)
+                                        : sl::launch_step2d_batch_fp32(t.l2[it.idx], b->c2[it.idx].N, st);
+            if (e == cudaErrorNotSupported) return SL_ERR_UNSUPPORTED;
+        }
         if (e != cudaSuccess) return SL_ERR_CUDA;
     }
+    for (int l = 1; l < L; ++l)
+        if (cudaEventRecord(b->join_ev[l], b->lane_st[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->st, b->join_ev[l], 0) != cudaSuccess)
+            return SL_ERR_CUDA;
     if (sl::launch_advance_counters(b->d_steps, n, steps, b->st) != cudaSuccess) return SL_ERR_CUDA;
     return SL_OK;
 }
@@ -287,6 +344,11 @@ void sl_batch_free(sl_batch *b)
     drop_graphs(b);
     for (sl_ctx *c : b->inst) sl_free(c);
     for (Class1D &k : b->c1) cudaFree(k.d_counter);
+    for (int l = 1; l < sl_batch::kMaxLanes; ++l) {
+        if (b->lane_st[l]) cudaStreamDestroy(b->lane_st[l]);
+        if (b->join_ev[l]) cudaEventDestroy(b->join_ev[l]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     cudaFree(b->d_steps);
     cudaFree(b->d_jobs);
     cudaFree(b->d_jprefix);
@@ -379,6 +441,16 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
         k.max_grid = 2 * b->nsm;  // refined by sl_batch_tune
         k.grid = b->nsm;
     }
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+        sl_batch_free(b);
+        return SL_ERR_CUDA;
+    }
+    for (int l = 1; l < sl_batch::kMaxLanes; ++l)
+        if (cudaStreamCreateWithFlags(&b->lane_st[l], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_ev[l], cudaEventDisableTiming) != cudaSuccess) {
+            sl_batch_free(b);
+            return SL_ERR_CUDA;
+        }
     if (cudaMalloc(&b->d_steps, count * sizeof(long long)) != cudaSuccess ||
         cudaMemset(b->d_steps, 0, count * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&b->d_jobs, count * sizeof(sl::WienerJob)) != cudaSuccess) {
@@ -497,6 +569,30 @@ int sl_batch_tune(sl_batch *b, int probe_steps, double *best_ms)
         k.grid = best;
         total_best += best_t;
     }
+    // the number of parallel branches, timed on whole steps
+    {
+        int best_l = 1;
+        float best_t = 1e30f;
+        for (int L : {1, 2, 4}) {
+            b->lanes = L;
+            std::vector<void *> keep;
+            StepTables tables;
+            int r = prepare_step(b, probe_steps, tables, keep);
+            cudaEventRecord(e0, b->st);
+            if (r == SL_OK) r = enqueue_step(b, probe_steps, tables);
+            cudaEventRecord(e1, b->st);
+            cudaEventSynchronize(e1);
+            for (void *p : keep) cudaFree(p);
+            float ms = -1.f;
+            if (r == SL_OK) cudaEventElapsedTime(&ms, e0, e1);
+            if (ms > 0.f && ms < best_t) {
+                best_t = ms;
+                best_l = L;
+            }
+        }
+        b->lanes = best_l;
+        total_best = best_t;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // restore states and counters; graphs captured before tuning are stale
@@ -520,6 +616,13 @@ int sl_batch_grid(const sl_batch *b, int cls, int *N, int *grid, int *instances)
     if (N) *N = b->c1[cls].N;
     if (grid) *grid = b->c1[cls].grid;
     if (instances) *instances = int(b->c1[cls].ids.size());
+    return SL_OK;
+}
+
+int sl_batch_lanes(const sl_batch *b, int *lanes)
+{
+    if (!b || !lanes) return SL_ERR_ARG;
+    *lanes = b->lanes;
     return SL_OK;
 }
 

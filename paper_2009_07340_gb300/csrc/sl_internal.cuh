@@ -91,7 +91,11 @@ struct Step2DArgs {
     int Kx, Ky, M;
     int nsteps;
     double dt, hx, hy;
+    double s4x, s4y;       // 4 / hx, 4 / hy (displacements in scaled element units)
     const double *xi;
+    const double *tab;     // [N N + 5 N] node tables: 4 (xi_i - xi_m), barycentric weights of the
+                           // scaled nodes, h_i(0), h_i(1), -4 xi_i, 4 (1 - xi_i)
+    unsigned char *fb;     // [M][E]: groups the iterative solve left to the direct one
     const double *nodeU;   // [2][E][n]
     const double *nodeB;   // [E][n]
     const double *nodeDiv; // [E][n]
@@ -146,6 +150,8 @@ cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st);
 // two fields per sample (Q [M][2][E][n], faces [M][2][E][4N]), N <= 8
 cudaError_t launch_step2d_c2(const Step2DArgs &a, int N, bool fp64, cudaStream_t st);
+// Host-side node tables of a 2D order (Step2DArgs::tab) from the nodes xi[N].
+void node_tables2d(int N, const double *xi, double *tab);
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
                                const double *phi0_nodal_dev, double *xi, double *nodeU, double *nodeB,
                                double *nodeDiv, double *faceU, double *faceB, void *Q, int M,
@@ -228,6 +234,8 @@ struct sl_ctx {
     int mom_chunk = 64;
     int *err = nullptr;
     void *faces2d = nullptr;  // 2D face-value scratch
+    double *tab2d = nullptr;  // 2D node tables of the order (Step2DArgs::tab)
+    unsigned char *fb2d = nullptr;  // 2D: groups left to the direct solve, [M][E]
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
     double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)

@@ -521,6 +521,29 @@ cudaError_t launch_moments_combine(const double *psum, const double *psq, int nc
     return cudaGetLastError();
 }
 
+void node_tables2d(int N, const double *xi, double *tab)
+{
+    // the same FP64 expressions, in the same order, as the step kernels used
+    // when they formed these tables themselves
+    double *Z = tab, *lam = tab + N * N, *h0 = lam + N, *h1 = h0 + N, *x0 = h1 + N, *x1 = x0 + N;
+    for (int i = 0; i < N; ++i)
+        for (int m = 0; m < N; ++m) Z[i * N + m] = 4.0 * (xi[i] - xi[m]);
+    for (int j = 0; j < N; ++j) {
+        double l = 1.0, l0 = 1.0, l1 = 1.0;
+        for (int m = 0; m < N; ++m)
+            if (m != j) {
+                l /= 4.0 * (xi[j] - xi[m]);
+                l0 *= (0.0 - xi[m]) / (xi[j] - xi[m]);
+                l1 *= (1.0 - xi[m]) / (xi[j] - xi[m]);
+            }
+        lam[j] = l;
+        h0[j] = l0;
+        h1[j] = l1;
+        x0[j] = -4.0 * xi[j];
+        x1[j] = 4.0 * (1.0 - xi[j]);
+    }
+}
+
 cudaError_t preload_setup()
 {
     cudaError_t e = prepare_kernel(init_nodes_kernel<double>);

@@ -96,7 +96,7 @@ constexpr int split2d()
     return std::is_same<R, float>::value ? (N <= 9 ? 1 : (N <= 11 ? 2 : 4)) : (N <= 8 ? 1 : (N <= 10 ? 2 : 4));
 }
 
-template <int N, typename R, int NCOMP = 1>
+template <int N, typename R, int NCOMP = 1, bool FASTONLY = false>
 struct Geo2D {
     static constexpr int n = N * N;
     static constexpr int SP = split2d<N, R>();                  // lanes per row
@@ -115,17 +115,19 @@ struct Geo2D {
     static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
     static constexpr int HXS = (2 * N + 3) & ~3;                // stride of the particles' basis-value table
     // the tensor-preconditioned fast path (one lane per row, N <= 8, one field)
-    static constexpr bool kFast = SP == 1 && N <= 8 && NCOMP == 1;
+    static constexpr bool kFast = SP == 1 && N <= 8 && NCOMP <= 2;
     __host__ __device__ static constexpr int r4(int v) { return (v + 3) & ~3; }
     // its buffers after the basis-value table: hxT, hyT [N][n]; Wx, WxT, Wy, WyT [N][N];
     // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [n]; u4, mu4 [4N]; two pivot rows [4N + 4];
     // convergence slots [2][GS / 32][2]
     static constexpr int kFastBuf = kFast ? 2 * N * r4(n) + 4 * r4(N * N) + 6 * r4(N) + 2 * r4(n) + 2 * r4(4 * N) +
-                                                2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1)
+                                                2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1) + 4 * N * r4(4 * N)
                                           : 0;
     // rhs, vec and res hold one P4-long array per field
     static constexpr int kRows0 = P * LD;
-    static constexpr int kRows = kFast && n * HXS + kFastBuf > kRows0 ? r4(n * HXS + kFastBuf) : kRows0;
+    // the fast-path kernel holds no stacked rows: only the basis values and its buffers
+    static constexpr int kRows = FASTONLY ? r4(n * HXS + kFastBuf)
+                                          : (kFast && n * HXS + kFastBuf > kRows0 ? r4(n * HXS + kFastBuf) : kRows0);
     static constexpr int kRhs = NCOMP * P4, kPiv = 2 * (LD + 4), kVec = NCOMP * P4, kRes = NCOMP * P4;
     static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
     // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N], -4 xi [N], 4 (1 - xi) [N]
@@ -144,17 +146,31 @@ constexpr int min_ctas2d()
     return std::is_same<R, float>::value ? (N <= 6 ? 3 : (N <= 11 ? 2 : 1)) : (N == 9 ? 2 : 1);
 }
 
+// CTAs per SM of the fast-path kernel (MODE 1): it holds no Gram or pivot
+// rows, so FP32 fits three 256-thread CTAs (85 registers) where the direct
+// solve fits two; FP64 keeps two.
+template <int N, typename R>
+constexpr int min_ctas2d_fast()
+{
+    return std::is_same<R, float>::value ? 3 : 2;
+}
+
 // BATCH = false: one instance (a0), group g = element-sample g.
 // BATCH = true: `ninst` instances of the same N, instance i owning groups
 // [prefix[i], prefix[i+1]) (its E*M element-samples).
 // NCOMP = 2: two fields per sample ([M][2][E][n]) on the same particles, so
 // one Gram matrix, one elimination and one upwind choice serve both; each
 // field has its own right-hand side, refinement, faces and state.
-template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1>
-__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args,
-                                                                    const long long *__restrict__ prefix, int ninst, int t)
+// MODE 0: the direct solve for every group (orders without the fast path).
+// MODE 1: the fast path only; a group it does not finish is flagged in fb.
+// MODE 2: the direct solve for the groups MODE 1 flagged (CTAs without one exit).
+template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 0>
+__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
+    sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args, const long long *__restrict__ prefix,
+                     int ninst, int t)
 {
-    using G = Geo2D<N, R, NCOMP>;
+    using G = Geo2D<N, R, NCOMP, MODE == 1>;
+    static_assert(MODE == 0 || G::kFast, "the fast path and its fallback exist for one-lane rows, N <= 8, one or two fields");
     constexpr int P4 = G::P4;  // stride of the per-field arrays
     constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
     constexpr int HXS = G::HXS;  // stride of the phase-2 basis-value table (16-byte rows)
@@ -187,26 +203,33 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     R *vec = piv + G::kPiv;        // [NCOMP][P4] broadcast vectors
     R *res = vec + G::kVec;        // [NCOMP][P4] residuals
 
-    // node tables depend on N only (every instance of a batch class shares them)
-    const double *xi = BATCH ? args[0].xi : a0.xi;
-    if (threadIdx.x < N * N) {
-        const int i = threadIdx.x / N, m = threadIdx.x % N;
-        sZ[threadIdx.x] = R(4.0 * (xi[i] - xi[m]));
-    }
-    if (threadIdx.x < N) {
-        const int j = threadIdx.x;
-        double lam = 1.0, l0 = 1.0, l1 = 1.0;
-        for (int m = 0; m < N; ++m)
-            if (m != j) {
-                lam /= 4.0 * (xi[j] - xi[m]);
-                l0 *= (0.0 - xi[m]) / (xi[j] - xi[m]);
-                l1 *= (1.0 - xi[m]) / (xi[j] - xi[m]);
+    // node tables depend on N only (every instance of a batch class shares
+    // them); computed once per context on the host (node_tables2d)
+    const double *tabsrc = BATCH ? args[0].tab : a0.tab;
+    for (int k = threadIdx.x; k < G::kTables; k += blockDim.x) tab[k] = R(tabsrc[k]);
+    if constexpr (MODE == 2) {  // a CTA none of whose groups was flagged has nothing to do
+        bool any = false;
+#pragma unroll
+        for (int g2 = 0; g2 < G::GPC; ++g2) {
+            const long long gg = (BATCH ? 0 : a0.g0) + (long long)blockIdx.x * G::GPC + g2;
+            long long gl = gg;
+            const Step2DArgs *ai = &a0;
+            if constexpr (BATCH) {
+                if (gg >= prefix[ninst]) continue;
+                int lo = 0, hi = ninst - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (prefix[mid] <= gg) lo = mid;
+                    else hi = mid - 1;
+                }
+                ai = args + lo;
+                gl = gg - prefix[lo];
+            } else if (gg >= a0.g1) {
+                continue;
             }
-        slam[j] = R(lam);
-        sh0[j] = R(l0);
-        sh1[j] = R(l1);
-        sX0[j] = R(-4.0 * xi[j]);
-        sX1[j] = R(4.0 * (1.0 - xi[j]));
+            any |= ai->fb[gl] != 0;
+        }
+        if (!any) return;  // uniform over the CTA, before its one CTA-wide barrier
     }
     __syncthreads();
 
@@ -231,6 +254,9 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     const bool real = group_active && c < n;     // every lane of a real row
     const bool real_lead = real && lead;          // its per-row work
     const int bar_id = 1 + grp;
+    if constexpr (MODE == 2) {
+        if (!(group_active && a.fb[gid] != 0)) return;  // finished by the fast path
+    }
 
     // reference values and own state, per field
     State *Qg = reinterpret_cast<State *>(a.Q);
@@ -271,8 +297,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
         const double b = a.nodeB[(long long)e * n + c];
         // explicit unfused products: the compiler may not contract these
         // differently in the batched and single kernels
-        const R dx = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx))) / a.hx);
-        const R dy = R(__dmul_rn(4.0, __dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy))) / a.hy);
+        const R dx = R(__dmul_rn(__dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx)), a.s4x));
+        const R dy = R(__dmul_rn(__dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy)), a.s4y));
         dxp = dx;
         dyp = dy;
         const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
@@ -455,7 +481,7 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     // the element) or whose iteration has not converged after kFastIters
     // takes the direct path below, which is unchanged by this one.
     bool done = false;
-    if constexpr (G::kFast) {
+    if constexpr (G::kFast && MODE == 1) {
         constexpr int NW = G::GS / 32;
         constexpr int NT = G::r4(n), R4N = G::r4(N);
         constexpr float kFastCond = 64.0f;
@@ -479,9 +505,10 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
         R *mu4 = u4 + G::r4(4 * N);     // [4N]
         R *prow = mu4 + G::r4(4 * N);   // [2][4N + 4] pivot rows of the inversion of C
         unsigned *red = reinterpret_cast<unsigned *>(prow + 2 * G::r4(4 * N + 4));  // [2][NW][2] maxima, [1] decision
+        R *Ci = prow + 2 * G::r4(4 * N + 4) + G::r4(4 * NW + 1);  // [4N][r4(4N)] C^{-1}
         static_assert(n * HXS + G::kFastBuf <= G::kRows, "fast-path buffers fit in the rows' space");
         const int lane = threadIdx.x & 31, wig = tig >> 5;
-        const R cref = R(fabs(double(ch[0])));
+        R cref = R(0);  // |c| of the field being iterated
 
         // displacements (and, in phase 2, the particles' basis values) to shared memory
         if (c < n) {
@@ -576,52 +603,65 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                 return __uint_as_float(md) <= kFastTol * (__uint_as_float(mx) + float(cref));
             };
             if constexpr (PHASE == 1) {
-                R x = R(0);                        // alpha - c at node c
-                R r = real ? rhs[c] : R(0);        // phi* - V alpha at particle c
-                for (int it = 0; it < kFastIters; ++it) {
-                    if (c < n) res[c] = r;
-                    group_sync(bar_id, G::GS);
-                    // V0^{-1} r: [(b, i)] = sum_a Wx[i][a] r[(b, a)] (stored at [i][b]), then sum_b Wy[j][b] [(b, i)]
-                    if (c < n) {
-                        const int i = c % N, b = c / N;
-                        R t = R(0);
+                // one field after the other, each with exactly the arithmetic
+                // and the stopping decision of a single-field run
+                bool all = true;
+                for (int cc = 0; cc < NCOMP && all; ++cc) {
+                    R *vc = vec + cc * P4, *rs = res + cc * P4;
+                    const R *hs = rhs + cc * P4;
+                    cref = R(fabs(double(ch[cc])));
+                    R x = R(0);                  // alpha - c at node c
+                    R r = real ? hs[c] : R(0);   // phi* - V alpha at particle c
+                    bool conv = false;
+                    for (int it = 0; it < kFastIters; ++it) {
+                        if (c < n) rs[c] = r;
+                        group_sync(bar_id, G::GS);
+                        // V0^{-1} r: [(b, i)] = sum_a Wx[i][a] r[(b, a)] (stored at [i][b]), then sum_b Wy[j][b] [(b, i)]
+                        if (c < n) {
+                            const int i = c % N, b = c / N;
+                            R t = R(0);
 #pragma unroll
-                        for (int a2 = 0; a2 < N; ++a2) t = fma(Wx[i * N + a2], res[b * N + a2], t);
-                        tA[i * N + b] = t;
-                    }
-                    group_sync(bar_id, G::GS);
-                    R d = R(0);
-                    if (c < n) {
-                        const int i = c % N, j = c / N;
-#pragma unroll
-                        for (int b = 0; b < N; ++b) d = fma(Wy[j * N + b], tA[i * N + b], d);
-                        x += d;
-                        vec[c] = x;
-                    }
-                    publish_maxima(it, d, x);
-                    group_sync(bar_id, G::GS);
-                    if (converged(it)) {
-                        done = true;
-                        break;
-                    }
-                    if (real) {  // the new residual at particle c, from every node's x
-                        R t2[N];
-#pragma unroll
-                        for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
-#pragma unroll
-                        for (int q = 0; q < n; q += VW) {
-                            const VT v = *reinterpret_cast<const VT *>(vec + q);
-#pragma unroll
-                            for (int i = 0; i < VW; ++i)
-                                if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                            for (int a2 = 0; a2 < N; ++a2) t = fma(Wx[i * N + a2], rs[b * N + a2], t);
+                            tA[i * N + b] = t;
                         }
-                        R vx = R(0);
+                        group_sync(bar_id, G::GS);
+                        R d = R(0);
+                        if (c < n) {
+                            const int i = c % N, j = c / N;
 #pragma unroll
-                        for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
-                        r = rhs[c] - vx;
+                            for (int b = 0; b < N; ++b) d = fma(Wy[j * N + b], tA[i * N + b], d);
+                            x += d;
+                            vc[c] = x;
+                        }
+                        publish_maxima(it, d, x);
+                        group_sync(bar_id, G::GS);
+                        if (converged(it)) {
+                            conv = true;
+                            break;
+                        }
+                        if (real) {  // the new residual at particle c, from every node's x
+                            R t2[N];
+#pragma unroll
+                            for (int jj = 0; jj < N; ++jj) t2[jj] = R(0);
+#pragma unroll
+                            for (int q = 0; q < n; q += VW) {
+                                const VT v = *reinterpret_cast<const VT *>(vc + q);
+#pragma unroll
+                                for (int i = 0; i < VW; ++i)
+                                    if (q + i < n) t2[(q + i) / N] = fma(hx[(q + i) % N], VV::at(v, i), t2[(q + i) / N]);
+                            }
+                            R vx = R(0);
+#pragma unroll
+                            for (int jj = 0; jj < N; ++jj) vx = fma(hy[jj], t2[jj], vx);
+                            r = hs[c] - vx;
+                        }
                     }
+                    all = all && conv;
                 }
+                done = all;
             } else {
+                R *const gvec = vec, *const gres = res;
+                const R *const grhs = rhs;
                 const R wb = R(a.w), wi2 = R(1) / (wb * wb);
                 // products for C: Wx Wx^T at tA, Wy Wy^T at tB, and
                 // hvx[s][i] = sum_a Wx[i][a] gx_s[a] at u4[s N + i], hvy[s][j] = sum_b Wy[j][b] gy_s[b] at u4[(2 + s) N + j]
@@ -697,8 +737,22 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                             }
                         }
                     }
+                    if (lane < 4 * N)  // row lane of C^{-1} to shared memory (16-byte stores)
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                            R v4[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
+                            *reinterpret_cast<VT *>(Ci + lane * G::r4(4 * N) + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                        }
                 }
-                R q = R(0);  // q - c at node c
+                R qf[NCOMP];  // q - c at node c, per field
+                bool all = true;
+                for (int cc = 0; cc < NCOMP && all; ++cc) {
+                R *vec = gvec + cc * P4, *res = gres + cc * P4;
+                const R *rhs = grhs + cc * P4;
+                cref = R(fabs(double(ch[cc])));
+                R q = R(0);
                 bool conv = false;
                 for (int it = 0; it <= kFastIters; ++it) {
                     if (c < n) vec[c] = q;
@@ -803,11 +857,17 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                         u4[c] = uv;
                     }
                     group_sync(bar_id, G::GS);
-                    if (wig == 0 && lane < 4 * N) {  // mu = C^{-1} u
+                    if (c < 4 * N) {  // mu = C^{-1} u
                         R m = R(0);
 #pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; ++f2) m = fma(creg[f2], u4[f2], m);
-                        mu4[lane] = m;
+                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                            const VT cv = *reinterpret_cast<const VT *>(Ci + c * G::r4(4 * N) + f2);
+                            const VT uv = *reinterpret_cast<const VT *>(u4 + f2);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i)
+                                if (f2 + i < 4 * N) m = fma(VV::at(cv, i), VV::at(uv, i), m);
+                        }
+                        mu4[c] = m;
                     }
                     group_sync(bar_id, G::GS);
                     // t - E0^T mu at particle (a, b)
@@ -846,23 +906,32 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
                     }
                     publish_maxima(it, d, q);
                 }
-                if (conv) {
+                qf[cc] = q;
+                all = all && conv;
+                }
+                if (all) {
                     done = true;
-                    if (real) {
-                        if constexpr (kPair) {
-                            float hi, lo;
-                            two_sum2d(ch[0], q, hi, lo);
-                            Qg[qoff[0] + c] = make_float2(hi, lo + cl[0]);
-                        } else {
-                            Qg[qoff[0] + c] = ch[0] + q;
+                    if (real)
+#pragma unroll
+                        for (int cc = 0; cc < NCOMP; ++cc) {
+                            if constexpr (kPair) {
+                                float hi, lo;
+                                two_sum2d(ch[cc], qf[cc], hi, lo);
+                                Qg[qoff[cc] + c] = make_float2(hi, lo + cl[cc]);
+                            } else {
+                                Qg[qoff[cc] + c] = ch[cc] + qf[cc];
+                            }
                         }
-                    }
                 }
             }
         }
     }
+    if constexpr (MODE == 1) {  // a group the fast path did not finish goes to the direct solve
+        if (group_active && tig == 0) a.fb[gid] = done ? 0 : 1;
+        if (!done) return;
+    }
     // ---------------------------------------------------------------- direct path
-    if (!done) {
+    if constexpr (MODE != 1) {
     if constexpr (PHASE == 1 && SP == 1) {
         // Phase 1: alpha = V^{-1} phi* by Gauss-Jordan elimination of the
         // square advected-basis matrix V itself, with partial (row) pivoting.
@@ -1374,76 +1443,114 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, min_ctas2d<N, R>()) sl2d_
     if (bad) atomicOr(a.err, 1);
 }
 
+template <int N, typename R, int NCOMP, int MODE>
+size_t smem2d()
+{
+    using G = Geo2D<N, R, NCOMP, MODE == 1>;
+    return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
+}
+
+// One phase over groups [g0, g1): for orders with the fast path, the fast
+// kernel and then the direct kernel for the groups it flagged.
+template <int N, typename R, int NCOMP, bool BATCH>
+cudaError_t launch_phase2d(int phase, unsigned grid, const Step2DArgs &b, const Step2DArgs *args,
+                           const long long *prefix, int ninst, int t, cudaStream_t st, LaunchThrottle *th)
+{
+    using G = Geo2D<N, R, NCOMP>;
+    const unsigned block = unsigned(G::kBlock);
+    auto one = [&](auto kernel, size_t smem) -> cudaError_t {
+        if (th) {
+            const cudaError_t e = th->before();
+            if (e != cudaSuccess) return e;
+        }
+        kernel<<<grid, block, smem, st>>>(b, args, prefix, ninst, t);
+        return th ? th->after(st) : cudaSuccess;
+    };
+    cudaError_t e;
+    if constexpr (G::kFast) {
+        if (phase == 1) {
+            e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, smem2d<N, R, NCOMP, 1>());
+            if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>, smem2d<N, R, NCOMP, 2>());
+        } else {
+            e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, smem2d<N, R, NCOMP, 1>());
+            if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>, smem2d<N, R, NCOMP, 2>());
+        }
+    } else {
+        e = phase == 1 ? one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 0>, smem2d<N, R, NCOMP, 0>())
+                       : one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 0>, smem2d<N, R, NCOMP, 0>());
+    }
+    return e;
+}
+
 template <int N, typename R, int NCOMP = 1>
 cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
 {
     using G = Geo2D<N, R, NCOMP>;
-    const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
     const long long groups = (long long)a.Kx * a.Ky * a.M;
     // a launch covers at most `chunk` groups (a multiple of the groups per CTA)
     const long long chunk =
         a.chunk > 0 ? std::min(groups, (a.chunk + G::GPC - 1) / G::GPC * G::GPC) : groups;
-    const unsigned block = unsigned(G::kBlock);
-    auto k1 = sl2d_step_kernel<N, R, 1, false, NCOMP>;
-    auto k2 = sl2d_step_kernel<N, R, 2, false, NCOMP>;
     Step2DArgs b = a;
     LaunchThrottle *th = a.chunk > 0 ? a.throttle : nullptr;
     for (int t = 0; t < a.nsteps; ++t) {
         for (int phase = 1; phase <= 2; ++phase)  // every group's faces before any remap
             for (long long g0 = 0; g0 < groups; g0 += chunk) {
-                if (th) {
-                    const cudaError_t e = th->before();
-                    if (e != cudaSuccess) return e;
-                }
                 b.g0 = g0;
                 b.g1 = std::min(groups, g0 + chunk);
                 const unsigned grid = unsigned((b.g1 - g0 + G::GPC - 1) / G::GPC);
-                if (phase == 1) k1<<<grid, block, smem, st>>>(b, nullptr, nullptr, 0, t);
-                else k2<<<grid, block, smem, st>>>(b, nullptr, nullptr, 0, t);
-                if (th) {
-                    const cudaError_t e = th->after(st);
-                    if (e != cudaSuccess) return e;
-                }
+                const cudaError_t e = launch_phase2d<N, R, NCOMP, false>(phase, grid, b, nullptr, nullptr, 0, t, st, th);
+                if (e != cudaSuccess) return e;
             }
     }
     return cudaGetLastError();
 }
 
-// Prepares the two single-instance kernels of one order for two fields.
+template <int N, typename R, int NCOMP, bool BATCH>
+cudaError_t preload_phases2d()
+{
+    using G = Geo2D<N, R, NCOMP>;
+    cudaError_t e = cudaSuccess;
+    if constexpr (G::kFast) {
+        for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>,
+                       sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>})
+            if (e == cudaSuccess) e = prepare_kernel(k);
+    } else {
+        for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 0>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 0>})
+            if (e == cudaSuccess) e = prepare_kernel(k);
+    }
+    return e;
+}
+
+// Prepares the single-instance kernels of one order for two fields.
 template <int N, typename R>
 cudaError_t preload_step2d_c2_n()
 {
-    cudaError_t e = prepare_kernel(sl2d_step_kernel<N, R, 1, false, 2>);
-    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, false, 2>);
-    return e;
+    return preload_phases2d<N, R, 2, false>();
 }
 
-// Prepares the four kernels of one order (two phases, single and batched).
+// Prepares the kernels of one order (both phases, single and batched).
 template <int N, typename R>
 cudaError_t preload_step2d_n()
 {
-    cudaError_t e = prepare_kernel(sl2d_step_kernel<N, R, 1, false>);
-    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, false>);
-    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 1, true>);
-    if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, true>);
+    cudaError_t e = preload_phases2d<N, R, 1, false>();
+    if (e == cudaSuccess) e = preload_phases2d<N, R, 1, true>();
     return e;
 }
 
-// All instances of one order N, `nsteps` steps: two launches per step.
+// All instances of one order N, `nsteps` steps: per step both phases, each
+// one launch (two with the fast path) over every instance's groups.
 template <int N, typename R>
 cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
 {
     using G = Geo2D<N, R>;
-    const size_t smem = sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
     const unsigned grid = unsigned((b.total_groups + G::GPC - 1) / G::GPC);
-    const unsigned block = unsigned(G::kBlock);
-    auto k1 = sl2d_step_kernel<N, R, 1, true>;
-    auto k2 = sl2d_step_kernel<N, R, 2, true>;
     Step2DArgs none = {};
-    for (int t = 0; t < b.nsteps; ++t) {
-        k1<<<grid, block, smem, st>>>(none, b.args, b.prefix, b.ninst, t);
-        k2<<<grid, block, smem, st>>>(none, b.args, b.prefix, b.ninst, t);
-    }
+    for (int t = 0; t < b.nsteps; ++t)
+        for (int phase = 1; phase <= 2; ++phase) {
+            const cudaError_t e = launch_phase2d<N, R, 1, true>(phase, grid, none, b.args, b.prefix, b.ninst, t, st,
+                                                                nullptr);
+            if (e != cudaSuccess) return e;
+        }
     return cudaGetLastError();
 }
 

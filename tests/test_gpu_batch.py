@@ -118,3 +118,16 @@ def test_batch_moments_match_oracle(sl, orc):
             ref = orc.run(I.with_(pb, steps=5), nthreads=8)
             rm = ref["sum"] / pb["M"]
             assert np.abs(mean - rm).max() / np.abs(rm).max() <= 1e-10
+
+
+def test_parallel_branches_equal_alone(sl, orc):
+    # order classes spread over the tuned number of parallel graph branches:
+    # every instance still equals its solo run bit for bit
+    pbs = _mix2d(orc) + _mix1d(orc)
+    with sl.Batch(pbs, "fp32") as b:
+        assert b.lanes() == 1
+        ms = b.tune(probe_steps=1)
+        assert ms > 0 and b.lanes() in (1, 2, 4)
+        b.step(3)
+        for i, pb in enumerate(pbs):
+            assert np.array_equal(b.samples(i), _alone(sl, pb, "fp32", 3)), i

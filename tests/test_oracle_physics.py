@@ -194,6 +194,29 @@ def test_amplification_at_the_bound(orc):
     assert g_half < 10.0
 
 
+def test_2d_amplification_at_the_bound(orc):
+    # 2D, N=8, elements of config 3's size (h = 1/64) on an 8x8 periodic
+    # patch, constant drift 2.2 per direction and D = 0.0065: at the
+    # Eq. (1d_timestep) node-gap bound a perturbation of the state grows
+    # about a hundredfold every ten steps (x5e4 in 30 steps); at a tenth of
+    # the bound it stays within a few times.  Measured on the oracle alone:
+    # two runs from phi0 and phi0 (1 + 1e-10 noise) with the same increments.
+    def growth(frac, steps):
+        L = 8 / 64.0
+        pb = I.problem(2, (8, 8), (0.0, 0.0), (L, L), 8, 2, steps, 0.0, 7, ("const", [2.2, 2.2]),
+                       ("const", [0.0065]), ("gauss", [1.0, 0.3 * L, 0.5 * L, 0.5 * L]))
+        pb["dt"] = frac * orc.dt_max(pb)
+        E, n = orc.shape(pb)
+        q0 = np.broadcast_to(orc.init_state(pb), (2, E, n)).copy()
+        p0 = q0 * (1 + 1e-10 * np.random.default_rng(0).standard_normal(q0.shape))
+        a = orc.run(pb, ns=2, nthreads=2, state_in=q0, want_states=True, want_sums=False)["states"]
+        b = orc.run(pb, ns=2, nthreads=2, state_in=p0, want_states=True, want_sums=False)["states"]
+        return np.abs(a - b).max() / np.abs(a).max() / 1e-10
+
+    assert growth(1.0, 30) > 1e3
+    assert growth(0.1, 60) < 10.0
+
+
 def _advected_fourier_reference(p, T, nm=256, dt=2e-6):
     """Fourier pseudo-spectral solution of phi_t + (u phi)_x = 0 on periodic
     [0, 2], u = 1 + 0.5 sin(pi x), phi0 the Fourier series of parameters p,
