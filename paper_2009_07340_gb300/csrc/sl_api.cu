@@ -129,6 +129,7 @@ cudaError_t set_coefficients(sl_ctx *c, const sl_field *drift, const sl_field *d
         e = stage_nodal(c, drift, m.dim * V, nif, du);
         if (e == cudaSuccess) e = stage_nodal(c, diffusion, V, nif, dD);
     }
+    ++c->fields_version;  // the 2D advance coefficients are formed again at the next step
     if (e == cudaSuccess)
         e = sl::launch_init_fields(m, du, dD, to_dev(phi0), phi0_nodal_dev, c->xi, c->nodeU, c->nodeB, c->nodeDiv,
                                    c->faceU, c->faceB, write_state ? c->Q : nullptr, c->M * c->ncomp,
@@ -253,6 +254,22 @@ int refresh_bounds(sl_ctx *c)
 
 }  // namespace
 
+namespace sl {
+// The 2D advance coefficients for step size dt, formed on the context's
+// stream when the step size or the fields changed since the last time.
+cudaError_t ensure_coef2d(sl_ctx *c, double dt)
+{
+    if (c->m.dim != 2 || (c->coef2d_dt == dt && c->coef2d_version == c->fields_version)) return cudaSuccess;
+    const cudaError_t e = launch_coef2d(c->nodeU, c->nodeB, c->nodeDiv, (long long)c->m.E * c->m.n, dt,
+                                        4.0 / c->m.h[0], 4.0 / c->m.h[1], c->precision == SL_FP64, c->coef2d, c->st);
+    if (e == cudaSuccess) {
+        c->coef2d_dt = dt;
+        c->coef2d_version = c->fields_version;
+    }
+    return e;
+}
+}  // namespace sl
+
 extern "C" {
 
 int sl_preload(int device)
@@ -311,6 +328,8 @@ void sl_free(sl_ctx *c)
     sl::ctx_free(c, c->err);
     sl::ctx_free(c, c->faces2d);
     sl::ctx_free(c, c->tab2d);
+    sl::ctx_free(c, c->alpha2d);
+    sl::ctx_free(c, c->coef2d);
     sl::ctx_free(c, c->fb2d);
     delete c;
 }
@@ -407,6 +426,8 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
     if (ok && dim == 2)
         ok = sl::ctx_alloc(c, &c->faces2d, size_t(M) * ncomp * m.E * 4 * N * c->state_elem) == cudaSuccess &&
              dalloc(c, &c->tab2d, size_t(N) * N + 5 * N) == cudaSuccess &&
+             sl::ctx_alloc(c, &c->alpha2d, size_t(M) * ncomp * V * (precision == SL_FP64 ? 8 : 4)) == cudaSuccess &&
+             sl::ctx_alloc(c, &c->coef2d, size_t(5) * V * (precision == SL_FP64 ? 8 : 4)) == cudaSuccess &&
              sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fb2d), size_t(M) * m.E) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -637,6 +658,9 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.dW = c->dW;
             a.Q = c->Q;
             a.faces = c->faces2d;
+            a.alpha = c->alpha2d;
+            a.coef = c->coef2d;
+            if (sl::ensure_coef2d(c, dt) != cudaSuccess) return fail_cuda(c);
             a.err = c->err;
             a.chunk = c->launch_chunk;
             a.g0 = a.g1 = 0;

@@ -171,6 +171,8 @@ sl::Step2DArgs args2d(const sl_ctx *c, double dt, int steps)
     a.dW = c->dW;
     a.Q = c->Q;
     a.faces = c->faces2d;
+    a.alpha = c->alpha2d;
+    a.coef = c->coef2d;  // formed for this dt at sl_batch_create
     a.err = c->err;
     a.w = c->bc_weight;
     a.periodic = 1;  // batches hold periodic instances only
@@ -404,6 +406,11 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
             sl_free(c);
             sl_batch_free(b);
             return SL_ERR_DT;
+        }
+        if (sl::ensure_coef2d(c, dt) != cudaSuccess) {
+            sl_free(c);
+            sl_batch_free(b);
+            return SL_ERR_CUDA;
         }
         b->inst.push_back(c);
         b->dt.push_back(dt);

@@ -96,6 +96,8 @@ struct Step2DArgs {
     const double *tab;     // [N N + 5 N] node tables: 4 (xi_i - xi_m), barycentric weights of the
                            // scaled nodes, h_i(0), h_i(1), -4 xi_i, 4 (1 - xi_i)
     unsigned char *fb;     // [M][E]: groups the iterative solve left to the direct one
+    const void *coef;      // [5][E][n] in the kernel's precision: 4 u_x dt / hx, 4 u_y dt / hy,
+                           // 4 b / hx, 4 b / hy (b = sqrt(2 D)), dt du_j/dx_j (launch_coef2d)
     const double *nodeU;   // [2][E][n]
     const double *nodeB;   // [E][n]
     const double *nodeDiv; // [E][n]
@@ -104,6 +106,8 @@ struct Step2DArgs {
     const double *dW;      // [nsteps][M][2]
     void *Q;               // [M][E][n]
     void *faces;           // scratch [M][E][4N] face values of the advected interpolant
+    void *alpha;           // scratch [M][NCOMP][E][n] (FP32 modes: float): phase 1's advected interpolant
+                           // relative to the element reference, phase 2's first iterate
     int *err;
     double w;              // weight of the face rows (1 unless the caller set one)
     int periodic;          // 0: Dirichlet boundaries on all four sides
@@ -150,6 +154,11 @@ cudaError_t launch_step2d_fp64(const Step2DArgs &a, int N, cudaStream_t st);
 cudaError_t launch_step2d_fp32(const Step2DArgs &a, int N, cudaStream_t st);
 // two fields per sample (Q [M][2][E][n], faces [M][2][E][4N]), N <= 8
 cudaError_t launch_step2d_c2(const Step2DArgs &a, int N, bool fp64, cudaStream_t st);
+// The context's 2D advance coefficients for step size dt (once per step size and fields).
+cudaError_t ensure_coef2d(sl_ctx *c, double dt);
+// The 2D advance coefficients of step size dt (Step2DArgs::coef), FP64 or float.
+cudaError_t launch_coef2d(const double *nodeU, const double *nodeB, const double *nodeDiv, long long V, double dt,
+                          double s4x, double s4y, bool fp64, void *out, cudaStream_t st);
 // Host-side node tables of a 2D order (Step2DArgs::tab) from the nodes xi[N].
 void node_tables2d(int N, const double *xi, double *tab);
 cudaError_t launch_init_fields(const Mesh &m, const FieldDev &u, const FieldDev &D, const FieldDev &phi0,
@@ -234,6 +243,10 @@ struct sl_ctx {
     int mom_chunk = 64;
     int *err = nullptr;
     void *faces2d = nullptr;  // 2D face-value scratch
+    void *alpha2d = nullptr;  // 2D: phase 1's interpolant at the nodes (Step2DArgs::alpha)
+    void *coef2d = nullptr;   // 2D: the advance coefficients of one step size (Step2DArgs::coef)
+    double coef2d_dt = 0.0;   // the step size they hold (0: none yet)
+    long long fields_version = 0, coef2d_version = -1;  // fields changed since they were formed?
     double *tab2d = nullptr;  // 2D node tables of the order (Step2DArgs::tab)
     unsigned char *fb2d = nullptr;  // 2D: groups left to the direct solve, [M][E]
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "sl_internal.cuh"
 #include "sl_rng.cuh"
 
@@ -344,10 +346,48 @@ cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_
 // consecutive nodes (one per lane: every warp load is 32 adjacent values,
 // 256 bytes) and one chunk c of `chunk` consecutive samples.  Warp w of the
 // block's kMomWarps sums the chunk's samples s0 + w, s0 + w + kMomWarps, ...
-// in ascending order; the warps' partials are then added in ascending w
-// through shared memory into psum/psq [c][V].  The final pass adds the chunk
-// partials in ascending c.  FP64 throughout.
+// in ascending order; the warps' partials are then added in ascending w in
+// FP64 through shared memory into psum/psq [c][V].  The final pass adds the
+// chunk partials in ascending c in FP64.
+//
+// A warp's own running sums: FP64 for FP64 states.  For float-pair states
+// (value hi + lo) they are float pairs kept exact to about 2^-48 relative by
+// error-free transformations (TwoSum, and the FMA product error), on the
+// FP32 pipe: FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, and an
+// FP64 add and FMA per loaded value made the pass FP64-bound at a ninth of
+// the HBM bandwidth.  Each warp's pair is rounded to FP64 once per chunk.
 constexpr int kMomWarps = 8;
+
+struct PairSum {  // s = hi + lo, |lo| <= ulp(hi) / 2
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float xh, float xl)
+    {
+        const float t = __fadd_rn(hi, xh);
+        const float bb = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(xh, bb));  // TwoSum(hi, xh)
+        const float e = __fadd_rn(err, __fadd_rn(lo, xl));
+        hi = __fadd_rn(t, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, t));  // FastTwoSum(t, e)
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+__device__ __forceinline__ void accumulate(const double *Q, long long i, double &a, double &b, PairSum &, PairSum &)
+{
+    const double x = Q[i];
+    a += x;
+    b = fma(x, x, b);
+}
+__device__ __forceinline__ void accumulate(const float2 *Q, long long i, double &, double &, PairSum &pa, PairSum &pb)
+{
+    const float2 v = Q[i];
+    pa.add(v.x, v.y);
+    // (hi + lo)^2 = hi^2 + 2 hi lo + lo^2: hi^2 exactly as a pair (FMA), the
+    // rest (below 2^-24 of it) in FP32
+    const float p = __fmul_rn(v.x, v.x);
+    const float pe = __fmaf_rn(v.x, v.x, -p);
+    pb.add(p, __fmaf_rn(__fmul_rn(2.f, v.x), v.y, __fmaf_rn(v.y, v.y, pe)));
+}
 
 template <typename State>
 __global__ void __launch_bounds__(32 * kMomWarps) moments_partial_kernel(const State *__restrict__ Q, int M, long long V,
@@ -360,13 +400,14 @@ __global__ void __launch_bounds__(32 * kMomWarps) moments_partial_kernel(const S
     const int c = blockIdx.y;
     const long long s0 = (long long)c * chunk, s1 = min((long long)M, s0 + chunk);
     double a = 0.0, b = 0.0;
+    PairSum pa, pb;
     if (v < V) {
 #pragma unroll 4
-        for (long long s = s0 + w; s < s1; s += kMomWarps) {
-            const double x = load_state(Q, s * V + v);
-            a += x;
-            b = fma(x, x, b);
-        }
+        for (long long s = s0 + w; s < s1; s += kMomWarps) accumulate(Q, s * V + v, a, b, pa, pb);
+    }
+    if constexpr (!std::is_same<State, double>::value) {
+        a = pa.value();
+        b = pb.value();
     }
     sa[w][lane] = a;
     sb[w][lane] = b;
@@ -521,6 +562,36 @@ cudaError_t launch_moments_combine(const double *psum, const double *psq, int nc
     return cudaGetLastError();
 }
 
+// Advance coefficients of the 2D step for step size dt, formed once per
+// step size and field change instead of in every step of every sample: the
+// particle displacement is then one FMA per direction, dx = ax + bx dW, in
+// the kernel's own precision (FP64 arithmetic is 1/64 of the FP32 rate).
+template <typename R>
+__global__ void coef2d_kernel(const double *__restrict__ nodeU, const double *__restrict__ nodeB,
+                              const double *__restrict__ nodeDiv, long long V, double dt, double s4x, double s4y,
+                              R *__restrict__ out)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const double b = nodeB[v];
+    out[v] = R(__dmul_rn(__dmul_rn(nodeU[v], dt), s4x));
+    out[V + v] = R(__dmul_rn(__dmul_rn(nodeU[V + v], dt), s4y));
+    out[2 * V + v] = R(__dmul_rn(b, s4x));
+    out[3 * V + v] = R(__dmul_rn(b, s4y));
+    out[4 * V + v] = R(__dmul_rn(dt, nodeDiv[v]));
+}
+
+cudaError_t launch_coef2d(const double *nodeU, const double *nodeB, const double *nodeDiv, long long V, double dt,
+                          double s4x, double s4y, bool fp64, void *out, cudaStream_t st)
+{
+    const unsigned grid = unsigned((V + 255) / 256);
+    if (fp64)
+        coef2d_kernel<double><<<grid, 256, 0, st>>>(nodeU, nodeB, nodeDiv, V, dt, s4x, s4y, static_cast<double *>(out));
+    else
+        coef2d_kernel<float><<<grid, 256, 0, st>>>(nodeU, nodeB, nodeDiv, V, dt, s4x, s4y, static_cast<float *>(out));
+    return cudaGetLastError();
+}
+
 void node_tables2d(int N, const double *xi, double *tab)
 {
     // the same FP64 expressions, in the same order, as the step kernels used
@@ -555,6 +626,8 @@ cudaError_t preload_setup()
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double>);
     if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
     if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
+    if (e == cudaSuccess) e = prepare_kernel(coef2d_kernel<double>);
+    if (e == cudaSuccess) e = prepare_kernel(coef2d_kernel<float>);
     if (e == cudaSuccess) e = prepare_kernel(reseed_kernel<double>);
     if (e == cudaSuccess) e = prepare_kernel(init_faces_hi_kernel);
     if (e == cudaSuccess) e = prepare_kernel(pdf_kernel<double>);

@@ -290,18 +290,17 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
 #pragma unroll
     for (int cc = 0; cc < NCOMP; ++cc) ph[cc] = R(0);
     if (real_lead) {
-        const long long V = (long long)E * n;
-        const double dWx = a.dW[((long long)t * a.M + s) * 2 + 0];
-        const double dWy = a.dW[((long long)t * a.M + s) * 2 + 1];
-        const double ux = a.nodeU[(long long)e * n + c], uy = a.nodeU[V + (long long)e * n + c];
-        const double b = a.nodeB[(long long)e * n + c];
-        // explicit unfused products: the compiler may not contract these
-        // differently in the batched and single kernels
-        const R dx = R(__dmul_rn(__dadd_rn(__dmul_rn(ux, a.dt), __dmul_rn(b, dWx)), a.s4x));
-        const R dy = R(__dmul_rn(__dadd_rn(__dmul_rn(uy, a.dt), __dmul_rn(b, dWy)), a.s4y));
+        const long long V = (long long)E * n, pe = (long long)e * n + c;
+        const R dWx = R(a.dW[((long long)t * a.M + s) * 2 + 0]);
+        const R dWy = R(a.dW[((long long)t * a.M + s) * 2 + 1]);
+        const R *cf = static_cast<const R *>(a.coef);
+        // displacement dx = 4 (u dt + b dW) / h as one explicit FMA of the
+        // step's coefficients (the same rounding in the batched and single kernels)
+        const R dx = fma(cf[2 * V + pe], dWx, cf[pe]);
+        const R dy = fma(cf[3 * V + pe], dWy, cf[V + pe]);
         dxp = dx;
         dyp = dy;
-        const R gam = R(a.dt * a.nodeDiv[(long long)e * n + c]);
+        const R gam = cf[4 * V + pe];
 #pragma unroll
         for (int cc = 0; cc < NCOMP; ++cc) {
             R dq = qh[cc] - ch[cc];
@@ -656,6 +655,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
                             r = hs[c] - vx;
                         }
                     }
+                    if (conv && real)  // phase 2 starts from it
+                        static_cast<R *>(a.alpha)[(((long long)s * NCOMP + cc) * E + e) * n + c] = x;
                     all = all && conv;
                 }
                 done = all;
@@ -752,7 +753,8 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
                 R *vec = gvec + cc * P4, *res = gres + cc * P4;
                 const R *rhs = grhs + cc * P4;
                 cref = R(fabs(double(ch[cc])));
-                R q = R(0);
+                // phase 1's interpolant: the remap differs from it only by the face correction
+                R q = real ? static_cast<const R *>(a.alpha)[(((long long)s * NCOMP + cc) * E + e) * n + c] : R(0);
                 bool conv = false;
                 for (int it = 0; it <= kFastIters; ++it) {
                     if (c < n) vec[c] = q;
@@ -1108,7 +1110,11 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
         // face values of the advected interpolant (alpha - c = x, node-indexed) at the 4N face points
 #pragma unroll
         for (int cc = 0; cc < NCOMP; ++cc)
-            if (has) vec[cc * P4 + mypiv] = x[cc];
+            if (has) {
+                vec[cc * P4 + mypiv] = x[cc];
+                if constexpr (MODE == 2)  // the fast phase 2 starts from it
+                    static_cast<R *>(a.alpha)[(((long long)s * NCOMP + cc) * E + e) * n + mypiv] = x[cc];
+            }
         group_sync(bar_id, G::GS);
     } else {
         // Gram row c: G[c][c'] = sum_p S[p][c] S[p][c'], b_c = sum_p S[p][c] rhs_p
