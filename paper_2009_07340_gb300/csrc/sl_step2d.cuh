@@ -483,7 +483,10 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
     if constexpr (G::kFast && MODE == 1) {
         constexpr int NW = G::GS / 32;
         constexpr int NT = G::r4(n), R4N = G::r4(N);
-        constexpr float kFastCond = 64.0f;
+        // largest ||Wx|| ||Wy|| tried: in a model of config-3 elements every
+        // case converged below these in the given iteration count (FP32 phase 2
+        // stops converging first)
+        constexpr float kFastCond = kPair ? (PHASE == 1 ? 512.0f : 160.0f) : 4096.0f;
         constexpr int kFastIters = kPair ? 8 : 16;
         const float kFastTol = kPair ? 1e-6f : 1e-13f;
         R *hxT = Vs + n * HXS;          // [N][NT]: hx_p[i] at [i][p]
@@ -718,23 +721,35 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
                             creg[f2] = f2 == f ? v + wi2 : v;
                         }
                     }
+                    // step k: the pivot lane scales its row by 1 / C[k][k] (the pivot
+                    // entry becomes that reciprocal) and publishes it; every other row
+                    // subtracts its entry k times the published row, and its entry k
+                    // becomes minus that product
 #pragma unroll
                     for (int k = 0; k < 4 * N; ++k) {
                         R *pr = prow + (k & 1) * G::r4(4 * N + 4);
-                        if (lane == k)
+                        if (lane == k) {
+                            const R pinv = R(1) / creg[k];
 #pragma unroll
-                            for (int f2 = 0; f2 < 4 * N; ++f2) pr[f2] = creg[f2];
+                            for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
+#pragma unroll
+                            for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                                R v4[4];
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
+                                *reinterpret_cast<VT *>(pr + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                            }
+                        }
                         __syncwarp();
-                        if (lane < 4 * N) {
-                            const R pinv = R(1) / pr[k];
-                            if (lane == k) {
+                        if (lane < 4 * N && lane != k) {
+                            const R l = creg[k];
 #pragma unroll
-                                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
-                            } else {
-                                const R l = creg[k];
+                            for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                                const VT v = *reinterpret_cast<const VT *>(pr + f2);
 #pragma unroll
-                                for (int f2 = 0; f2 < 4 * N; ++f2)
-                                    creg[f2] = f2 == k ? -l * pinv : fma(-l, pr[f2] * pinv, creg[f2]);
+                                for (int i = 0; i < VW; ++i)
+                                    if (f2 + i < 4 * N)
+                                        creg[f2 + i] = f2 + i == k ? -l * VV::at(v, i) : fma(-l, VV::at(v, i), creg[f2 + i]);
                             }
                         }
                     }
