@@ -271,7 +271,11 @@ int sl_pdf(sl_ctx *c, int nbins, double lo, double hi, unsigned int *counts);
 int sl_pdf_device(sl_ctx *c, int nbins, double lo, double hi, unsigned int *d_counts);
 
 /* Largest dt satisfying |u|max dt + sqrt(2 Dmax dt) <= dx_min in every      */
-/* direction (Eq. 1d_timestep), dx_min = smallest node gap times h.          */
+/* direction (Eq. 1d_timestep), dx_min = smallest node gap times h.  In 2D   */
+/* the step is not stable at this bound: a perturbation of the state grows  */
+/* ~12 % per step there on 64x64 elements of N = 8 (measured on an FP64     */
+/* reference); half of it is stable for a rotating drift, and a strong      */
+/* uniform drift needs a quarter or less.  2D workloads take a fraction.    */
 int sl_dt_max(const sl_ctx *c, double *dt);
 
 /* The same bound with dx_min = the first Gauss node's distance to the       */
