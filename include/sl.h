@@ -290,6 +290,15 @@ int sl_dt_edge(const sl_ctx *c, double *dt);
 /* Step counter (number of SL steps taken so far). */
 int sl_step_count(const sl_ctx *c, long long *n);
 
+/* 2D: how many element-sample groups the iterative (tensor-preconditioned)  */
+/* solve handed to the direct solve since the context was created, per      */
+/* phase: phase 1 = the interpolant's face values (Eq. remap_bnd), phase 2 = */
+/* the constrained remap.  A group goes there when its conditioning test    */
+/* fails or the iteration has not converged within its limit; the result   */
+/* is the same solution either way.  Either pointer may be NULL.  1D        */
+/* contexts report 0.  Synchronises; SL_ERR_ARG for a NULL context.         */
+int sl_fallback_count(sl_ctx *c, long long *phase1, long long *phase2);
+
 /* Copies samples [s0, s0+count) of the state to host memory, FP64,          */
 /* [count][elements][N^dim].  Synchronises.                                   */
 int sl_get_samples(sl_ctx *c, int s0, int count, double *out);

@@ -22,6 +22,7 @@ from . import build as _build
 __all__ = ["SL_FP64", "SL_MIXED", "SL_FP32", "SLError", "Solver", "lib", "sl_init", "sl_step",
            "sl_moments", "sl_moments_device", "sl_dt_max", "sl_step_count", "sl_get_samples",
            "sl_set_samples", "sl_set_step_count", "sl_wiener", "sl_dt_edge", "sl_profile", "sl_profile_read",
+           "sl_fallback_count",
            "sl_moments_static", "sl_moments_partial", "sl_moment_chunk", "sl_moments_combine", "sl_free",
            "sl_strerror"]
 
@@ -102,6 +103,7 @@ def lib():
         L.sl_dt_max.argtypes = [vp, _dp]
         L.sl_dt_edge.argtypes = [vp, _dp]
         L.sl_step_count.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.sl_fallback_count.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.sl_set_step_count.argtypes = [vp, C.c_longlong]
         L.sl_get_samples.argtypes = [vp, C.c_int, C.c_int, _dp]
         L.sl_set_samples.argtypes = [vp, C.c_int, C.c_int, _dp]
@@ -268,6 +270,14 @@ def sl_step_count(ctx):
     v = C.c_longlong()
     _check(lib().sl_step_count(C.c_void_p(ctx), C.byref(v)), "sl_step_count")
     return v.value
+
+
+def sl_fallback_count(ctx):
+    """(phase 1, phase 2) element-sample groups the 2D iterative solve handed
+    to the direct one since the context was created."""
+    a, b = C.c_longlong(), C.c_longlong()
+    _check(lib().sl_fallback_count(C.c_void_p(ctx), C.byref(a), C.byref(b)), "sl_fallback_count")
+    return a.value, b.value
 
 
 def sl_set_step_count(ctx, n):
@@ -633,6 +643,11 @@ class Solver:
     @step_count.setter
     def step_count(self, n):
         sl_set_step_count(self.ctx, n)
+
+    @property
+    def fallbacks(self):
+        """(phase 1, phase 2) groups the 2D fast path left to the direct solve."""
+        return sl_fallback_count(self.ctx)
 
     def close(self):
         if self.ctx:

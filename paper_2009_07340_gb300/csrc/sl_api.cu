@@ -331,6 +331,7 @@ void sl_free(sl_ctx *c)
     sl::ctx_free(c, c->alpha2d);
     sl::ctx_free(c, c->coef2d);
     sl::ctx_free(c, c->fb2d);
+    sl::ctx_free(c, c->fbcount2d);
     delete c;
 }
 
@@ -428,7 +429,10 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
              dalloc(c, &c->tab2d, size_t(N) * N + 5 * N) == cudaSuccess &&
              sl::ctx_alloc(c, &c->alpha2d, size_t(M) * ncomp * V * (precision == SL_FP64 ? 8 : 4)) == cudaSuccess &&
              sl::ctx_alloc(c, &c->coef2d, size_t(5) * V * (precision == SL_FP64 ? 8 : 4)) == cudaSuccess &&
-             sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fb2d), size_t(M) * m.E) == cudaSuccess;
+             sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fb2d), size_t(M) * m.E) == cudaSuccess &&
+             sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fbcount2d), 2 * sizeof(unsigned long long)) ==
+                 cudaSuccess &&
+             cudaMemsetAsync(c->fbcount2d, 0, 2 * sizeof(unsigned long long), c->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         sl_free(c);
@@ -519,6 +523,19 @@ int sl_step_count(const sl_ctx *c, long long *n)
 {
     if (!c || !n) return SL_ERR_ARG;
     *n = c->step;
+    return SL_OK;
+}
+
+int sl_fallback_count(sl_ctx *c, long long *phase1, long long *phase2)
+{
+    if (!c) return SL_ERR_ARG;
+    if (c->poisoned) return SL_ERR_STATE;
+    unsigned long long h[2] = {0, 0};
+    if (c->fbcount2d && (cudaMemcpyAsync(h, c->fbcount2d, sizeof(h), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+                         cudaStreamSynchronize(c->st) != cudaSuccess))
+        return fail_cuda(c);
+    if (phase1) *phase1 = (long long)h[0];
+    if (phase2) *phase2 = (long long)h[1];
     return SL_OK;
 }
 
@@ -650,6 +667,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.xi = c->xi;
             a.tab = c->tab2d;
             a.fb = c->fb2d;
+            a.fbcount = c->fbcount2d;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
             a.nodeDiv = c->nodeDiv;

@@ -96,6 +96,7 @@ struct Step2DArgs {
     const double *tab;     // [N N + 5 N] node tables: 4 (xi_i - xi_m), barycentric weights of the
                            // scaled nodes, h_i(0), h_i(1), -4 xi_i, 4 (1 - xi_i)
     unsigned char *fb;     // [M][E]: groups the iterative solve left to the direct one
+    unsigned long long *fbcount = nullptr;  // [2]: per phase, groups so left, cumulative (may be null)
     const void *coef;      // [5][E][n] in the kernel's precision: 4 u_x dt / hx, 4 u_y dt / hy,
                            // 4 b / hx, 4 b / hy (b = sqrt(2 D)), dt du_j/dx_j (launch_coef2d)
     const double *nodeU;   // [2][E][n]
@@ -249,6 +250,7 @@ struct sl_ctx {
     long long fields_version = 0, coef2d_version = -1;  // fields changed since they were formed?
     double *tab2d = nullptr;  // 2D node tables of the order (Step2DArgs::tab)
     unsigned char *fb2d = nullptr;  // 2D: groups left to the direct solve, [M][E]
+    unsigned long long *fbcount2d = nullptr;  // 2D: their cumulative count per phase [2]
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
     double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)

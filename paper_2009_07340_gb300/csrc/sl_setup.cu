@@ -2,6 +2,7 @@
 // fields at the nodes and faces, the initial state (Section 5.1), the Wiener
 // increments (Section 5.2) and the sample moments (Section 5.4).
 #include <cmath>
+#include <cstdint>
 
 #include <algorithm>
 
@@ -342,21 +343,26 @@ cudaError_t launch_advance_counters(long long *steps, int n, int by, cudaStream_
     return cudaGetLastError();
 }
 
-// Moments, Eq. (averaged), in a fixed summation order.  A block owns 32
-// consecutive nodes (one per lane: every warp load is 32 adjacent values,
-// 256 bytes) and one chunk c of `chunk` consecutive samples.  Warp w of the
-// block's kMomWarps sums the chunk's samples s0 + w, s0 + w + kMomWarps, ...
-// in ascending order; the warps' partials are then added in ascending w in
-// FP64 through shared memory into psum/psq [c][V].  The final pass adds the
-// chunk partials in ascending c in FP64.
+// Moments, Eq. (averaged), in a fixed summation order.  A warp owns
+// kMomVL x W consecutive values (W = 2 when V is even and the state is
+// 16-byte aligned: one 16-byte load per value lane) and chunk c = blockIdx.y
+// of `chunk` consecutive samples.  Its lanes form kMomSL sample lanes of
+// kMomVL value lanes: sample lane j adds samples s0 + j, s0 + j + kMomSL,
+// ... in ascending order (each warp load reads kMomSL rows of 128
+// contiguous bytes), and the sample lanes' sums are then added by a
+// butterfly of warp shuffles (lanes j and j ^ 1, then j ^ 2), which lands
+// the same bits in every lane.  psum/psq [c][V] receive the chunk sums; the
+// final pass adds them in ascending c in FP64.
 //
-// A warp's own running sums: FP64 for FP64 states.  For float-pair states
-// (value hi + lo) they are float pairs kept exact to about 2^-48 relative by
-// error-free transformations (TwoSum, and the FMA product error), on the
-// FP32 pipe: FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, and an
-// FP64 add and FMA per loaded value made the pass FP64-bound at a ninth of
-// the HBM bandwidth.  Each warp's pair is rounded to FP64 once per chunk.
-constexpr int kMomWarps = 8;
+// Running sums: FP64 for FP64 states.  For float-pair states (value hi +
+// lo) float pairs kept exact to about 2^-48 relative by error-free
+// transformations (TwoSum, and the FMA product error), on the FP32 pipe:
+// FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, and FP64 adds per
+// loaded value made the pass FP64-bound.  The pairs are rounded to FP64
+// once per chunk.
+constexpr int kMomThreads = 128;
+constexpr int kMomSL = 4;            // sample lanes per warp
+constexpr int kMomVL = 32 / kMomSL;  // value lanes per warp
 
 struct PairSum {  // s = hi + lo, |lo| <= ulp(hi) / 2
     float hi = 0.f, lo = 0.f;
@@ -369,45 +375,132 @@ struct PairSum {  // s = hi + lo, |lo| <= ulp(hi) / 2
         hi = __fadd_rn(t, e);
         lo = __fsub_rn(e, __fsub_rn(hi, t));  // FastTwoSum(t, e)
     }
+    // x = xh + xl squared: xh^2 exactly as a pair (FMA), the rest (below
+    // 2^-24 of it) in FP32
+    __device__ __forceinline__ void add_square(float xh, float xl)
+    {
+        const float p = __fmul_rn(xh, xh);
+        const float pe = __fmaf_rn(xh, xh, -p);
+        add(p, __fmaf_rn(__fadd_rn(xh, xh), xl, __fmaf_rn(xl, xl, pe)));
+    }
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
-__device__ __forceinline__ void accumulate(const double *Q, long long i, double &a, double &b, PairSum &, PairSum &)
+template <typename State, int W>
+struct MomLoad;
+template <>
+struct MomLoad<double, 1> {
+    using T = double;
+    __device__ static void get(const T &v, double *x) { x[0] = v; }
+};
+template <>
+struct MomLoad<double, 2> {
+    using T = double2;
+    __device__ static void get(const T &v, double *x) { x[0] = v.x, x[1] = v.y; }
+};
+template <>
+struct MomLoad<float2, 1> {
+    using T = float2;
+    __device__ static void get(const T &v, float *h, float *l) { h[0] = v.x, l[0] = v.y; }
+};
+template <>
+struct MomLoad<float2, 2> {
+    using T = float4;
+    __device__ static void get(const T &v, float *h, float *l) { h[0] = v.x, l[0] = v.y, h[1] = v.z, l[1] = v.w; }
+};
+
+template <typename State, int W>
+__global__ void __launch_bounds__(kMomThreads) moments_partial_kernel(const State *__restrict__ Q, int M, long long V,
+                                                                      int chunk, double *__restrict__ psum,
+                                                                      double *__restrict__ psq)
 {
-    const double x = Q[i];
-    a += x;
-    b = fma(x, x, b);
-}
-__device__ __forceinline__ void accumulate(const float2 *Q, long long i, double &, double &, PairSum &pa, PairSum &pb)
-{
-    const float2 v = Q[i];
-    pa.add(v.x, v.y);
-    // (hi + lo)^2 = hi^2 + 2 hi lo + lo^2: hi^2 exactly as a pair (FMA), the
-    // rest (below 2^-24 of it) in FP32
-    const float p = __fmul_rn(v.x, v.x);
-    const float pe = __fmaf_rn(v.x, v.x, -p);
-    pb.add(p, __fmaf_rn(__fmul_rn(2.f, v.x), v.y, __fmaf_rn(v.y, v.y, pe)));
+    using L = MomLoad<State, W>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = lane / kMomVL, i = lane % kMomVL;  // sample lane, value lane
+    const long long v0 = (((long long)blockIdx.x * (kMomThreads / 32) + warp) * kMomVL + i) * W;
+    const bool live = v0 < V;  // W = 2 only for even V: a live lane's pair lies inside [0, V)
+    const int c = blockIdx.y;
+    const long long s0 = (long long)c * chunk + j, s1 = min((long long)M, (long long)c * chunk + chunk);
+    const typename L::T *q = reinterpret_cast<const typename L::T *>(Q + (live ? v0 : 0));
+    const long long stride = V / W;  // one sample, in loads
+    double a[W], b[W];
+    if constexpr (std::is_same<State, double>::value) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) a[k] = b[k] = 0.0;
+        if (live) {
+#pragma unroll 4
+            for (long long s = s0; s < s1; s += kMomSL) {
+                double x[W];
+                L::get(q[s * stride], x);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    a[k] += x[k];
+                    b[k] = fma(x[k], x[k], b[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = kMomVL; off < 32; off <<= 1)
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+                b[k] += __shfl_xor_sync(0xffffffffu, b[k], off);
+            }
+    } else {
+        PairSum pa[W], pb[W];
+        if (live) {
+#pragma unroll 4
+            for (long long s = s0; s < s1; s += kMomSL) {
+                float h[W], l[W];
+                L::get(q[s * stride], h, l);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    pa[k].add(h[k], l[k]);
+                    pb[k].add_square(h[k], l[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = kMomVL; off < 32; off <<= 1)
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const float ah = __shfl_xor_sync(0xffffffffu, pa[k].hi, off);
+                const float al = __shfl_xor_sync(0xffffffffu, pa[k].lo, off);
+                const float bh = __shfl_xor_sync(0xffffffffu, pb[k].hi, off);
+                const float bl = __shfl_xor_sync(0xffffffffu, pb[k].lo, off);
+                pa[k].add(ah, al);
+                pb[k].add(bh, bl);
+            }
+#pragma unroll
+        for (int k = 0; k < W; ++k) a[k] = pa[k].value(), b[k] = pb[k].value();
+    }
+    if (live && j == 0)
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            psum[(long long)c * V + v0 + k] = a[k];
+            psq[(long long)c * V + v0 + k] = b[k];
+        }
 }
 
-template <typename State>
-__global__ void __launch_bounds__(32 * kMomWarps) moments_partial_kernel(const State *__restrict__ Q, int M, long long V,
-                                                                         int chunk, double *__restrict__ psum,
-                                                                         double *__restrict__ psq)
+// The final pass: a block owns 32 consecutive values (one per lane) and its
+// kFinWarps warps split the chunks, warp w adding chunks w, w + kFinWarps,
+// ... in ascending order; warp 0 then adds the warps' sums in ascending w.
+constexpr int kFinWarps = 8;
+
+__global__ void __launch_bounds__(32 * kFinWarps)
+    moments_final_kernel(const double *__restrict__ psum, const double *__restrict__ psq, int nc, long long V,
+                         double M, double *__restrict__ mean, double *__restrict__ m2)
 {
-    __shared__ double sa[kMomWarps][32], sb[kMomWarps][32];
+    __shared__ double sa[kFinWarps][32], sb[kFinWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long v = (long long)blockIdx.x * 32 + lane;
-    const int c = blockIdx.y;
-    const long long s0 = (long long)c * chunk, s1 = min((long long)M, s0 + chunk);
     double a = 0.0, b = 0.0;
-    PairSum pa, pb;
     if (v < V) {
 #pragma unroll 4
-        for (long long s = s0 + w; s < s1; s += kMomWarps) accumulate(Q, s * V + v, a, b, pa, pb);
-    }
-    if constexpr (!std::is_same<State, double>::value) {
-        a = pa.value();
-        b = pb.value();
+        for (int c = w; c < nc; c += kFinWarps) {
+            a += psum[(long long)c * V + v];
+            b += psq[(long long)c * V + v];
+        }
     }
     sa[w][lane] = a;
     sb[w][lane] = b;
@@ -415,27 +508,13 @@ __global__ void __launch_bounds__(32 * kMomWarps) moments_partial_kernel(const S
     if (w == 0 && v < V) {
         double ta = sa[0][lane], tb = sb[0][lane];
 #pragma unroll
-        for (int k = 1; k < kMomWarps; ++k) {
+        for (int k = 1; k < kFinWarps; ++k) {
             ta += sa[k][lane];
             tb += sb[k][lane];
         }
-        psum[(long long)c * V + v] = ta;
-        psq[(long long)c * V + v] = tb;
+        mean[v] = ta / M;
+        if (m2) m2[v] = tb / M;
     }
-}
-
-__global__ void moments_final_kernel(const double *__restrict__ psum, const double *__restrict__ psq, int nc,
-                                     long long V, double M, double *__restrict__ mean, double *__restrict__ m2)
-{
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    double a = 0.0, b = 0.0;
-    for (int c = 0; c < nc; ++c) {
-        a += psum[(long long)c * V + v];
-        b += psq[(long long)c * V + v];
-    }
-    mean[v] = a / M;
-    if (m2) m2[v] = b / M;
 }
 
 // 2D faces on the upper domain boundaries (used with Dirichlet boundaries):
@@ -533,33 +612,36 @@ cudaError_t launch_moment_partials(const void *Q, int state_is_double, int M, lo
 {
     const int nc = (M + chunk - 1) / chunk;
     if (nc > 65535) return cudaErrorInvalidValue;  // chunks are the grid's y dimension
-    dim3 g1(unsigned((V + 31) / 32), unsigned(nc));
-    if (state_is_double)
-        moments_partial_kernel<double><<<g1, 32 * kMomWarps, 0, st>>>(static_cast<const double *>(Q), M, V, chunk,
-                                                                      psum, psq);
-    else
-        moments_partial_kernel<float2><<<g1, 32 * kMomWarps, 0, st>>>(static_cast<const float2 *>(Q), M, V, chunk,
-                                                                      psum, psq);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
-                           double *psq, double *mean, double *m2, cudaStream_t st)
-{
-    const int tb = 256;
-    const int nc = (M + chunk - 1) / chunk;
-    cudaError_t e = launch_moment_partials(Q, state_is_double, M, V, chunk, psum, psq, st);
-    if (e != cudaSuccess) return e;
-    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, double(M), mean, m2);
+    // two values per thread where V is even and the state starts on a
+    // 16-byte boundary (then every sample row does: 16-byte loads)
+    const bool two = V % 2 == 0 && reinterpret_cast<uintptr_t>(Q) % 16 == 0;
+    const long long per_block = (kMomThreads / 32) * kMomVL * (two ? 2 : 1);  // values per block
+    const dim3 g1(unsigned((V + per_block - 1) / per_block), unsigned(nc));
+    if (state_is_double) {
+        const double *q = static_cast<const double *>(Q);
+        if (two) moments_partial_kernel<double, 2><<<g1, kMomThreads, 0, st>>>(q, M, V, chunk, psum, psq);
+        else moments_partial_kernel<double, 1><<<g1, kMomThreads, 0, st>>>(q, M, V, chunk, psum, psq);
+    } else {
+        const float2 *q = static_cast<const float2 *>(Q);
+        if (two) moments_partial_kernel<float2, 2><<<g1, kMomThreads, 0, st>>>(q, M, V, chunk, psum, psq);
+        else moments_partial_kernel<float2, 1><<<g1, kMomThreads, 0, st>>>(q, M, V, chunk, psum, psq);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments_combine(const double *psum, const double *psq, int nc, long long V, long long M,
                                    double *mean, double *m2, cudaStream_t st)
 {
-    const int tb = 256;
-    moments_final_kernel<<<unsigned((V + tb - 1) / tb), tb, 0, st>>>(psum, psq, nc, V, double(M), mean, m2);
+    moments_final_kernel<<<unsigned((V + 31) / 32), 32 * kFinWarps, 0, st>>>(psum, psq, nc, V, double(M), mean, m2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const void *Q, int state_is_double, int M, long long V, int chunk, double *psum,
+                           double *psq, double *mean, double *m2, cudaStream_t st)
+{
+    const int nc = (M + chunk - 1) / chunk;
+    const cudaError_t e = launch_moment_partials(Q, state_is_double, M, V, chunk, psum, psq, st);
+    return e != cudaSuccess ? e : launch_moments_combine(psum, psq, nc, V, M, mean, m2, st);
 }
 
 // Advance coefficients of the 2D step for step size dt, formed once per
@@ -623,8 +705,10 @@ cudaError_t preload_setup()
     if (e == cudaSuccess) e = prepare_kernel(wiener_kernel);
     if (e == cudaSuccess) e = prepare_kernel(wiener_batch_kernel);
     if (e == cudaSuccess) e = prepare_kernel(advance_counters_kernel);
-    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double>);
-    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double, 1>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<double, 2>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2, 1>);
+    if (e == cudaSuccess) e = prepare_kernel(moments_partial_kernel<float2, 2>);
     if (e == cudaSuccess) e = prepare_kernel(moments_final_kernel);
     if (e == cudaSuccess) e = prepare_kernel(coef2d_kernel<double>);
     if (e == cudaSuccess) e = prepare_kernel(coef2d_kernel<float>);

@@ -13,20 +13,26 @@
 //            face values B alpha at the 4N face points  (Eq. remap_bnd);
 //   phase 2: upwind face values g (Eq. bnd_update) and
 //            q = argmin |V q - phi*|^2 + |B q - g|^2     (Section 5.3).
-// The two phases are two launches per step: phase 2 of an element needs its
-// neighbours' phase-1 face values.
+// The two phases are two launches each per step: phase 2 of an element needs
+// its neighbours' phase-1 face values.
 //
-// Mapping: a group of n threads (rounded up to a warp multiple, its own named
-// barrier) per element-sample; thread p owns particle p.  Rows of the stacked
-// system [V; B] (B only in phase 2) are staged in shared memory; thread c
-// builds row c of the Gram matrix G = [V;B]^T [V;B] in registers and the
-// group solves G x = [V;B]^T rhs by Gauss-Jordan elimination without
-// pivoting (G is SPD), one broadcast pivot row per step.  Everything is
-// relative to the element reference value c (the middle node's state):
-// [V;B] 1 = 1 (partition of unity), so the unknown is q - c.  The FP32 mode
-// keeps the state and face values as float pairs (as in 1D) and applies one
-// step of iterative refinement of the stacked least-squares residual against
-// the original rows, replaying the stored elimination multipliers.
+// Mapping: a group of threads (its own named barrier) per element-sample;
+// thread p owns particle p.  Everything is relative to the element reference
+// value c (the middle node's state): [V;B] 1 = 1 (partition of unity), so the
+// unknown is q - c.  The FP32 mode keeps the state and face values as float
+// pairs (as in 1D).  Each phase runs two kernels:
+//  - the fast kernel (MODE 1, one thread per node, every order): the
+//    iteration preconditioned by the tensor product V0 = Vy (x) Vx of two 1D
+//    advected bases (the particle rows' and columns' mean positions), in
+//    phase 2 with the face rows through the 4N x 4N capacitance matrix.  A
+//    group whose conditioning test fails, or which has not converged within
+//    its iteration limit, is flagged for
+//  - the direct kernel (MODE 2, the flagged groups only; SP lanes per row):
+//    phase 1 by Gauss-Jordan elimination of V with partial pivoting (orders
+//    with one lane per row) or of the Gram matrix V^T V; phase 2 by the Gram
+//    matrix G = [V;B]^T [V;B], Gauss-Jordan without pivoting (G is SPD), and
+//    in FP32 one step of iterative refinement of the stacked least-squares
+//    residual against the original rows.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -99,7 +105,8 @@ constexpr int split2d()
 template <int N, typename R, int NCOMP = 1, bool FASTONLY = false>
 struct Geo2D {
     static constexpr int n = N * N;
-    static constexpr int SP = split2d<N, R>();                  // lanes per row
+    // lanes per row (the fast-path kernel holds no rows: one thread per node)
+    static constexpr int SP = FASTONLY ? 1 : split2d<N, R>();
     static constexpr int VWg = sizeof(R) == 4 ? 4 : 2;          // values per 16 bytes
     // columns per lane (SP > 1), widened by one 16-byte vector where a lane's
     // block would span a multiple of 128 bytes: the lanes of a row then read
@@ -114,20 +121,19 @@ struct Geo2D {
     // per-group shared memory (elements of R)
     static constexpr int P4 = (P + 3) & ~3;                     // P rounded to 16-byte multiples
     static constexpr int HXS = (2 * N + 3) & ~3;                // stride of the particles' basis-value table
-    // the tensor-preconditioned fast path (one lane per row, N <= 8, one field)
-    static constexpr bool kFast = SP == 1 && N <= 8 && NCOMP <= 2;
+    // the order has the tensor-preconditioned fast path (one or two fields)
+    static constexpr bool kFast = N <= 12 && NCOMP <= 2;
     __host__ __device__ static constexpr int r4(int v) { return (v + 3) & ~3; }
     // its buffers after the basis-value table: hxT, hyT [N][n]; Wx, WxT, Wy, WyT [N][N];
     // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [n]; u4, mu4 [4N]; two pivot rows [4N + 4];
     // convergence slots [2][GS / 32][2]
-    static constexpr int kFastBuf = kFast ? 2 * N * r4(n) + 4 * r4(N * N) + 6 * r4(N) + 2 * r4(n) + 2 * r4(4 * N) +
-                                                2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1) + 4 * N * r4(4 * N)
-                                          : 0;
+    static constexpr int kFastBuf = FASTONLY ? 2 * N * r4(n) + 4 * r4(N * N) + 6 * r4(N) + 2 * r4(n) + 2 * r4(4 * N) +
+                                                   2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1) + 4 * N * r4(4 * N)
+                                             : 0;
     // rhs, vec and res hold one P4-long array per field
     static constexpr int kRows0 = P * LD;
     // the fast-path kernel holds no stacked rows: only the basis values and its buffers
-    static constexpr int kRows = FASTONLY ? r4(n * HXS + kFastBuf)
-                                          : (kFast && n * HXS + kFastBuf > kRows0 ? r4(n * HXS + kFastBuf) : kRows0);
+    static constexpr int kRows = FASTONLY ? r4(n * HXS + kFastBuf) : kRows0;
     static constexpr int kRhs = NCOMP * P4, kPiv = 2 * (LD + 4), kVec = NCOMP * P4, kRes = NCOMP * P4;
     static constexpr int kGroup = (kRows + kRhs + kPiv + kVec + kRes + 3) & ~3;  // keeps rows 16-byte aligned
     // per-CTA tables: Z [N][N], lambda [N], h0 [N], h1 [N], -4 xi [N], 4 (1 - xi) [N]
@@ -147,12 +153,15 @@ constexpr int min_ctas2d()
 }
 
 // CTAs per SM of the fast-path kernel (MODE 1): it holds no Gram or pivot
-// rows, so FP32 fits three 256-thread CTAs (85 registers) where the direct
-// solve fits two; FP64 keeps two.
+// rows, so FP32 fits three CTAs (85 registers at 256 threads) where the
+// direct solve fits two, and four of the smaller CTAs of N = 9 (192 threads,
+// 80 registers) and N = 12 (160 threads, 96 registers; the compiler spills
+// no more there than at three); FP64 keeps two, and one at N = 11, whose
+// 151 KB of shared memory per CTA leave room for no second.
 template <int N, typename R>
 constexpr int min_ctas2d_fast()
 {
-    return std::is_same<R, float>::value ? 3 : 2;
+    return std::is_same<R, float>::value ? (N == 9 || N == 12 ? 4 : 3) : (N <= 10 ? 2 : 1);
 }
 
 // BATCH = false: one instance (a0), group g = element-sample g.
@@ -161,16 +170,16 @@ constexpr int min_ctas2d_fast()
 // NCOMP = 2: two fields per sample ([M][2][E][n]) on the same particles, so
 // one Gram matrix, one elimination and one upwind choice serve both; each
 // field has its own right-hand side, refinement, faces and state.
-// MODE 0: the direct solve for every group (orders without the fast path).
 // MODE 1: the fast path only; a group it does not finish is flagged in fb.
 // MODE 2: the direct solve for the groups MODE 1 flagged (CTAs without one exit).
-template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 0>
-__global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
+template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 1>
+__global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
+                                  MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
     sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args, const long long *__restrict__ prefix,
                      int ninst, int t)
 {
     using G = Geo2D<N, R, NCOMP, MODE == 1>;
-    static_assert(MODE == 0 || G::kFast, "the fast path and its fallback exist for one-lane rows, N <= 8, one or two fields");
+    static_assert((MODE == 1 || MODE == 2) && G::kFast, "the fast path and its fallback: N <= 12, one or two fields");
     constexpr int P4 = G::P4;  // stride of the per-field arrays
     constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
     constexpr int HXS = G::HXS;  // stride of the phase-2 basis-value table (16-byte rows)
@@ -474,11 +483,11 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
     // q += G0^{-1} S^T (rhs - S q) on the stacked system S = [V; w B], with
     // G0 = V0^T (I + w^2 E0^T E0) V0, E0 = B V0^{-1}, applied in the stable
     // order V0^{-1} (I - E0^T C^{-1} E0) V0^{-T}, C = w^{-2} I + E0 E0^T
-    // (4N x 4N, assembled from 1D products and inverted by one warp).  Both
-    // converge to the direct solution.  A group whose tensor factors are
-    // ill-conditioned (||Wx|| ||Wy|| above kFastCond: particles far outside
-    // the element) or whose iteration has not converged after kFastIters
-    // takes the direct path below, which is unchanged by this one.
+    // (4N x 4N, assembled from 1D products and inverted by its 4N row
+    // threads).  Both converge to the direct solution.  A group whose tensor
+    // factors are ill-conditioned (||Wx|| ||Wy|| above kFastCond: particles
+    // far outside the element) or whose iteration has not converged after
+    // kFastIters is flagged for the direct kernel.
     bool done = false;
     if constexpr (G::kFast && MODE == 1) {
         constexpr int NW = G::GS / 32;
@@ -690,78 +699,82 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
                     u4[c] = v;
                 }
                 group_sync(bar_id, G::GS);
-                // lane f of warp 0 assembles row f of C and, with the other lanes, inverts C in place
-                // (Gauss-Jordan without pivoting: C is symmetric positive definite, eigenvalues >= w^-2)
+                // thread f < 4N assembles row f of C, and those threads invert C in
+                // place (Gauss-Jordan without pivoting: C is symmetric positive
+                // definite, eigenvalues >= w^-2).  4N <= 32: the rows are one warp,
+                // synchronised per step by __syncwarp; above that (N >= 9) they span
+                // two warps and every step takes a group barrier.
+                constexpr bool kOneWarp = 4 * N <= 32;
                 R creg[4 * N];
 #pragma unroll
                 for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = R(0);
-                if (wig == 0) {
-                    if (lane < 4 * N) {
-                        const int f = lane;
-                        const bool fx = f < 2 * N;
-                        const int s = (f / N) & 1, k = f % N;
-                        const R *g = fx ? gx0 + s * R4N : gy0 + s * R4N;
-                        const R *g0 = fx ? gx0 : gy0;
-                        const R *g1 = fx ? gx1 : gy1;
-                        R gg0 = R(0), gg1 = R(0);
+                if (c < 4 * N) {
+                    const int f = c;
+                    const bool fx = f < 2 * N;
+                    const int s = (f / N) & 1, k = f % N;
+                    const R *g = fx ? gx0 + s * R4N : gy0 + s * R4N;
+                    const R *g0 = fx ? gx0 : gy0;
+                    const R *g1 = fx ? gx1 : gy1;
+                    R gg0 = R(0), gg1 = R(0);
 #pragma unroll
-                        for (int m = 0; m < N; ++m) {
-                            gg0 = fma(g[m], g0[m], gg0);
-                            gg1 = fma(g[m], g1[m], gg1);
-                        }
-                        const R *Mw = fx ? tB : tA;  // Wy Wy^T along x faces, Wx Wx^T along y faces
-#pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; ++f2) {
-                            const bool f2x = f2 < 2 * N;
-                            const int s2 = (f2 / N) & 1, k2 = f2 % N;
-                            R v;
-                            if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
-                            else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
-                            else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
-                            creg[f2] = f2 == f ? v + wi2 : v;
-                        }
+                    for (int m = 0; m < N; ++m) {
+                        gg0 = fma(g[m], g0[m], gg0);
+                        gg1 = fma(g[m], g1[m], gg1);
                     }
-                    // step k: the pivot lane scales its row by 1 / C[k][k] (the pivot
-                    // entry becomes that reciprocal) and publishes it; every other row
-                    // subtracts its entry k times the published row, and its entry k
-                    // becomes minus that product
+                    const R *Mw = fx ? tB : tA;  // Wy Wy^T along x faces, Wx Wx^T along y faces
 #pragma unroll
-                    for (int k = 0; k < 4 * N; ++k) {
-                        R *pr = prow + (k & 1) * G::r4(4 * N + 4);
-                        if (lane == k) {
-                            const R pinv = R(1) / creg[k];
-#pragma unroll
-                            for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
-#pragma unroll
-                            for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                                R v4[4];
-#pragma unroll
-                                for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
-                                *reinterpret_cast<VT *>(pr + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
-                            }
-                        }
-                        __syncwarp();
-                        if (lane < 4 * N && lane != k) {
-                            const R l = creg[k];
-#pragma unroll
-                            for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                                const VT v = *reinterpret_cast<const VT *>(pr + f2);
-#pragma unroll
-                                for (int i = 0; i < VW; ++i)
-                                    if (f2 + i < 4 * N)
-                                        creg[f2 + i] = f2 + i == k ? -l * VV::at(v, i) : fma(-l, VV::at(v, i), creg[f2 + i]);
-                            }
-                        }
+                    for (int f2 = 0; f2 < 4 * N; ++f2) {
+                        const bool f2x = f2 < 2 * N;
+                        const int s2 = (f2 / N) & 1, k2 = f2 % N;
+                        R v;
+                        if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
+                        else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
+                        else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
+                        creg[f2] = f2 == f ? v + wi2 : v;
                     }
-                    if (lane < 4 * N)  // row lane of C^{-1} to shared memory (16-byte stores)
+                }
+                // step k: the pivot row scales itself by 1 / C[k][k] (the pivot entry
+                // becomes that reciprocal) and publishes itself; every other row
+                // subtracts its entry k times the published row, and its entry k
+                // becomes minus that product
+                if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
+#pragma unroll
+                for (int k = 0; k < 4 * N; ++k) {
+                    R *pr = prow + (k & 1) * G::r4(4 * N + 4);
+                    if (c == k) {
+                        const R pinv = R(1) / creg[k];
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
 #pragma unroll
                         for (int f2 = 0; f2 < 4 * N; f2 += VW) {
                             R v4[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
-                            *reinterpret_cast<VT *>(Ci + lane * G::r4(4 * N) + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                            *reinterpret_cast<VT *>(pr + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                         }
+                    }
+                    if constexpr (kOneWarp) __syncwarp();
+                    else group_sync(bar_id, G::GS);
+                    if (c < 4 * N && c != k) {
+                        const R l = creg[k];
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                            const VT v = *reinterpret_cast<const VT *>(pr + f2);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i)
+                                if (f2 + i < 4 * N)
+                                    creg[f2 + i] = f2 + i == k ? -l * VV::at(v, i) : fma(-l, VV::at(v, i), creg[f2 + i]);
+                        }
+                    }
                 }
+                if (c < 4 * N)  // row c of C^{-1} to shared memory (16-byte stores)
+#pragma unroll
+                    for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                        R v4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
+                        *reinterpret_cast<VT *>(Ci + c * G::r4(4 * N) + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                    }
                 R qf[NCOMP];  // q - c at node c, per field
                 bool all = true;
                 for (int cc = 0; cc < NCOMP && all; ++cc) {
@@ -944,7 +957,10 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
         }
     }
     if constexpr (MODE == 1) {  // a group the fast path did not finish goes to the direct solve
-        if (group_active && tig == 0) a.fb[gid] = done ? 0 : 1;
+        if (group_active && tig == 0) {
+            a.fb[gid] = done ? 0 : 1;
+            if (!done && a.fbcount) atomicAdd(a.fbcount + (PHASE - 1), 1ull);
+        }
         if (!done) return;
     }
     // ---------------------------------------------------------------- direct path
@@ -1416,7 +1432,11 @@ __global__ void __launch_bounds__(Geo2D<N, R>::kBlock, MODE == 1 ? min_ctas2d_fa
         if constexpr (PHASE == 1) {
 #pragma unroll
             for (int cc = 0; cc < NCOMP; ++cc)
-                if (c < n && lead) vec[cc * P4 + c] = x[cc];  // the group may have more threads than nodes
+                if (c < n && lead) {  // the group may have more threads than nodes
+                    vec[cc * P4 + c] = x[cc];
+                    if constexpr (MODE == 2)  // the fast phase 2 starts from it
+                        static_cast<R *>(a.alpha)[(((long long)s * NCOMP + cc) * E + e) * n + c] = x[cc];
+                }
             group_sync(bar_id, G::GS);
         } else {
             if (real_lead) {
@@ -1473,32 +1493,32 @@ size_t smem2d()
 
 // One phase over groups [g0, g1): for orders with the fast path, the fast
 // kernel and then the direct kernel for the groups it flagged.
+// The two kernels group element-samples into CTAs differently (the fast one
+// runs one thread per node, the direct one SP lanes per row), so each takes
+// its own grid over the same `groups`.
 template <int N, typename R, int NCOMP, bool BATCH>
-cudaError_t launch_phase2d(int phase, unsigned grid, const Step2DArgs &b, const Step2DArgs *args,
+cudaError_t launch_phase2d(int phase, long long groups, const Step2DArgs &b, const Step2DArgs *args,
                            const long long *prefix, int ninst, int t, cudaStream_t st, LaunchThrottle *th)
 {
-    using G = Geo2D<N, R, NCOMP>;
-    const unsigned block = unsigned(G::kBlock);
-    auto one = [&](auto kernel, size_t smem) -> cudaError_t {
+    auto one = [&](auto kernel, auto geo, size_t smem) -> cudaError_t {
+        using G = decltype(geo);
         if (th) {
             const cudaError_t e = th->before();
             if (e != cudaSuccess) return e;
         }
-        kernel<<<grid, block, smem, st>>>(b, args, prefix, ninst, t);
+        const unsigned grid = unsigned((groups + G::GPC - 1) / G::GPC);
+        kernel<<<grid, unsigned(G::kBlock), smem, st>>>(b, args, prefix, ninst, t);
         return th ? th->after(st) : cudaSuccess;
     };
+    using GF = Geo2D<N, R, NCOMP, true>;
+    using GD = Geo2D<N, R, NCOMP, false>;
     cudaError_t e;
-    if constexpr (G::kFast) {
-        if (phase == 1) {
-            e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, smem2d<N, R, NCOMP, 1>());
-            if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>, smem2d<N, R, NCOMP, 2>());
-        } else {
-            e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, smem2d<N, R, NCOMP, 1>());
-            if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>, smem2d<N, R, NCOMP, 2>());
-        }
+    if (phase == 1) {
+        e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>());
+        if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>, GD{}, smem2d<N, R, NCOMP, 2>());
     } else {
-        e = phase == 1 ? one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 0>, smem2d<N, R, NCOMP, 0>())
-                       : one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 0>, smem2d<N, R, NCOMP, 0>());
+        e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>());
+        if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>, GD{}, smem2d<N, R, NCOMP, 2>());
     }
     return e;
 }
@@ -1518,8 +1538,8 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
             for (long long g0 = 0; g0 < groups; g0 += chunk) {
                 b.g0 = g0;
                 b.g1 = std::min(groups, g0 + chunk);
-                const unsigned grid = unsigned((b.g1 - g0 + G::GPC - 1) / G::GPC);
-                const cudaError_t e = launch_phase2d<N, R, NCOMP, false>(phase, grid, b, nullptr, nullptr, 0, t, st, th);
+                const cudaError_t e =
+                    launch_phase2d<N, R, NCOMP, false>(phase, b.g1 - g0, b, nullptr, nullptr, 0, t, st, th);
                 if (e != cudaSuccess) return e;
             }
     }
@@ -1529,16 +1549,10 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
 template <int N, typename R, int NCOMP, bool BATCH>
 cudaError_t preload_phases2d()
 {
-    using G = Geo2D<N, R, NCOMP>;
     cudaError_t e = cudaSuccess;
-    if constexpr (G::kFast) {
-        for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>,
-                       sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>})
-            if (e == cudaSuccess) e = prepare_kernel(k);
-    } else {
-        for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 0>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 0>})
-            if (e == cudaSuccess) e = prepare_kernel(k);
-    }
+    for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>,
+                   sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>})
+        if (e == cudaSuccess) e = prepare_kernel(k);
     return e;
 }
 
@@ -1563,13 +1577,11 @@ cudaError_t preload_step2d_n()
 template <int N, typename R>
 cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
 {
-    using G = Geo2D<N, R>;
-    const unsigned grid = unsigned((b.total_groups + G::GPC - 1) / G::GPC);
     Step2DArgs none = {};
     for (int t = 0; t < b.nsteps; ++t)
         for (int phase = 1; phase <= 2; ++phase) {
-            const cudaError_t e = launch_phase2d<N, R, 1, true>(phase, grid, none, b.args, b.prefix, b.ninst, t, st,
-                                                                nullptr);
+            const cudaError_t e = launch_phase2d<N, R, 1, true>(phase, b.total_groups, none, b.args, b.prefix, b.ninst,
+                                                                t, st, nullptr);
             if (e != cudaSuccess) return e;
         }
     return cudaGetLastError();

@@ -71,6 +71,7 @@ def test_invalid_precision_and_null(sl):
     assert L.sl_moments_partial(None, None, None) == -1
     assert L.sl_moments_combine(None, None, 1, 4, 4, None, None, None) == -1
     assert L.sl_moment_chunk() == 64
+    assert L.sl_fallback_count(None, None, None) == -1
 
 
 @pytest.mark.parametrize("bad,precision,code", [

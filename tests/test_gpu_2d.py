@@ -131,6 +131,37 @@ def test_high_order_launch_geometry_vs_oracle(sl, orc, precision, N):
     assert e_mean <= tol and e_m2 <= tol and e_st <= tol
 
 
+@pytest.mark.parametrize("precision,N", [("fp32", 8), ("fp32", 9), ("fp32", 12), ("fp64", 10), ("fp64", 11)])
+def test_fast_path_finishes_every_group_at_half_edge_dt(sl, orc, precision, N):
+    # particles a fraction of the node gap from their nodes: the tensor-
+    # preconditioned iteration converges for every element-sample in both
+    # phases, and no group goes to the direct solve
+    pb = _rot(K=(8, 8), N=N, M=8, steps=3, orc=orc)
+    pb["dt"] = 0.5 * orc.dt_edge(pb)
+    with sl.Solver(pb, precision) as s:
+        s.step()
+        assert s.fallbacks == (0, 0)
+
+
+@pytest.mark.parametrize("N", [4, 10])
+def test_fast_and_direct_solves_mix_vs_oracle(sl, orc, N):
+    # at the node-gap bound the conditioning test sends a share of the
+    # element-samples to the direct solve (in both phases at N = 4, in the
+    # remap at N = 10): each step runs both kernels on disjoint groups, the
+    # remap's iteration starting from interpolants either kernel formed, and
+    # still matches the oracle
+    pb = _rot(K=(8, 8), N=N, M=8, steps=3, orc=orc)
+    pb["dt"] = orc.dt_max(pb)
+    ref = orc.run(pb, want_states=True, nthreads=8, ns=pb["M"])
+    with sl.Solver(pb, "fp64") as s:
+        s.step()
+        f1, f2 = s.fallbacks
+        st = s.samples()
+    groups = 64 * pb["M"] * pb["steps"]
+    assert 0 < f2 < groups and (N > 4 or 0 < f1 < groups)
+    assert _rel(st, ref["states"], np.abs(ref["states"]).max()) <= FP64_TOL
+
+
 @pytest.mark.parametrize("N", [9, 10, 11, 12])
 def test_fp32_high_order_vs_oracle(sl, orc, N):
     # N = 11, 12: each Gram row split over four lanes
