@@ -332,6 +332,7 @@ void sl_free(sl_ctx *c)
     sl::ctx_free(c, c->coef2d);
     sl::ctx_free(c, c->fb2d);
     sl::ctx_free(c, c->fbcount2d);
+    sl::ctx_free(c, c->slots2d);
     delete c;
 }
 
@@ -432,7 +433,10 @@ int sl_init(sl_ctx **out, const sl_mesh *mesh, int N, int M, const sl_field *dri
              sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fb2d), size_t(M) * m.E) == cudaSuccess &&
              sl::ctx_alloc(c, reinterpret_cast<void **>(&c->fbcount2d), 2 * sizeof(unsigned long long)) ==
                  cudaSuccess &&
-             cudaMemsetAsync(c->fbcount2d, 0, 2 * sizeof(unsigned long long), c->st) == cudaSuccess;
+             cudaMemsetAsync(c->fbcount2d, 0, 2 * sizeof(unsigned long long), c->st) == cudaSuccess &&
+             sl::ctx_alloc(c, reinterpret_cast<void **>(&c->slots2d), (2 * size_t(M) * m.E + 2) * sizeof(unsigned)) ==
+                 cudaSuccess &&
+             cudaMemsetAsync(c->slots2d, 0, (2 * size_t(M) * m.E + 2) * sizeof(unsigned), c->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         sl_free(c);
@@ -668,6 +672,9 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.tab = c->tab2d;
             a.fb = c->fb2d;
             a.fbcount = c->fbcount2d;
+            a.slot_mark = c->slots2d;
+            a.slot_list = c->slots2d + size_t(c->M) * m.E;
+            a.slot_ctl = c->slots2d + 2 * size_t(c->M) * m.E;
             a.nodeU = c->nodeU;
             a.nodeB = c->nodeB;
             a.nodeDiv = c->nodeDiv;

@@ -44,6 +44,8 @@ struct Class2D {
     int N = 0;
     std::vector<int> ids;
     long long total = 0;
+    long long groups = 0;        // element-sample groups of the class
+    unsigned *d_slots = nullptr;  // [2 groups + 2]: the class's slot marks, list and list control
 };
 
 struct GraphSet {
@@ -251,6 +253,9 @@ int prepare_step(sl_batch *b, int steps, StepTables &t, std::vector<void *> &kee
         std::vector<long long> prefix(1, 0);
         for (int id : k.ids) {
             args.push_back(args2d(b->inst[id], b->dt[id], steps));
+            args.back().slot_mark = k.d_slots;  // the class's groups share one slot list
+            args.back().slot_list = k.d_slots + k.groups;
+            args.back().slot_ctl = k.d_slots + 2 * k.groups;
             prefix.push_back(prefix.back() + (long long)b->inst[id]->m.E * b->inst[id]->M);
         }
         sl::Batch2DLaunch l;
@@ -346,6 +351,7 @@ void sl_batch_free(sl_batch *b)
     drop_graphs(b);
     for (sl_ctx *c : b->inst) sl_free(c);
     for (Class1D &k : b->c1) cudaFree(k.d_counter);
+    for (Class2D &k : b->c2) cudaFree(k.d_slots);
     for (int l = 1; l < sl_batch::kMaxLanes; ++l) {
         if (b->lane_st[l]) cudaStreamDestroy(b->lane_st[l]);
         if (b->join_ev[l]) cudaEventDestroy(b->join_ev[l]);
@@ -447,6 +453,14 @@ int sl_batch_create(sl_batch **out, int count, const sl_instance *specs, const s
         }
         k.max_grid = 2 * b->nsm;  // refined by sl_batch_tune
         k.grid = b->nsm;
+    }
+    for (Class2D &k : b->c2) {
+        for (int id : k.ids) k.groups += (long long)b->inst[id]->m.E * b->inst[id]->M;
+        const size_t bytes = (2 * size_t(k.groups) + 2) * sizeof(unsigned);
+        if (cudaMalloc(&k.d_slots, bytes) != cudaSuccess || cudaMemset(k.d_slots, 0, bytes) != cudaSuccess) {
+            sl_batch_free(b);
+            return SL_ERR_OOM;
+        }
     }
     if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
         sl_batch_free(b);

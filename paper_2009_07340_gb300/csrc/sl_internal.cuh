@@ -97,6 +97,11 @@ struct Step2DArgs {
                            // scaled nodes, h_i(0), h_i(1), -4 xi_i, 4 (1 - xi_i)
     unsigned char *fb;     // [M][E]: groups the iterative solve left to the direct one
     unsigned long long *fbcount = nullptr;  // [2]: per phase, groups so left, cumulative (may be null)
+    // the direct kernel's CTA slots holding a flagged group (in a batch, those
+    // of args[0] serve the class): slot_mark [slots] 1 while listed,
+    // slot_list [slots], slot_ctl [2] = list length, CTAs finished; all zero
+    // between launches
+    unsigned *slot_mark = nullptr, *slot_list = nullptr, *slot_ctl = nullptr;
     const void *coef;      // [5][E][n] in the kernel's precision: 4 u_x dt / hx, 4 u_y dt / hy,
                            // 4 b / hx, 4 b / hy (b = sqrt(2 D)), dt du_j/dx_j (launch_coef2d)
     const double *nodeU;   // [2][E][n]
@@ -251,6 +256,7 @@ struct sl_ctx {
     double *tab2d = nullptr;  // 2D node tables of the order (Step2DArgs::tab)
     unsigned char *fb2d = nullptr;  // 2D: groups left to the direct solve, [M][E]
     unsigned long long *fbcount2d = nullptr;  // 2D: their cumulative count per phase [2]
+    unsigned *slots2d = nullptr;  // 2D: [2 M E + 2] slot marks, slot list, list control (Step2DArgs::slot_*)
     long long launch_chunk = 0;  // 2D: element-sample groups per kernel launch (0: all)
     double bc_weight = 1.0;       // weight w of the remap's boundary rows (INFINITY: hard, 1D)
     double inv_w2 = 1.0;          // 1 / w^2 (0 for hard constraints)

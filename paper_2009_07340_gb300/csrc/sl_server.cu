@@ -112,7 +112,7 @@ size_t footprint_of(const sl_instance &s, int slice)
     const size_t elem = 8;  // FP64 or FP32 pair
     size_t b = size_t(s.M) * V * elem;                                  // state
     if (dim == 2) b += size_t(s.M) * E * 4 * s.N * elem;                // face buffer
-    if (dim == 2) b += size_t(s.M) * V * elem + size_t(s.M) * E;        // interpolant carried between phases, flags
+    if (dim == 2) b += size_t(s.M) * V * elem + size_t(s.M) * E * 9;    // interpolant between phases, flags, slot list
     b += size_t(std::max(slice, 1)) * s.M * dim * sizeof(double);       // Wiener scratch
     b += size_t((s.M + 63) / 64) * V * 2 * sizeof(double);             // moment partials
     b += size_t(V) * (dim + 4) * sizeof(double) + size_t(2 * E * s.N) * 2 * sizeof(double);  // tables

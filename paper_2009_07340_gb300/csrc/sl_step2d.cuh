@@ -37,6 +37,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include <type_traits>
 
@@ -124,12 +125,28 @@ struct Geo2D {
     // the order has the tensor-preconditioned fast path (one or two fields)
     static constexpr bool kFast = N <= 12 && NCOMP <= 2;
     __host__ __device__ static constexpr int r4(int v) { return (v + 3) & ~3; }
-    // its buffers after the basis-value table: hxT, hyT [N][n]; Wx, WxT, Wy, WyT [N][N];
-    // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [n]; u4, mu4 [4N]; two pivot rows [4N + 4];
-    // convergence slots [2][GS / 32][2]
-    static constexpr int kFastBuf = FASTONLY ? 2 * N * r4(n) + 4 * r4(N * N) + 6 * r4(N) + 2 * r4(n) + 2 * r4(4 * N) +
-                                                   2 * r4(4 * N + 4) + r4(4 * (GS / 32) + 1) + 4 * N * r4(4 * N)
+    // row stride (elements) for v values read by 16-byte loads from
+    // consecutive rows: an odd number of 16-byte units, so that the eight
+    // rows of one quarter-warp fall in eight different groups of four banks
+    __host__ __device__ static constexpr int odd16(int v)
+    {
+        const int u = (v * int(sizeof(R)) + 15) / 16;
+        return (u | 1) * 16 / int(sizeof(R));
+    }
+    static constexpr int NTP = odd16(n);      // rows of the particles' basis values by node (hxT, hyT)
+    // rows of C^{-1} (FP64 N = 10 unpadded: the padding would leave room for
+    // one CTA per SM instead of two)
+    static constexpr int CIS = sizeof(R) == 8 && N == 10 ? r4(4 * N) : odd16(4 * N);
+    // pivot block of the inversion of C (divides 4N; the published block rows,
+    // 2 CB r4(4N) values, fit in the space of C^{-1})
+    static constexpr int kCB = 2;
+    // its buffers after the basis-value table: hxT, hyT [N][NTP]; Wx, WxT, Wy, WyT [N][N];
+    // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [NTP]; u4, mu4 [4N];
+    // convergence slots [2][GS / 32][2]; C^{-1} [4N][CIS]
+    static constexpr int kFastBuf = FASTONLY ? 2 * N * NTP + 4 * r4(N * N) + 6 * r4(N) + 2 * NTP + 2 * r4(4 * N) +
+                                                   r4(4 * (GS / 32) + 1) + 4 * N * CIS
                                              : 0;
+    static_assert((4 * N) % kCB == 0 && 2 * kCB * r4(4 * N) <= 4 * N * CIS, "pivot blocks of C");
     // rhs, vec and res hold one P4-long array per field
     static constexpr int kRows0 = P * LD;
     // the fast-path kernel holds no stacked rows: only the basis values and its buffers
@@ -170,13 +187,15 @@ constexpr int min_ctas2d_fast()
 // NCOMP = 2: two fields per sample ([M][2][E][n]) on the same particles, so
 // one Gram matrix, one elimination and one upwind choice serve both; each
 // field has its own right-hand side, refinement, faces and state.
-// MODE 1: the fast path only; a group it does not finish is flagged in fb.
-// MODE 2: the direct solve for the groups MODE 1 flagged (CTAs without one exit).
-template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 1>
-__global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
-                                  MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
-    sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args, const long long *__restrict__ prefix,
-                     int ninst, int t)
+// MODE 1: the fast path only; a group it does not finish is flagged in fb,
+//         and its direct-kernel CTA slot is listed (Step2DArgs::slot_*).
+// MODE 2: the direct solve for the groups MODE 1 flagged, CTA slot by slot
+//         from that list.
+// One CTA slot: groups [g0 + cta GPC, g0 + (cta + 1) GPC) (g0 = 0 in a batch),
+// the node tables already in shared memory.
+template <int N, typename R, int PHASE, bool BATCH, int NCOMP, int MODE>
+__device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs *__restrict__ args,
+                                         const long long *__restrict__ prefix, int ninst, int t, long long cta)
 {
     using G = Geo2D<N, R, NCOMP, MODE == 1>;
     static_assert((MODE == 1 || MODE == 2) && G::kFast, "the fast path and its fallback: N <= 12, one or two fields");
@@ -212,37 +231,7 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
     R *vec = piv + G::kPiv;        // [NCOMP][P4] broadcast vectors
     R *res = vec + G::kVec;        // [NCOMP][P4] residuals
 
-    // node tables depend on N only (every instance of a batch class shares
-    // them); computed once per context on the host (node_tables2d)
-    const double *tabsrc = BATCH ? args[0].tab : a0.tab;
-    for (int k = threadIdx.x; k < G::kTables; k += blockDim.x) tab[k] = R(tabsrc[k]);
-    if constexpr (MODE == 2) {  // a CTA none of whose groups was flagged has nothing to do
-        bool any = false;
-#pragma unroll
-        for (int g2 = 0; g2 < G::GPC; ++g2) {
-            const long long gg = (BATCH ? 0 : a0.g0) + (long long)blockIdx.x * G::GPC + g2;
-            long long gl = gg;
-            const Step2DArgs *ai = &a0;
-            if constexpr (BATCH) {
-                if (gg >= prefix[ninst]) continue;
-                int lo = 0, hi = ninst - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (prefix[mid] <= gg) lo = mid;
-                    else hi = mid - 1;
-                }
-                ai = args + lo;
-                gl = gg - prefix[lo];
-            } else if (gg >= a0.g1) {
-                continue;
-            }
-            any |= ai->fb[gl] != 0;
-        }
-        if (!any) return;  // uniform over the CTA, before its one CTA-wide barrier
-    }
-    __syncthreads();
-
-    const long long ggid = (BATCH ? 0 : a0.g0) + (long long)blockIdx.x * G::GPC + grp;
+    const long long ggid = (BATCH ? 0 : a0.g0) + cta * G::GPC + grp;
     int inst = 0;
     if constexpr (BATCH) {
         int lo = 0, hi = ninst - 1;  // last instance with prefix[i] <= ggid
@@ -491,7 +480,7 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
     bool done = false;
     if constexpr (G::kFast && MODE == 1) {
         constexpr int NW = G::GS / 32;
-        constexpr int NT = G::r4(n), R4N = G::r4(N);
+        constexpr int NT = G::NTP, R4N = G::r4(N);
         // largest ||Wx|| ||Wy|| tried: in a model of config-3 elements every
         // case converged below these in the given iteration count (FP32 phase 2
         // stops converging first)
@@ -514,9 +503,8 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
         R *tB = tA + NT;
         R *u4 = tB + NT;                // [4N]
         R *mu4 = u4 + G::r4(4 * N);     // [4N]
-        R *prow = mu4 + G::r4(4 * N);   // [2][4N + 4] pivot rows of the inversion of C
-        unsigned *red = reinterpret_cast<unsigned *>(prow + 2 * G::r4(4 * N + 4));  // [2][NW][2] maxima, [1] decision
-        R *Ci = prow + 2 * G::r4(4 * N + 4) + G::r4(4 * NW + 1);  // [4N][r4(4N)] C^{-1}
+        unsigned *red = reinterpret_cast<unsigned *>(mu4 + G::r4(4 * N));  // [2][NW][2] maxima, [1] decision
+        R *Ci = mu4 + G::r4(4 * N) + G::r4(4 * NW + 1);  // [4N][CIS] C^{-1}
         static_assert(n * HXS + G::kFastBuf <= G::kRows, "fast-path buffers fit in the rows' space");
         const int lane = threadIdx.x & 31, wig = tig >> 5;
         R cref = R(0);  // |c| of the field being iterated
@@ -733,39 +721,89 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
                         creg[f2] = f2 == f ? v + wi2 : v;
                     }
                 }
-                // step k: the pivot row scales itself by 1 / C[k][k] (the pivot entry
-                // becomes that reciprocal) and publishes itself; every other row
-                // subtracts its entry k times the published row, and its entry k
-                // becomes minus that product
+                // Block Gauss-Jordan inversion in place with CB x CB pivot blocks
+                // (every pivot block of an SPD matrix is SPD: no pivoting).  Step K:
+                // the CB pivot rows publish themselves; after one barrier every row
+                // thread inverts the pivot block P in registers and forms CB
+                // coefficients w: pivot row t takes row t of P^{-1}, any other row
+                // w = -C[r][K] P^{-1}; then C[r][j] <- C[r][j] + sum_m w_m C[K_m][j]
+                // outside the block (the pivot rows start from 0 instead of C[r][j])
+                // and C[r][K] <- w.  The published rows are double-buffered in the
+                // space of C^{-1}, which is written only after the last step.
+                constexpr int CB = G::kCB;
+                constexpr int CR = G::r4(4 * N);  // stride of the published rows
                 if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
 #pragma unroll
-                for (int k = 0; k < 4 * N; ++k) {
-                    R *pr = prow + (k & 1) * G::r4(4 * N + 4);
-                    if (c == k) {
-                        const R pinv = R(1) / creg[k];
-#pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = f2 == k ? pinv : creg[f2] * pinv;
+                for (int K = 0; K < 4 * N; K += CB) {
+                    R *pb = Ci + ((K / CB) & 1) * CB * CR;
+                    const bool pivot = c >= K && c < K + CB;
+                    if (pivot)
 #pragma unroll
                         for (int f2 = 0; f2 < 4 * N; f2 += VW) {
                             R v4[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
-                            *reinterpret_cast<VT *>(pr + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                            *reinterpret_cast<VT *>(pb + (c - K) * CR + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                         }
-                    }
                     if constexpr (kOneWarp) __syncwarp();
                     else group_sync(bar_id, G::GS);
-                    if (c < 4 * N && c != k) {
-                        const R l = creg[k];
+                    if (c < 4 * N) {
+                        R Pm[CB][CB];  // the pivot block, then its inverse
+#pragma unroll
+                        for (int t2 = 0; t2 < CB; ++t2)
+#pragma unroll
+                            for (int m = 0; m < CB; ++m) Pm[t2][m] = pb[t2 * CR + K + m];
+#pragma unroll
+                        for (int p = 0; p < CB; ++p) {
+                            const R d = R(1) / Pm[p][p];
+#pragma unroll
+                            for (int m = 0; m < CB; ++m) Pm[p][m] = m == p ? d : Pm[p][m] * d;
+#pragma unroll
+                            for (int q2 = 0; q2 < CB; ++q2)
+                                if (q2 != p) {
+                                    const R l = Pm[q2][p];
+#pragma unroll
+                                    for (int m = 0; m < CB; ++m) Pm[q2][m] = m == p ? -l * d : fma(-l, Pm[p][m], Pm[q2][m]);
+                                }
+                        }
+                        R w[CB];
+#pragma unroll
+                        for (int m = 0; m < CB; ++m) {
+                            R other = R(0), own = R(0);
+#pragma unroll
+                            for (int t2 = 0; t2 < CB; ++t2) {
+                                other = fma(-creg[K + t2], Pm[t2][m], other);
+                                own = c == K + t2 ? Pm[t2][m] : own;
+                            }
+                            w[m] = pivot ? own : other;
+                        }
 #pragma unroll
                         for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                            const VT v = *reinterpret_cast<const VT *>(pr + f2);
+                            VT v[CB];
 #pragma unroll
-                            for (int i = 0; i < VW; ++i)
-                                if (f2 + i < 4 * N)
-                                    creg[f2 + i] = f2 + i == k ? -l * VV::at(v, i) : fma(-l, VV::at(v, i), creg[f2 + i]);
+                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VT *>(pb + m * CR + f2);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i) {
+                                const int j = f2 + i;
+                                if (j < 4 * N) {
+                                    if (j >= K && j < K + CB) {
+                                        creg[j] = w[j - K];
+                                    } else {
+                                        R acc = pivot ? R(0) : creg[j];
+#pragma unroll
+                                        for (int m = 0; m < CB; ++m) acc = fma(w[m], VV::at(v[m], i), acc);
+                                        creg[j] = acc;
+                                    }
+                                }
+                            }
                         }
                     }
+                }
+                // the last step's published rows are read before C^{-1} overwrites them
+                if constexpr (kOneWarp) {
+                    if (wig == 0) __syncwarp();
+                } else {
+                    group_sync(bar_id, G::GS);
                 }
                 if (c < 4 * N)  // row c of C^{-1} to shared memory (16-byte stores)
 #pragma unroll
@@ -773,7 +811,7 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
                         R v4[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
-                        *reinterpret_cast<VT *>(Ci + c * G::r4(4 * N) + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                        *reinterpret_cast<VT *>(Ci + c * G::CIS + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                     }
                 R qf[NCOMP];  // q - c at node c, per field
                 bool all = true;
@@ -891,7 +929,7 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
                         R m = R(0);
 #pragma unroll
                         for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                            const VT cv = *reinterpret_cast<const VT *>(Ci + c * G::r4(4 * N) + f2);
+                            const VT cv = *reinterpret_cast<const VT *>(Ci + c * G::CIS + f2);
                             const VT uv = *reinterpret_cast<const VT *>(u4 + f2);
 #pragma unroll
                             for (int i = 0; i < VW; ++i)
@@ -959,7 +997,13 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
     if constexpr (MODE == 1) {  // a group the fast path did not finish goes to the direct solve
         if (group_active && tig == 0) {
             a.fb[gid] = done ? 0 : 1;
-            if (!done && a.fbcount) atomicAdd(a.fbcount + (PHASE - 1), 1ull);
+            if (!done) {
+                if (a.fbcount) atomicAdd(a.fbcount + (PHASE - 1), 1ull);
+                // its direct-kernel CTA slot, listed once however many of its groups are flagged
+                const Step2DArgs &L = BATCH ? args[0] : a0;
+                const long long slot = ggid / Geo2D<N, R, NCOMP, false>::GPC;
+                if (atomicExch(L.slot_mark + slot, 1u) == 0u) L.slot_list[atomicAdd(L.slot_ctl, 1u)] = unsigned(slot);
+            }
         }
         if (!done) return;
     }
@@ -1484,6 +1528,50 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
     if (bad) atomicOr(a.err, 1);
 }
 
+// The step kernel of one phase (see sl2d_cta).  MODE 1 runs one CTA slot per
+// CTA.  MODE 2 is a persistent grid over the slot list MODE 1 left: with no
+// flagged group it reads the list's length and exits; the last CTA to finish
+// empties the list for the next launch.
+template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 1>
+__global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
+                                  MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
+    sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args, const long long *__restrict__ prefix,
+                     int ninst, int t)
+{
+    using G = Geo2D<N, R, NCOMP, MODE == 1>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *tab = reinterpret_cast<R *>(smem_raw);
+    // node tables depend on N only (every instance of a batch class shares
+    // them); computed once per context on the host (node_tables2d)
+    const double *tabsrc = BATCH ? args[0].tab : a0.tab;
+    if constexpr (MODE == 1) {
+        for (int k = threadIdx.x; k < G::kTables; k += blockDim.x) tab[k] = R(tabsrc[k]);
+        __syncthreads();
+        sl2d_cta<N, R, PHASE, BATCH, NCOMP, MODE>(a0, args, prefix, ninst, t, blockIdx.x);
+    } else {
+        const Step2DArgs &L = BATCH ? args[0] : a0;
+        const unsigned count = *static_cast<volatile const unsigned *>(L.slot_ctl);
+        const long long slot0 = BATCH ? 0 : a0.g0 / G::GPC;  // a launch starts on a slot boundary
+        if (blockIdx.x < count) {
+            for (int k = threadIdx.x; k < G::kTables; k += blockDim.x) tab[k] = R(tabsrc[k]);
+            __syncthreads();
+            for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
+                const long long slot = L.slot_list[i];
+                sl2d_cta<N, R, PHASE, BATCH, NCOMP, MODE>(a0, args, prefix, ninst, t, slot - slot0);
+                __syncthreads();  // the slot's shared memory is free again
+                if (threadIdx.x == 0) L.slot_mark[slot] = 0u;
+            }
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(L.slot_ctl + 1, 1u) == gridDim.x - 1) {  // every other CTA has read the length
+                L.slot_ctl[0] = 0u;
+                L.slot_ctl[1] = 0u;
+            }
+        }
+    }
+}
+
 template <int N, typename R, int NCOMP, int MODE>
 size_t smem2d()
 {
@@ -1493,32 +1581,57 @@ size_t smem2d()
 
 // One phase over groups [g0, g1): for orders with the fast path, the fast
 // kernel and then the direct kernel for the groups it flagged.
-// The two kernels group element-samples into CTAs differently (the fast one
-// runs one thread per node, the direct one SP lanes per row), so each takes
-// its own grid over the same `groups`.
+// CTAs of kernel K resident on the device at once (at least one per SM).
+template <auto K>
+unsigned resident_ctas(int block, size_t smem)
+{
+    static std::atomic<int> per_sm{0};  // queried once the kernel has been prepared
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 1;
+    if (per_sm.load() == 0) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, block, smem) == cudaSuccess && per > 0)
+            per_sm.store(per);
+        else
+            cudaGetLastError();
+    }
+    return unsigned(std::max(1, nsm) * std::max(1, per_sm.load()));
+}
+
+// The fast kernel runs one CTA per slot of its own geometry (one thread per
+// node); the direct kernel (SP lanes per row, fewer groups per CTA) is a
+// persistent grid over the slots the fast kernel listed, at most one CTA
+// per slot of the launch and no more than fit on the device at once.
 template <int N, typename R, int NCOMP, bool BATCH>
 cudaError_t launch_phase2d(int phase, long long groups, const Step2DArgs &b, const Step2DArgs *args,
                            const long long *prefix, int ninst, int t, cudaStream_t st, LaunchThrottle *th)
 {
-    auto one = [&](auto kernel, auto geo, size_t smem) -> cudaError_t {
+    auto one = [&](auto kernel, auto geo, size_t smem, unsigned cap) -> cudaError_t {
         using G = decltype(geo);
         if (th) {
             const cudaError_t e = th->before();
             if (e != cudaSuccess) return e;
         }
-        const unsigned grid = unsigned((groups + G::GPC - 1) / G::GPC);
+        const unsigned grid = std::min(unsigned((groups + G::GPC - 1) / G::GPC), cap);
         kernel<<<grid, unsigned(G::kBlock), smem, st>>>(b, args, prefix, ninst, t);
         return th ? th->after(st) : cudaSuccess;
     };
     using GF = Geo2D<N, R, NCOMP, true>;
     using GD = Geo2D<N, R, NCOMP, false>;
+    constexpr unsigned kAll = ~0u;
     cudaError_t e;
     if (phase == 1) {
-        e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>());
-        if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>, GD{}, smem2d<N, R, NCOMP, 2>());
+        constexpr auto k2 = sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>;
+        e = one(sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>(), kAll);
+        if (e == cudaSuccess)
+            e = one(k2, GD{}, smem2d<N, R, NCOMP, 2>(), resident_ctas<k2>(GD::kBlock, smem2d<N, R, NCOMP, 2>()));
     } else {
-        e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>());
-        if (e == cudaSuccess) e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>, GD{}, smem2d<N, R, NCOMP, 2>());
+        constexpr auto k2 = sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>;
+        e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>(), kAll);
+        if (e == cudaSuccess)
+            e = one(k2, GD{}, smem2d<N, R, NCOMP, 2>(), resident_ctas<k2>(GD::kBlock, smem2d<N, R, NCOMP, 2>()));
     }
     return e;
 }
