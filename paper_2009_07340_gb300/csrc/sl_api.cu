@@ -672,6 +672,7 @@ int sl_step(sl_ctx *c, double dt, int steps)
             a.tab = c->tab2d;
             a.fb = c->fb2d;
             a.fbcount = c->fbcount2d;
+            a.f64_factor = c->precision == SL_MIXED;
             a.slot_mark = c->slots2d;
             a.slot_list = c->slots2d + size_t(c->M) * m.E;
             a.slot_ctl = c->slots2d + 2 * size_t(c->M) * m.E;

@@ -265,6 +265,7 @@ int prepare_step(sl_batch *b, int steps, StepTables &t, std::vector<void *> &kee
         l.ninst = int(k.ids.size());
         l.total_groups = prefix.back();
         l.nsteps = steps;
+        l.f64_factor = b->precision == SL_MIXED;
         t.l2.push_back(l);
     }
     return SL_OK;

@@ -102,6 +102,7 @@ struct Step2DArgs {
     // slot_list [slots], slot_ctl [2] = list length, CTAs finished; all zero
     // between launches
     unsigned *slot_mark = nullptr, *slot_list = nullptr, *slot_ctl = nullptr;
+    int f64_factor = 0;  // host: the FP32 remap factors its capacitance matrix in FP64 (SL_MIXED)
     const void *coef;      // [5][E][n] in the kernel's precision: 4 u_x dt / hx, 4 u_y dt / hy,
                            // 4 b / hx, 4 b / hy (b = sqrt(2 D)), dt du_j/dx_j (launch_coef2d)
     const double *nodeU;   // [2][E][n]
@@ -153,6 +154,7 @@ struct Batch2DLaunch {
     int ninst;
     long long total_groups;
     int nsteps;
+    int f64_factor = 0;        // SL_MIXED: capacitance matrix factored in FP64
 };
 cudaError_t launch_step2d_batch_fp64(const Batch2DLaunch &b, int N, cudaStream_t st);
 cudaError_t launch_step2d_batch_fp32(const Batch2DLaunch &b, int N, cudaStream_t st);

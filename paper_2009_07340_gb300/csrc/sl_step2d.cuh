@@ -138,8 +138,10 @@ struct Geo2D {
     // one CTA per SM instead of two)
     static constexpr int CIS = sizeof(R) == 8 && N == 10 ? r4(4 * N) : odd16(4 * N);
     // pivot block of the inversion of C (divides 4N; the published block rows,
-    // 2 CB r4(4N) values, fit in the space of C^{-1})
-    static constexpr int kCB = 2;
+    // 2 CB r4(4N) values, fit in the space of C^{-1}).  Measured on 16 x 16
+    // meshes: 4 x 4 blocks are 3-9 % faster than 2 x 2 for FP32 N >= 8 and
+    // 4-7 % slower in FP64 (its extra FP64 block inversions); below N = 8 a tie.
+    static constexpr int kCB = sizeof(R) == 4 && N >= 8 ? 4 : 2;
     // its buffers after the basis-value table: hxT, hyT [N][NTP]; Wx, WxT, Wy, WyT [N][N];
     // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [NTP]; u4, mu4 [4N];
     // convergence slots [2][GS / 32][2]; C^{-1} [4N][CIS]
@@ -191,14 +193,18 @@ constexpr int min_ctas2d_fast()
 //         and its direct-kernel CTA slot is listed (Step2DArgs::slot_*).
 // MODE 2: the direct solve for the groups MODE 1 flagged, CTA slot by slot
 //         from that list.
+// MODE 3: MODE 1 of the FP32 remap (phase 2) with the capacitance matrix C
+//         factored (inverted) in FP64 and C^{-1} rounded to FP32 for its
+//         applications: the mixed-precision form (SL_MIXED).
 // One CTA slot: groups [g0 + cta GPC, g0 + (cta + 1) GPC) (g0 = 0 in a batch),
 // the node tables already in shared memory.
 template <int N, typename R, int PHASE, bool BATCH, int NCOMP, int MODE>
 __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs *__restrict__ args,
                                          const long long *__restrict__ prefix, int ninst, int t, long long cta)
 {
-    using G = Geo2D<N, R, NCOMP, MODE == 1>;
-    static_assert((MODE == 1 || MODE == 2) && G::kFast, "the fast path and its fallback: N <= 12, one or two fields");
+    using G = Geo2D<N, R, NCOMP, MODE != 2>;
+    static_assert(MODE >= 1 && MODE <= 3 && G::kFast, "the fast path and its fallback: N <= 12, one or two fields");
+    static_assert(MODE != 3 || (PHASE == 2 && std::is_same<R, float>::value), "an FP64 capacitance factor: FP32 remap");
     constexpr int P4 = G::P4;  // stride of the per-field arrays
     constexpr int n = G::n, LD = G::LD, SP = G::SP, NC = G::NC;
     constexpr int HXS = G::HXS;  // stride of the phase-2 basis-value table (16-byte rows)
@@ -478,7 +484,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
     // far outside the element) or whose iteration has not converged after
     // kFastIters is flagged for the direct kernel.
     bool done = false;
-    if constexpr (G::kFast && MODE == 1) {
+    if constexpr (G::kFast && MODE != 2) {
         constexpr int NW = G::GS / 32;
         constexpr int NT = G::NTP, R4N = G::r4(N);
         // largest ||Wx|| ||Wy|| tried: in a model of config-3 elements every
@@ -693,9 +699,13 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 // synchronised per step by __syncwarp; above that (N >= 9) they span
                 // two warps and every step takes a group barrier.
                 constexpr bool kOneWarp = 4 * N <= 32;
-                R creg[4 * N];
+                using RC = typename std::conditional<MODE == 3, double, R>::type;  // the factor's precision
+                using VC = Vec16<RC>;
+                using VCT = typename VC::T;
+                constexpr int VWC = VC::W;
+                RC creg[4 * N];
 #pragma unroll
-                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = R(0);
+                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = RC(0);
                 if (c < 4 * N) {
                     const int f = c;
                     const bool fx = f < 2 * N;
@@ -718,7 +728,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
                         else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
                         else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
-                        creg[f2] = f2 == f ? v + wi2 : v;
+                        creg[f2] = f2 == f ? RC(v) + RC(wi2) : RC(v);
                     }
                 }
                 // Block Gauss-Jordan inversion in place with CB x CB pivot blocks
@@ -730,46 +740,47 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 // outside the block (the pivot rows start from 0 instead of C[r][j])
                 // and C[r][K] <- w.  The published rows are double-buffered in the
                 // space of C^{-1}, which is written only after the last step.
-                constexpr int CB = G::kCB;
-                constexpr int CR = G::r4(4 * N);  // stride of the published rows
+                constexpr int CB = MODE == 3 ? 2 : G::kCB;  // FP64 blocks: 2 x 2 (as in the FP64 kernels)
+                constexpr int CR = G::r4(4 * N);  // stride of the published rows (elements of RC)
+                static_assert(2 * CB * CR * sizeof(RC) <= 4 * N * G::CIS * sizeof(R), "published rows fit in C^{-1}");
                 if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
 #pragma unroll
                 for (int K = 0; K < 4 * N; K += CB) {
-                    R *pb = Ci + ((K / CB) & 1) * CB * CR;
+                    RC *pb = reinterpret_cast<RC *>(Ci) + ((K / CB) & 1) * CB * CR;
                     const bool pivot = c >= K && c < K + CB;
                     if (pivot)
 #pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                            R v4[4];
+                        for (int f2 = 0; f2 < 4 * N; f2 += VWC) {
+                            RC v4[4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
-                            *reinterpret_cast<VT *>(pb + (c - K) * CR + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                            for (int i = 0; i < 4; ++i) v4[i] = (i < VWC && f2 + i < 4 * N) ? creg[f2 + i] : RC(0);
+                            *reinterpret_cast<VCT *>(pb + (c - K) * CR + f2) = VC::make(v4[0], v4[1], v4[2], v4[3]);
                         }
                     if constexpr (kOneWarp) __syncwarp();
                     else group_sync(bar_id, G::GS);
                     if (c < 4 * N) {
-                        R Pm[CB][CB];  // the pivot block, then its inverse
+                        RC Pm[CB][CB];  // the pivot block, then its inverse
 #pragma unroll
                         for (int t2 = 0; t2 < CB; ++t2)
 #pragma unroll
                             for (int m = 0; m < CB; ++m) Pm[t2][m] = pb[t2 * CR + K + m];
 #pragma unroll
                         for (int p = 0; p < CB; ++p) {
-                            const R d = R(1) / Pm[p][p];
+                            const RC d = RC(1) / Pm[p][p];
 #pragma unroll
                             for (int m = 0; m < CB; ++m) Pm[p][m] = m == p ? d : Pm[p][m] * d;
 #pragma unroll
                             for (int q2 = 0; q2 < CB; ++q2)
                                 if (q2 != p) {
-                                    const R l = Pm[q2][p];
+                                    const RC l = Pm[q2][p];
 #pragma unroll
                                     for (int m = 0; m < CB; ++m) Pm[q2][m] = m == p ? -l * d : fma(-l, Pm[p][m], Pm[q2][m]);
                                 }
                         }
-                        R w[CB];
+                        RC w[CB];
 #pragma unroll
                         for (int m = 0; m < CB; ++m) {
-                            R other = R(0), own = R(0);
+                            RC other = RC(0), own = RC(0);
 #pragma unroll
                             for (int t2 = 0; t2 < CB; ++t2) {
                                 other = fma(-creg[K + t2], Pm[t2][m], other);
@@ -778,20 +789,20 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             w[m] = pivot ? own : other;
                         }
 #pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                            VT v[CB];
+                        for (int f2 = 0; f2 < 4 * N; f2 += VWC) {
+                            VCT v[CB];
 #pragma unroll
-                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VT *>(pb + m * CR + f2);
+                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VCT *>(pb + m * CR + f2);
 #pragma unroll
-                            for (int i = 0; i < VW; ++i) {
+                            for (int i = 0; i < VWC; ++i) {
                                 const int j = f2 + i;
                                 if (j < 4 * N) {
                                     if (j >= K && j < K + CB) {
                                         creg[j] = w[j - K];
                                     } else {
-                                        R acc = pivot ? R(0) : creg[j];
+                                        RC acc = pivot ? RC(0) : creg[j];
 #pragma unroll
-                                        for (int m = 0; m < CB; ++m) acc = fma(w[m], VV::at(v[m], i), acc);
+                                        for (int m = 0; m < CB; ++m) acc = fma(w[m], VC::at(v[m], i), acc);
                                         creg[j] = acc;
                                     }
                                 }
@@ -810,7 +821,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     for (int f2 = 0; f2 < 4 * N; f2 += VW) {
                         R v4[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? creg[f2 + i] : R(0);
+                        for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? R(creg[f2 + i]) : R(0);
                         *reinterpret_cast<VT *>(Ci + c * G::CIS + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                     }
                 R qf[NCOMP];  // q - c at node c, per field
@@ -994,7 +1005,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
             }
         }
     }
-    if constexpr (MODE == 1) {  // a group the fast path did not finish goes to the direct solve
+    if constexpr (MODE != 2) {  // a group the fast path did not finish goes to the direct solve
         if (group_active && tig == 0) {
             a.fb[gid] = done ? 0 : 1;
             if (!done) {
@@ -1008,7 +1019,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
         if (!done) return;
     }
     // ---------------------------------------------------------------- direct path
-    if constexpr (MODE != 1) {
+    if constexpr (MODE == 2) {
     if constexpr (PHASE == 1 && SP == 1) {
         // Phase 1: alpha = V^{-1} phi* by Gauss-Jordan elimination of the
         // square advected-basis matrix V itself, with partial (row) pivoting.
@@ -1533,18 +1544,18 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
 // flagged group it reads the list's length and exits; the last CTA to finish
 // empties the list for the next launch.
 template <int N, typename R, int PHASE, bool BATCH, int NCOMP = 1, int MODE = 1>
-__global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
-                                  MODE == 1 ? min_ctas2d_fast<N, R>() : min_ctas2d<N, R>())
+__global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE != 2>::kBlock,
+                                  MODE == 1 ? min_ctas2d_fast<N, R>() : (MODE == 3 ? 2 : min_ctas2d<N, R>()))
     sl2d_step_kernel(const Step2DArgs a0, const Step2DArgs *__restrict__ args, const long long *__restrict__ prefix,
                      int ninst, int t)
 {
-    using G = Geo2D<N, R, NCOMP, MODE == 1>;
+    using G = Geo2D<N, R, NCOMP, MODE != 2>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *tab = reinterpret_cast<R *>(smem_raw);
     // node tables depend on N only (every instance of a batch class shares
     // them); computed once per context on the host (node_tables2d)
     const double *tabsrc = BATCH ? args[0].tab : a0.tab;
-    if constexpr (MODE == 1) {
+    if constexpr (MODE != 2) {
         for (int k = threadIdx.x; k < G::kTables; k += blockDim.x) tab[k] = R(tabsrc[k]);
         __syncthreads();
         sl2d_cta<N, R, PHASE, BATCH, NCOMP, MODE>(a0, args, prefix, ninst, t, blockIdx.x);
@@ -1575,7 +1586,7 @@ __global__ void __launch_bounds__(Geo2D<N, R, NCOMP, MODE == 1>::kBlock,
 template <int N, typename R, int NCOMP, int MODE>
 size_t smem2d()
 {
-    using G = Geo2D<N, R, NCOMP, MODE == 1>;
+    using G = Geo2D<N, R, NCOMP, MODE != 2>;
     return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
 }
 
@@ -1604,9 +1615,15 @@ unsigned resident_ctas(int block, size_t smem)
 // node); the direct kernel (SP lanes per row, fewer groups per CTA) is a
 // persistent grid over the slots the fast kernel listed, at most one CTA
 // per slot of the launch and no more than fit on the device at once.
+// The mixed-precision form (an FP64 capacitance factor, MODE 3) exists for
+// the FP32 remap of one field.
+template <typename R, int NCOMP>
+constexpr bool kHasMode3 = std::is_same<R, float>::value && NCOMP == 1;
+
 template <int N, typename R, int NCOMP, bool BATCH>
 cudaError_t launch_phase2d(int phase, long long groups, const Step2DArgs &b, const Step2DArgs *args,
-                           const long long *prefix, int ninst, int t, cudaStream_t st, LaunchThrottle *th)
+                           const long long *prefix, int ninst, int t, bool f64c, cudaStream_t st,
+                           LaunchThrottle *th)
 {
     auto one = [&](auto kernel, auto geo, size_t smem, unsigned cap) -> cudaError_t {
         using G = decltype(geo);
@@ -1629,7 +1646,12 @@ cudaError_t launch_phase2d(int phase, long long groups, const Step2DArgs &b, con
             e = one(k2, GD{}, smem2d<N, R, NCOMP, 2>(), resident_ctas<k2>(GD::kBlock, smem2d<N, R, NCOMP, 2>()));
     } else {
         constexpr auto k2 = sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>;
-        e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>(), kAll);
+        if constexpr (kHasMode3<R, NCOMP>) {
+            e = f64c ? one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 3>, GF{}, smem2d<N, R, NCOMP, 3>(), kAll)
+                     : one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>(), kAll);
+        } else {
+            e = one(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, GF{}, smem2d<N, R, NCOMP, 1>(), kAll);
+        }
         if (e == cudaSuccess)
             e = one(k2, GD{}, smem2d<N, R, NCOMP, 2>(), resident_ctas<k2>(GD::kBlock, smem2d<N, R, NCOMP, 2>()));
     }
@@ -1651,8 +1673,8 @@ cudaError_t launch_step2d_n(const Step2DArgs &a, cudaStream_t st)
             for (long long g0 = 0; g0 < groups; g0 += chunk) {
                 b.g0 = g0;
                 b.g1 = std::min(groups, g0 + chunk);
-                const cudaError_t e =
-                    launch_phase2d<N, R, NCOMP, false>(phase, b.g1 - g0, b, nullptr, nullptr, 0, t, st, th);
+                const cudaError_t e = launch_phase2d<N, R, NCOMP, false>(phase, b.g1 - g0, b, nullptr, nullptr, 0, t,
+                                                                         a.f64_factor != 0, st, th);
                 if (e != cudaSuccess) return e;
             }
     }
@@ -1666,6 +1688,8 @@ cudaError_t preload_phases2d()
     for (auto k : {sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 1, BATCH, NCOMP, 2>,
                    sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 1>, sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 2>})
         if (e == cudaSuccess) e = prepare_kernel(k);
+    if constexpr (kHasMode3<R, NCOMP>)
+        if (e == cudaSuccess) e = prepare_kernel(sl2d_step_kernel<N, R, 2, BATCH, NCOMP, 3>);
     return e;
 }
 
@@ -1694,7 +1718,7 @@ cudaError_t launch_step2d_batch_n(const Batch2DLaunch &b, cudaStream_t st)
     for (int t = 0; t < b.nsteps; ++t)
         for (int phase = 1; phase <= 2; ++phase) {
             const cudaError_t e = launch_phase2d<N, R, 1, true>(phase, b.total_groups, none, b.args, b.prefix, b.ninst,
-                                                                t, st, nullptr);
+                                                                t, b.f64_factor != 0, st, nullptr);
             if (e != cudaSuccess) return e;
         }
     return cudaGetLastError();

@@ -116,6 +116,47 @@ def test_config3_full_mesh_fp32_vs_oracle(sl, orc):
     assert e_mean <= MIXED_TOL and e_m2 <= MIXED_TOL and e_st <= MIXED_TOL
 
 
+_ORACLE_CFG3_HALF = {}
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_config3_full_mesh_at_half_node_gap_vs_oracle(sl, orc, precision):
+    # the full mesh at config 3's time step (half the particle-gap bound: the
+    # bound itself is unstable in 2D), 16 samples, 6 steps.  The mixed form
+    # factors the remap's capacitance matrix in FP64 (the rest in FP32).
+    pb = I.config3(M=16, steps=6, dt=I.DT_CFG3_HALF)
+    if "ref" not in _ORACLE_CFG3_HALF:
+        _ORACLE_CFG3_HALF["ref"] = orc.run(pb, want_states=True, nthreads=8, ns=pb["M"])
+    ref = _ORACLE_CFG3_HALF["ref"]
+    with sl.Solver(pb, precision) as s:
+        s.step()
+        mean, m2 = s.moments()
+        st = s.samples()
+    rm = ref["sum"] / pb["M"]
+    scale = np.abs(rm).max()
+    assert _rel(mean, rm, scale) <= MIXED_TOL
+    assert _rel(m2, ref["sumsq"] / pb["M"]) <= MIXED_TOL
+    assert _rel(st, ref["states"], scale) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("N", [4, 8, 12])
+def test_mixed_factor_in_fp64_vs_oracle(sl, orc, N):
+    # the mixed form runs its own remap kernel (the capacitance matrix in
+    # FP64): its states differ from the FP32 form's in the last bits, and
+    # both are within the mixed tolerance of the oracle
+    pb = _rot(K=(8, 8), N=N, M=8, steps=3, orc=orc)
+    pb["dt"] = 0.5 * orc.dt_edge(pb)
+    ref = orc.run(pb, want_states=True, nthreads=8, ns=pb["M"])["states"]
+    out = {}
+    for precision in ("mixed", "fp32"):
+        with sl.Solver(pb, precision) as s:
+            s.step()
+            out[precision] = s.samples()
+            assert s.fallbacks == (0, 0)
+        assert _rel(out[precision], ref, np.abs(ref).max()) <= MIXED_TOL
+    assert not np.array_equal(out["mixed"], out["fp32"])
+
+
 @pytest.mark.parametrize("precision,N", [("fp32", 9), ("fp32", 10), ("fp32", 11), ("fp32", 12),
                                          ("fp64", 9), ("fp64", 10), ("fp64", 11)])
 def test_high_order_launch_geometry_vs_oracle(sl, orc, precision, N):

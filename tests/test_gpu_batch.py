@@ -66,7 +66,7 @@ def test_batch_equals_alone_1d(sl, orc, precision):
             assert np.array_equal(b.samples(i), _alone(sl, pb, precision, 11)), i
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_batch_equals_alone_2d_and_mixed_dims(sl, orc, precision):
     pbs = _mix2d(orc) + _mix1d(orc)[:2]
     with sl.Batch(pbs, precision) as b:
@@ -76,7 +76,7 @@ def test_batch_equals_alone_2d_and_mixed_dims(sl, orc, precision):
             assert np.array_equal(b.samples(i), _alone(sl, pb, precision, 6)), i
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_batch_high_orders_equal_alone(sl, orc, precision):
     # 2D orders whose Gram rows are split over several lanes (FP64 N = 9..11,
     # FP32 N = 11), batched with a one-lane order
