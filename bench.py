@@ -292,9 +292,9 @@ def leg_batch(sl, stream, m_div=32):
         one_d.append(pb)
     small = I.small_instances_1d()
     # config 4 in its stated precision, FP32 bulk with the FP64 factor (the
-    # mixed form); the 1D legs in FP32
-    for name, pbs, steps, prec in (("config4_all_512", cfg4, 1, "mixed"), ("config5_1d_mix", one_d, 20, "fp32"),
-                                   ("small_1d_uneven", small, 20, "fp32")):
+    # mixed form), and in FP32; the 1D legs in FP32
+    for name, pbs, steps, prec in (("config4_all_512", cfg4, 1, "mixed"), ("config4_all_512_fp32", cfg4, 1, "fp32"),
+                                   ("config5_1d_mix", one_d, 20, "fp32"), ("small_1d_uneven", small, 20, "fp32")):
         for pb in pbs:  # half of each instance's particle bound (2D: edge distance)
             pb["dt"] = ("edge", 0.5) if pb["dim"] == 2 else ("node", 0.5)
         esu = sum(int(np.prod(pb["K"])) * pb["M"] for pb in pbs) * steps
@@ -328,12 +328,16 @@ def leg_batch(sl, stream, m_div=32):
                   f"the configuration as drawn (full M, 100 steps) is "
                   f"{full:.3g} ESU, {full / c4['esu']:.0f}x this")
     c4["full_config_extrapolated_s"] = full / c4["batched"]["value"]
+    c4f = out["config4_all_512_fp32"]
+    c4f["what"] = c4["what"].replace("FP32 remap with the capacitance matrix factored in FP64", "FP32")
+    c4f["full_config_extrapolated_s"] = full / c4f["batched"]["value"]
     out["small_1d_uneven"]["what"] = ("256 instances, K ~ U{8..64}, N ~ U{4..8}, M ~ U{16..128}: each alone is "
                                       "far from filling the GPU, so one-by-one stepping is launch-bound")
     out["summary"] = {k: {"batched_esu_per_s": v["batched"]["value"], "speedup": v["speedup"],
                           "branches": v["tuned_branches"]}
                       for k, v in out.items() if isinstance(v, dict) and "batched" in v}
-    out["summary"]["config4_full_extrapolated_s"] = c4["full_config_extrapolated_s"]
+    out["summary"]["config4_full_extrapolated_s"] = {"mixed": c4["full_config_extrapolated_s"],
+                                                     "fp32": c4f["full_config_extrapolated_s"]}
     return out
 
 

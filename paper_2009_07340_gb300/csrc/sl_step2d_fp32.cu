@@ -1,9 +1,7 @@
-// 2D step kernels in FP32 with float-pair state and one refinement step
-// (see sl_step2d.cuh); N <= 12 (a Gram row of up to 81 floats per thread,
-// split over two or four lanes above that).
-// Both FP32 modes (SL_MIXED, SL_FP32) run this kernel in 2D: an FP64 Gram
-// factor would cost ~n^3/2 FP64 operations per element-sample, at 1/64 of the
-// FP32 rate on GB300.  The orders are compiled in sl_step2d_fp32_nNN.cu.
+// 2D step kernels of the FP32 remap with float-pair state (see
+// sl_step2d.cuh), N <= 12.  Both FP32 modes run them; SL_MIXED differs only
+// in the remap's fast kernel, which factors the capacitance matrix in FP64
+// (MODE 3).  The orders are compiled in sl_step2d_fp32_nNN.cu.
 #include "sl_internal.cuh"
 
 namespace sl {
