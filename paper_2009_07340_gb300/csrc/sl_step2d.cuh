@@ -142,6 +142,13 @@ struct Geo2D {
     // meshes: 4 x 4 blocks are 3-9 % faster than 2 x 2 for FP32 N >= 8 and
     // 4-7 % slower in FP64 (its extra FP64 block inversions); below N = 8 a tie.
     static constexpr int kCB = sizeof(R) == 4 && N >= 8 ? 4 : 2;
+    // threads per row of C in its assembly and inversion (measured on 16 x 16
+    // meshes in FP32): one up to N = 9, two at N = 10 and 11 (5 and 8 %
+    // faster than one), three at N = 12 (7 % faster than one, level with
+    // two).  At N = 8 two were 11 % slower than one (the 32 rows then need a
+    // group barrier per step instead of __syncwarp), at N = 9 two and at
+    // N = 10 three 7 % slower.
+    static constexpr int kQB = N <= 9 ? 1 : (N == 12 ? 3 : 2);
     // its buffers after the basis-value table: hxT, hyT [N][NTP]; Wx, WxT, Wy, WyT [N][N];
     // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [NTP]; u4, mu4 [4N];
     // convergence slots [2][GS / 32][2]; C^{-1} [4N][CIS]
@@ -693,21 +700,26 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     u4[c] = v;
                 }
                 group_sync(bar_id, G::GS);
-                // thread f < 4N assembles row f of C, and those threads invert C in
-                // place (Gauss-Jordan without pivoting: C is symmetric positive
-                // definite, eigenvalues >= w^-2).  4N <= 32: the rows are one warp,
-                // synchronised per step by __syncwarp; above that (N >= 9) they span
-                // two warps and every step takes a group barrier.
-                constexpr bool kOneWarp = 4 * N <= 32;
+                // C's rows are held by QB threads each (thread c: row c / QB, its
+                // columns [q CW, q CW + CW), q = c % QB), which assemble them from
+                // the 1D products and invert C in place (C is symmetric positive
+                // definite, eigenvalues >= w^-2).  4N QB <= 32: one warp,
+                // synchronised per step by __syncwarp; above that the group
+                // barrier.
+                constexpr int QB = G::kQB;
+                constexpr int CW = G::r4((4 * N + QB - 1) / QB);  // columns per thread
+                constexpr bool kOneWarp = 4 * N * QB <= 32;
                 using RC = typename std::conditional<MODE == 3, double, R>::type;  // the factor's precision
                 using VC = Vec16<RC>;
                 using VCT = typename VC::T;
                 constexpr int VWC = VC::W;
-                RC creg[4 * N];
+                const bool crow = c < 4 * N * QB;  // a thread holding part of a row of C
+                const int row = c / QB, col0 = (c - row * QB) * CW;
+                RC creg[CW];
 #pragma unroll
-                for (int f2 = 0; f2 < 4 * N; ++f2) creg[f2] = RC(0);
-                if (c < 4 * N) {
-                    const int f = c;
+                for (int jj = 0; jj < CW; ++jj) creg[jj] = RC(0);
+                if (crow) {
+                    const int f = row;
                     const bool fx = f < 2 * N;
                     const int s = (f / N) & 1, k = f % N;
                     const R *g = fx ? gx0 + s * R4N : gy0 + s * R4N;
@@ -721,44 +733,52 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     }
                     const R *Mw = fx ? tB : tA;  // Wy Wy^T along x faces, Wx Wx^T along y faces
 #pragma unroll
-                    for (int f2 = 0; f2 < 4 * N; ++f2) {
-                        const bool f2x = f2 < 2 * N;
-                        const int s2 = (f2 / N) & 1, k2 = f2 % N;
-                        R v;
-                        if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
-                        else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
-                        else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
-                        creg[f2] = f2 == f ? RC(v) + RC(wi2) : RC(v);
+                    for (int jj = 0; jj < CW; ++jj) {
+                        const int f2 = col0 + jj;
+                        if (QB == 1 || f2 < 4 * N) {
+                            const bool f2x = f2 < 2 * N;
+                            const int s2 = (f2 / N) & 1, k2 = f2 % N;
+                            R v;
+                            if (fx == f2x) v = (s2 == 0 ? gg0 : gg1) * Mw[k * N + k2];
+                            else if (fx) v = u4[(2 + s2) * N + k] * u4[s * N + k2];
+                            else v = u4[(2 + s) * N + k2] * u4[s2 * N + k];
+                            creg[jj] = f2 == f ? RC(v) + RC(wi2) : RC(v);
+                        }
                     }
                 }
                 // Block Gauss-Jordan inversion in place with CB x CB pivot blocks
                 // (every pivot block of an SPD matrix is SPD: no pivoting).  Step K:
-                // the CB pivot rows publish themselves; after one barrier every row
+                // the CB pivot rows publish themselves; after one barrier every
                 // thread inverts the pivot block P in registers and forms CB
                 // coefficients w: pivot row t takes row t of P^{-1}, any other row
                 // w = -C[r][K] P^{-1}; then C[r][j] <- C[r][j] + sum_m w_m C[K_m][j]
                 // outside the block (the pivot rows start from 0 instead of C[r][j])
-                // and C[r][K] <- w.  The published rows are double-buffered in the
-                // space of C^{-1}, which is written only after the last step.
+                // and C[r][K] <- w.  A thread reads its row's entries C[r][K] from
+                // the published rows: the partly inverted SPD matrix keeps
+                // C[r][k] = C[k][r] while r is not yet eliminated and
+                // C[r][k] = -C[k][r] once it is.  The published rows are
+                // double-buffered in the space of C^{-1}, written only after the
+                // last step.
                 constexpr int CB = MODE == 3 ? 2 : G::kCB;  // FP64 blocks: 2 x 2 (as in the FP64 kernels)
-                constexpr int CR = G::r4(4 * N);  // stride of the published rows (elements of RC)
+                constexpr int CR = G::r4(QB * CW);  // stride of the published rows (elements of RC)
                 static_assert(2 * CB * CR * sizeof(RC) <= 4 * N * G::CIS * sizeof(R), "published rows fit in C^{-1}");
                 if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
 #pragma unroll
                 for (int K = 0; K < 4 * N; K += CB) {
                     RC *pb = reinterpret_cast<RC *>(Ci) + ((K / CB) & 1) * CB * CR;
-                    const bool pivot = c >= K && c < K + CB;
+                    const bool pivot = crow && row >= K && row < K + CB;
                     if (pivot)
 #pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; f2 += VWC) {
+                        for (int jj = 0; jj < CW; jj += VWC) {
                             RC v4[4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) v4[i] = (i < VWC && f2 + i < 4 * N) ? creg[f2 + i] : RC(0);
-                            *reinterpret_cast<VCT *>(pb + (c - K) * CR + f2) = VC::make(v4[0], v4[1], v4[2], v4[3]);
+                            for (int i = 0; i < 4; ++i) v4[i] = i < VWC ? creg[jj + i] : RC(0);
+                            *reinterpret_cast<VCT *>(pb + (row - K) * CR + col0 + jj) =
+                                VC::make(v4[0], v4[1], v4[2], v4[3]);
                         }
                     if constexpr (kOneWarp) __syncwarp();
                     else group_sync(bar_id, G::GS);
-                    if (c < 4 * N) {
+                    if (crow) {
                         RC Pm[CB][CB];  // the pivot block, then its inverse
 #pragma unroll
                         for (int t2 = 0; t2 < CB; ++t2)
@@ -777,33 +797,37 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                                     for (int m = 0; m < CB; ++m) Pm[q2][m] = m == p ? -l * d : fma(-l, Pm[p][m], Pm[q2][m]);
                                 }
                         }
+                        const RC sgn = row >= K ? RC(1) : RC(-1);
                         RC w[CB];
 #pragma unroll
                         for (int m = 0; m < CB; ++m) {
                             RC other = RC(0), own = RC(0);
 #pragma unroll
                             for (int t2 = 0; t2 < CB; ++t2) {
-                                other = fma(-creg[K + t2], Pm[t2][m], other);
-                                own = c == K + t2 ? Pm[t2][m] : own;
+                                other = fma(-sgn * pb[t2 * CR + row], Pm[t2][m], other);
+                                own = row == K + t2 ? Pm[t2][m] : own;
                             }
                             w[m] = pivot ? own : other;
                         }
 #pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; f2 += VWC) {
+                        for (int jj = 0; jj < CW; jj += VWC) {
                             VCT v[CB];
 #pragma unroll
-                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VCT *>(pb + m * CR + f2);
+                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VCT *>(pb + m * CR + col0 + jj);
 #pragma unroll
                             for (int i = 0; i < VWC; ++i) {
-                                const int j = f2 + i;
-                                if (j < 4 * N) {
+                                const int j = col0 + jj + i;
+                                if (QB == 1 || j < 4 * N) {
                                     if (j >= K && j < K + CB) {
-                                        creg[j] = w[j - K];
+                                        RC wj = w[0];
+#pragma unroll
+                                        for (int m = 1; m < CB; ++m) wj = j == K + m ? w[m] : wj;
+                                        creg[jj + i] = wj;
                                     } else {
-                                        RC acc = pivot ? RC(0) : creg[j];
+                                        RC acc = pivot ? RC(0) : creg[jj + i];
 #pragma unroll
                                         for (int m = 0; m < CB; ++m) acc = fma(w[m], VC::at(v[m], i), acc);
-                                        creg[j] = acc;
+                                        creg[jj + i] = acc;
                                     }
                                 }
                             }
@@ -816,14 +840,15 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 } else {
                     group_sync(bar_id, G::GS);
                 }
-                if (c < 4 * N)  // row c of C^{-1} to shared memory (16-byte stores)
+                if (crow)  // this thread's part of row `row` of C^{-1} (16-byte stores)
 #pragma unroll
-                    for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                        R v4[4];
+                    for (int jj = 0; jj < CW; jj += VW)
+                        if (col0 + jj < 4 * N) {
+                            R v4[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) v4[i] = (i < VW && f2 + i < 4 * N) ? R(creg[f2 + i]) : R(0);
-                        *reinterpret_cast<VT *>(Ci + c * G::CIS + f2) = VV::make(v4[0], v4[1], v4[2], v4[3]);
-                    }
+                            for (int i = 0; i < 4; ++i) v4[i] = i < VW ? R(creg[jj + i]) : R(0);
+                            *reinterpret_cast<VT *>(Ci + row * G::CIS + col0 + jj) = VV::make(v4[0], v4[1], v4[2], v4[3]);
+                        }
                 R qf[NCOMP];  // q - c at node c, per field
                 bool all = true;
                 for (int cc = 0; cc < NCOMP && all; ++cc) {
