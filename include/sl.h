@@ -64,7 +64,7 @@ enum {
     SL_MIXED = 1, /* basis evaluation / remap contractions in FP32, the       */
                   /* constrained least-squares (capacitance) factor in FP64  */
                   /* (2D: the iterative remap's 4N x 4N capacitance matrix;  */
-                  /* its direct fallback and two-field runs factor in FP32)  */
+                  /* its direct fallback factors in FP32)                    */
     SL_FP32 = 2   /* as SL_MIXED but the factor in FP32 too                   */
 };
 

@@ -1641,9 +1641,9 @@ unsigned resident_ctas(int block, size_t smem)
 // persistent grid over the slots the fast kernel listed, at most one CTA
 // per slot of the launch and no more than fit on the device at once.
 // The mixed-precision form (an FP64 capacitance factor, MODE 3) exists for
-// the FP32 remap of one field.
+// the FP32 remap (one or two fields).
 template <typename R, int NCOMP>
-constexpr bool kHasMode3 = std::is_same<R, float>::value && NCOMP == 1;
+constexpr bool kHasMode3 = std::is_same<R, float>::value && NCOMP <= 2;
 
 template <int N, typename R, int NCOMP, bool BATCH>
 cudaError_t launch_phase2d(int phase, long long groups, const Step2DArgs &b, const Step2DArgs *args,
