@@ -156,6 +156,9 @@ struct Geo2D {
                                                    r4(4 * (GS / 32) + 1) + 4 * N * CIS
                                              : 0;
     static_assert((4 * N) % kCB == 0 && 2 * kCB * r4(4 * N) <= 4 * N * CIS, "pivot blocks of C");
+    // the mixed form's FP64 factor (MODE 3), per group after all groups (floats):
+    // [4][N][N] and [4][2][N] and [8][N] doubles, 88 doubles, [4][N][N] + [4N][4] + 56 floats
+    static constexpr int kX3 = FASTONLY ? r4(2 * (4 * N * N + 8 * N + 8 * N + 88) + 4 * N * N + 16 * N + 56) : 0;
     // rhs, vec and res hold one P4-long array per field
     static constexpr int kRows0 = P * LD;
     // the fast-path kernel holds no stacked rows: only the basis values and its buffers
@@ -700,6 +703,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     u4[c] = v;
                 }
                 group_sync(bar_id, G::GS);
+                if constexpr (MODE != 3) {
                 // C's rows are held by QB threads each (thread c: row c / QB, its
                 // columns [q CW, q CW + CW), q = c % QB), which assemble them from
                 // the 1D products and invert C in place (C is symmetric positive
@@ -709,7 +713,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 constexpr int QB = G::kQB;
                 constexpr int CW = G::r4((4 * N + QB - 1) / QB);  // columns per thread
                 constexpr bool kOneWarp = 4 * N * QB <= 32;
-                using RC = typename std::conditional<MODE == 3, double, R>::type;  // the factor's precision
+                using RC = R;
                 using VC = Vec16<RC>;
                 using VCT = typename VC::T;
                 constexpr int VWC = VC::W;
@@ -759,7 +763,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 // C[r][k] = -C[k][r] once it is.  The published rows are
                 // double-buffered in the space of C^{-1}, written only after the
                 // last step.
-                constexpr int CB = MODE == 3 ? 2 : G::kCB;  // FP64 blocks: 2 x 2 (as in the FP64 kernels)
+                constexpr int CB = G::kCB;
                 constexpr int CR = G::r4(QB * CW);  // stride of the published rows (elements of RC)
                 static_assert(2 * CB * CR * sizeof(RC) <= 4 * N * G::CIS * sizeof(R), "published rows fit in C^{-1}");
                 if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
@@ -849,6 +853,250 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             for (int i = 0; i < 4; ++i) v4[i] = i < VW ? R(creg[jj + i]) : R(0);
                             *reinterpret_cast<VT *>(Ci + row * G::CIS + col0 + jj) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                         }
+                } else {
+                // MODE 3: C^{-1} from its structure, the factors in FP64.  C =
+                // w^-2 I + [[Gx (x) My, Cxy], [Cxy^T, Gy (x) Mx]] with Gx = [gx_s . gx_s']
+                // (2 x 2), My = Wy Wy^T and Cxy of rank 4 (its (s, s') blocks are
+                // hvy_s' hvx_s^T).  The Kronecker blocks invert through the
+                // eigenvectors Q of Gx and Gy: (w^-2 I + Gx (x) My)^{-1} =
+                // sum_t q_t q_t^T (x) (w^-2 I + lambda_t My)^{-1}, four N x N
+                // inverses; the coupling enters by block elimination and the
+                // Woodbury identity on the Schur complement, with 4 x 4 matrices
+                // P = A^T Cxx^{-1} A, Qm = B^T Cyy^{-1} B (Cxy = A B^T) and
+                // T = P^{-1} - Qm.  The N x N and 4 x 4 inverses and the products
+                // that form P and Qm run in FP64; C^{-1}'s entries are assembled
+                // in FP32 from them.  Same result as the inverse of the dense C
+                // (checked in a NumPy model with these index conventions).
+                double *xd = reinterpret_cast<double *>(tab + ((G::kTables + 3) & ~3) + G::GPC * G::kGroup +
+                                                        grp * G::kX3);
+                double *Ainv = xd;                 // [4][N][N]: (w^-2 I + lx_t My)^{-1}, t = 0, 1; then the y side
+                double *piv64 = Ainv + 4 * N * N;  // [4][2][N] pivot rows of their Gauss-Jordan
+                double *yz = piv64 + 8 * N;        // [8][N]: y_{t,tp} = Ainv_t hvy_tp, z_{t,tg} = Ainv_{2+t} hvx_tg
+                double *sm64 = yz + 8 * N;         // Qx [2][2], lx [2], Qy [2][2], ly [2], then warp-0 scratch
+                float *A32 = reinterpret_cast<float *>(sm64 + 88);  // [4][N][N] Ainv rounded
+                float *Z32 = A32 + 4 * N * N;      // [4N][4]: rows of Cxx^{-1} A (x faces), Cyy^{-1} B (y faces)
+                float *s32 = Z32 + 16 * N;         // Qx [4], Qy [4], Mxx [16], M1 [16], Ti [16]
+                const R *hvx = u4, *hvy = u4 + 2 * N;  // hvx[s N + i] = (Wx gx_s)_i, hvy[s N + j] = (Wy gy_s)_j
+                // GB300 runs FP64 at 2 lanes per clock per SM, so a warp-wide FP64
+                // instruction costs the same whatever its active lanes: the small
+                // FP64 steps below spread their work over the lanes of warp 0.
+                double *w64 = sm64 + 12;  // warp-0 scratch: [6] Gram entries, then [16] dots, [3][16] 4 x 4 matrices
+                if (wig == 0) {  // the 2 x 2 eigen-decompositions (a Jacobi rotation each)
+                    if (lane < 6) {  // lane 3 d + e: d = 0 x, 1 y; e = 0: g0.g0, 1: g0.g1, 2: g1.g1
+                        const int d = lane / 3, e = lane - 3 * d;
+                        const R *ga = d == 0 ? (e == 2 ? gx1 : gx0) : (e == 2 ? gy1 : gy0);
+                        const R *gb = d == 0 ? (e == 0 ? gx0 : gx1) : (e == 0 ? gy0 : gy1);
+                        double acc = 0.0;
+#pragma unroll
+                        for (int m = 0; m < N; ++m) acc = fma(double(ga[m]), double(gb[m]), acc);
+                        w64[lane] = acc;
+                    }
+                    __syncwarp();
+                    if (lane < 2) {
+                        const int d = lane;
+                        const double g00 = w64[3 * d], g01 = w64[3 * d + 1], g11 = w64[3 * d + 2];
+                        double cs = 1.0, sn = 0.0, l0 = g00, l1 = g11;
+                        if (g01 != 0.0) {
+                            const double tau = (g11 - g00) / (2.0 * g01);
+                            const double tn = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+                            cs = 1.0 / sqrt(fma(tn, tn, 1.0));
+                            sn = tn * cs;
+                            l0 = fma(-tn, g01, g00);
+                            l1 = fma(tn, g01, g11);
+                        }
+                        double *q = sm64 + 6 * d;  // Q = [[cs, sn], [-sn, cs]]: column t the eigenvector of l_t
+                        q[0] = cs;
+                        q[1] = sn;
+                        q[2] = -sn;
+                        q[3] = cs;
+                        q[4] = l0;
+                        q[5] = l1;
+                        s32[4 * d + 0] = float(cs);
+                        s32[4 * d + 1] = float(sn);
+                        s32[4 * d + 2] = float(-sn);
+                        s32[4 * d + 3] = float(cs);
+                    }
+                }
+                group_sync(bar_id, G::GS);
+                {  // the four N x N inverses, Gauss-Jordan in FP64, each matrix's rows in one warp
+                    constexpr bool kOneWarp3 = 4 * N <= 32;
+                    int mat = -1, row = 0;
+                    if constexpr (kOneWarp3) {
+                        if (tig < 4 * N) mat = tig / N, row = tig % N;
+                    } else {
+                        if (wig < 2 && lane < 2 * N) mat = 2 * wig + lane / N, row = lane % N;
+                    }
+                    double arow[N];
+                    if (mat >= 0) {
+                        const double lam = sm64[(mat >> 1) * 6 + 4 + (mat & 1)];
+                        const R *M = mat < 2 ? tB : tA;  // My for the x faces, Mx for the y faces
+#pragma unroll
+                        for (int j = 0; j < N; ++j)
+                            arow[j] = j == row ? fma(lam, double(M[row * N + j]), double(wi2)) : lam * double(M[row * N + j]);
+                    }
+                    if (kOneWarp3 ? wig == 0 : wig < 2) {  // uniform per warp
+#pragma unroll
+                        for (int k = 0; k < N; ++k) {
+                            // the pivot row publishes itself unscaled; every row then takes
+                            // one FMA per entry (the pivot row from zero), so that the
+                            // warp's FP64 instructions are not split by the pivot's scaling
+                            double *pr = piv64 + ((mat < 0 ? 0 : mat) * 2 + (k & 1)) * N;
+                            if (mat >= 0 && row == k)
+#pragma unroll
+                                for (int j = 0; j < N; ++j) pr[j] = arow[j];
+                            __syncwarp();
+                            if (mat >= 0) {
+                                const double pinv = 1.0 / pr[k];
+                                const bool own = row == k;
+                                const double coef = own ? pinv : -arow[k] * pinv;
+#pragma unroll
+                                for (int j = 0; j < N; ++j)
+                                    arow[j] = j == k ? (own ? pinv : coef) : fma(coef, pr[j], own ? 0.0 : arow[j]);
+                            }
+                        }
+                    }
+                    if (mat >= 0)
+#pragma unroll
+                        for (int j = 0; j < N; ++j) {
+                            Ainv[(mat * N + row) * N + j] = arow[j];
+                            A32[(mat * N + row) * N + j] = float(arow[j]);
+                        }
+                }
+                group_sync(bar_id, G::GS);
+                for (int e2 = tig; e2 < 8 * N; e2 += G::GS) {  // y and z, FP64
+                    const int v = e2 / N, k = e2 - v * N;
+                    const int mat = v < 4 ? v >> 1 : 2 + ((v - 4) >> 1);
+                    const R *h = v < 4 ? hvy + (v & 1) * N : hvx + (v & 1) * N;
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k2 = 0; k2 < N; ++k2) acc = fma(Ainv[(mat * N + k) * N + k2], double(h[k2]), acc);
+                    yz[e2] = acc;
+                }
+                group_sync(bar_id, G::GS);
+                if (wig == 0) {  // P, Qm and the 4 x 4 algebra, FP64, one entry per lane
+                    double *dyz = w64 + 6;   // [16]: dy[t][a1][a2] = hvy_a1 . y_{t,a2} at 4t + 2a1 + a2, dz at 8 + ...
+                    double *Pm = dyz + 16;   // [16] P, then P^{-1}, then T^{-1}
+                    double *Qm = Pm + 16;    // [16]
+                    double *QT = Qm + 16;    // [16] Qm T^{-1}
+                    if (lane < 16) {
+                        const bool isz = lane >= 8;
+                        const int t = (lane >> 2) & 1, a1 = (lane >> 1) & 1, a2 = lane & 1;
+                        const R *h = isz ? hvx + a1 * N : hvy + a1 * N;
+                        const double *v = yz + ((isz ? 4 : 0) + 2 * t + a2) * N;
+                        double acc = 0.0;
+#pragma unroll
+                        for (int k = 0; k < N; ++k) acc = fma(double(h[k]), v[k], acc);
+                        dyz[lane] = acc;
+                    }
+                    __syncwarp();
+                    const int e = lane & 15, i4 = e >> 2, j4 = e & 3;
+                    {
+                        const double *Qx = sm64, *Qy = sm64 + 6;
+                        const int sg = i4 >> 1, sp = i4 & 1, tg = j4 >> 1, tp = j4 & 1;
+                        double v = 0.0;
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+                            v = lane < 16 ? fma(Qx[2 * sg + t] * Qx[2 * tg + t], dyz[4 * t + 2 * sp + tp], v)
+                                          : fma(Qy[2 * sp + t] * Qy[2 * tp + t], dyz[8 + 4 * t + 2 * sg + tg], v);
+                        (lane < 16 ? Pm : Qm)[e] = v;
+                    }
+                    __syncwarp();
+                    auto inv4w = [&](double *A) {  // in place, one entry per lane (both half-warps alike)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const double p = A[5 * k], aik = A[4 * i4 + k], akj = A[4 * k + j4], aij = A[e];
+                            __syncwarp();
+                            const double pinv = 1.0 / p;
+                            const double v = i4 == k ? (j4 == k ? pinv : akj * pinv)
+                                                     : (j4 == k ? -aik * pinv : fma(-aik, akj * pinv, aij));
+                            if (lane < 16) A[e] = v;
+                            __syncwarp();
+                        }
+                    };
+                    inv4w(Pm);
+                    if (lane < 16) Pm[e] -= Qm[e];  // T = P^{-1} - Qm
+                    __syncwarp();
+                    inv4w(Pm);                      // T^{-1}
+                    double qt = 0.0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) qt = fma(Qm[4 * i4 + m], Pm[4 * m + j4], qt);
+                    if (lane < 16) QT[e] = qt;
+                    __syncwarp();
+                    double mxx = Qm[e];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) mxx = fma(QT[4 * i4 + m], Qm[4 * m + j4], mxx);
+                    if (lane < 16) {
+                        s32[8 + e] = float(mxx);                                   // Mxx = Qm + Qm T^-1 Qm
+                        s32[24 + e] = float((i4 == j4 ? 1.0 : 0.0) + QT[e]);      // M1 = I + Qm T^-1
+                        s32[40 + e] = float(Pm[e]);                                // T^-1
+                    }
+                }
+                if (c < 4 * N) {  // row c of Cxx^{-1} A (x faces) or Cyy^{-1} B (y faces)
+                    const int f = c, s = (f / N) & 1, k = f % N;
+                    const double *Qd = f < 2 * N ? sm64 : sm64 + 6;
+                    float zr[4];
+#pragma unroll
+                    for (int a1 = 0; a1 < 2; ++a1)
+#pragma unroll
+                        for (int a2 = 0; a2 < 2; ++a2) {
+                            double acc = 0.0;
+#pragma unroll
+                            for (int t = 0; t < 2; ++t)
+                                acc = f < 2 * N ? fma(Qd[2 * s + t] * Qd[2 * a1 + t], yz[(2 * t + a2) * N + k], acc)
+                                                : fma(Qd[2 * s + t] * Qd[2 * a2 + t], yz[(4 + 2 * t + a1) * N + k], acc);
+                            zr[2 * a1 + a2] = float(acc);
+                        }
+                    *reinterpret_cast<float4 *>(Z32 + 4 * f) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+                }
+                group_sync(bar_id, G::GS);
+                if (c < 4 * N) {  // row c of C^{-1}, assembled in FP32
+                    const int f = c, s = (f / N) & 1, k = f % N;
+                    const bool fx = f < 2 * N;
+                    const float4 zv = *reinterpret_cast<const float4 *>(Z32 + 4 * f);
+                    const float zr[4] = {zv.x, zv.y, zv.z, zv.w};
+                    const float *Mxx = s32 + 8, *M1 = s32 + 24, *Tinv = s32 + 40;
+                    float rr[4], rp[4];  // the row's coefficients for its own block and the other
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            a1 = fmaf(zr[m], fx ? Mxx[4 * m + j] : Tinv[4 * m + j], a1);
+                            a2 = fmaf(fx ? zr[m] : zr[m], fx ? M1[4 * m + j] : M1[4 * j + m], a2);
+                        }
+                        rr[j] = a1;
+                        rp[j] = -a2;
+                    }
+                    const float *Q32 = fx ? s32 : s32 + 4;
+                    float cq[2][2];  // Q[s][t] Q[s2][t]
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) cq[s2][t] = Q32[2 * s + t] * Q32[2 * s2 + t];
+                    const float *Ab = A32 + (fx ? 0 : 2) * N * N + k * N;  // row k of the block's inverses t = 0, 1
+#pragma unroll
+                    for (int f2 = 0; f2 < 4 * N; f2 += 4) {
+                        float v4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int g2 = f2 + i, s2 = (g2 / N) & 1, k2 = g2 % N;
+                            const bool same = fx == (g2 < 2 * N);
+                            const float4 z2 = *reinterpret_cast<const float4 *>(Z32 + 4 * g2);
+                            const float *cf = same ? rr : rp;
+                            float v = cf[0] * z2.x;
+                            v = fmaf(cf[1], z2.y, v);
+                            v = fmaf(cf[2], z2.z, v);
+                            v = fmaf(cf[3], z2.w, v);
+                            if (same) {
+                                v = fmaf(cq[s2][0], Ab[k2], v);
+                                v = fmaf(cq[s2][1], Ab[N * N + k2], v);
+                            }
+                            v4[i] = v;
+                        }
+                        *reinterpret_cast<float4 *>(Ci + f * G::CIS + f2) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+                    }
+                }
+                }
                 R qf[NCOMP];  // q - c at node c, per field
                 bool all = true;
                 for (int cc = 0; cc < NCOMP && all; ++cc) {
@@ -1612,7 +1860,7 @@ template <int N, typename R, int NCOMP, int MODE>
 size_t smem2d()
 {
     using G = Geo2D<N, R, NCOMP, MODE != 2>;
-    return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * G::kGroup);
+    return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * (G::kGroup + (MODE == 3 ? G::kX3 : 0)));
 }
 
 // One phase over groups [g0, g1): for orders with the fast path, the fast
