@@ -624,7 +624,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 for (int cc = 0; cc < NCOMP && all; ++cc) {
                     R *vc = vec + cc * P4, *rs = res + cc * P4;
                     const R *hs = rhs + cc * P4;
-                    cref = R(fabs(double(ch[cc])));
+                    cref = fabs(ch[cc]);
                     R x = R(0);                  // alpha - c at node c
                     R r = real ? hs[c] : R(0);   // phi* - V alpha at particle c
                     bool conv = false;
@@ -1102,7 +1102,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 for (int cc = 0; cc < NCOMP && all; ++cc) {
                 R *vec = gvec + cc * P4, *res = gres + cc * P4;
                 const R *rhs = grhs + cc * P4;
-                cref = R(fabs(double(ch[cc])));
+                cref = fabs(ch[cc]);
                 // phase 1's interpolant: the remap differs from it only by the face correction
                 R q = real ? static_cast<const R *>(a.alpha)[(((long long)s * NCOMP + cc) * E + e) * n + c] : R(0);
                 bool conv = false;
