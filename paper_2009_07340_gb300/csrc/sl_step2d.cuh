@@ -149,7 +149,7 @@ struct Geo2D {
     // group barrier per step instead of __syncwarp), at N = 9 two and at
     // N = 10 three 7 % slower.
     static constexpr int kQB = N <= 9 ? 1 : (N == 12 ? 3 : 2);
-    // its buffers after the basis-value table: hxT, hyT [N][NTP]; Wx, WxT, Wy, WyT [N][N];
+    // its buffers after the basis-value table: hxT, hyT [N][NTP]; Wx, Mx = Wx Wx^T, Wy, My [N][N];
     // gx0, gx1, gy0, gy1, dbx, dby [N]; tA, tB [NTP]; u4, mu4 [4N];
     // convergence slots [2][GS / 32][2]; C^{-1} [4N][CIS]
     static constexpr int kFastBuf = FASTONLY ? 2 * N * NTP + 4 * r4(N * N) + 6 * r4(N) + 2 * NTP + 2 * r4(4 * N) +
@@ -506,10 +506,10 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
         R *hxT = Vs + n * HXS;          // [N][NT]: hx_p[i] at [i][p]
         R *hyT = hxT + N * NT;          // [N][NT]
         R *Wx = hyT + N * NT;           // [N][N]: Wx[i][a]
-        R *WxT = Wx + G::r4(N * N);     // [N][N]: Wx transposed
-        R *Wy = WxT + G::r4(N * N);
-        R *WyT = Wy + G::r4(N * N);
-        R *gx0 = WyT + G::r4(N * N);    // [N] l~_a(0); then l~_a(1), and the same in y
+        R *Mx = Wx + G::r4(N * N);      // [N][N]: Wx Wx^T
+        R *Wy = Mx + G::r4(N * N);
+        R *My = Wy + G::r4(N * N);      // [N][N]: Wy Wy^T
+        R *gx0 = My + G::r4(N * N);     // [N] l~_a(0); then l~_a(1), and the same in y
         R *gx1 = gx0 + R4N;
         R *gy0 = gx1 + R4N;
         R *gy1 = gy0 + R4N;
@@ -519,6 +519,8 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
         R *tB = tA + NT;
         R *u4 = tB + NT;                // [4N]
         R *mu4 = u4 + G::r4(4 * N);     // [4N]
+        R *uu4 = piv;                   // [4N] u = E0 t, in the direct solve's pivot rows (unused here)
+        static_assert(G::kPiv >= G::r4(4 * N), "u fits in the pivot rows");
         unsigned *red = reinterpret_cast<unsigned *>(mu4 + G::r4(4 * N));  // [2][NW][2] maxima, [1] decision
         R *Ci = mu4 + G::r4(4 * N) + G::r4(4 * NW + 1);  // [4N][CIS] C^{-1}
         static_assert(n * HXS + G::kFastBuf <= G::kRows, "fast-path buffers fit in the rows' space");
@@ -565,9 +567,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 }
             const R wx = nx / dx_, wy = ny / dy_;
             Wx[i * N + a2] = wx;
-            WxT[a2 * N + i] = wx;
             Wy[i * N + a2] = wy;
-            WyT[a2 * N + i] = wy;
         }
         if (c < 4 * N) {
             const int s2 = c / N, a2 = c % N;
@@ -680,7 +680,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 R *const gvec = vec, *const gres = res;
                 const R *const grhs = rhs;
                 const R wb = R(a.w), wi2 = R(1) / (wb * wb);
-                // products for C: Wx Wx^T at tA, Wy Wy^T at tB, and
+                // products for C: Mx = Wx Wx^T, My = Wy Wy^T (kept for the iteration), and
                 // hvx[s][i] = sum_a Wx[i][a] gx_s[a] at u4[s N + i], hvy[s][j] = sum_b Wy[j][b] gy_s[b] at u4[(2 + s) N + j]
                 if (c < n) {
                     const int i = c / N, i2 = c % N;
@@ -690,8 +690,8 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         sxx = fma(Wx[i * N + a2], Wx[i2 * N + a2], sxx);
                         syy = fma(Wy[i * N + a2], Wy[i2 * N + a2], syy);
                     }
-                    tA[c] = sxx;
-                    tB[c] = syy;
+                    Mx[c] = sxx;
+                    My[c] = syy;
                 }
                 if (c < 4 * N) {
                     const int s2 = c / N, k = c % N;
@@ -735,7 +735,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         gg0 = fma(g[m], g0[m], gg0);
                         gg1 = fma(g[m], g1[m], gg1);
                     }
-                    const R *Mw = fx ? tB : tA;  // Wy Wy^T along x faces, Wx Wx^T along y faces
+                    const R *Mw = fx ? My : Mx;  // Wy Wy^T along x faces, Wx Wx^T along y faces
 #pragma unroll
                     for (int jj = 0; jj < CW; ++jj) {
                         const int f2 = col0 + jj;
@@ -929,7 +929,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     double arow[N];
                     if (mat >= 0) {
                         const double lam = sm64[(mat >> 1) * 6 + 4 + (mat & 1)];
-                        const R *M = mat < 2 ? tB : tA;  // My for the x faces, Mx for the y faces
+                        const R *M = mat < 2 ? My : Mx;  // My for the x faces, Mx for the y faces
 #pragma unroll
                         for (int j = 0; j < N; ++j)
                             arow[j] = j == row ? fma(lam, double(M[row * N + j]), double(wi2)) : lam * double(M[row * N + j]);
@@ -1166,81 +1166,54 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         tA[c] = z;
                     }
                     group_sync(bar_id, G::GS);
-                    // V0^{-T} z: [(j, a)] = sum_i Wx[i][a] z[(j, i)] (stored at [a][j]), then sum_j Wy[j][b] [(j, a)]
+                    // V0^{-T} z, first pass: [(j, a)] = sum_i Wx[i][a] z[(j, i)] (stored at [a][j]).
+                    // With it, the face rows' u = E0 V0^{-T} z comes from z directly: since
+                    // the rows of E0 are outer products, u on x face s at node k is
+                    // (My rx_s)_k with rx_s[j] = sum_i hvx_s[i] z[(j, i)], and on y face s
+                    // (Mx ry_s)_k with ry_s[i] = sum_j hvy_s[j] z[(j, i)]: first r, here
                     if (c < n) {
                         const int a2 = c % N, j = c / N;
                         R t = R(0);
 #pragma unroll
-                        for (int i = 0; i < N; ++i) t = fma(WxT[a2 * N + i], tA[j * N + i], t);
+                        for (int i = 0; i < N; ++i) t = fma(Wx[i * N + a2], tA[j * N + i], t);
                         tB[a2 * N + j] = t;
                     }
+                    if (c < 4 * N) {
+                        R r4v = R(0);
+                        if (c < 2 * N) {
+                            const R *hv = u4 + (c / N) * N;
+                            const int j = c % N;
+#pragma unroll
+                            for (int i = 0; i < N; ++i) r4v = fma(hv[i], tA[j * N + i], r4v);
+                        } else {
+                            const R *hv = u4 + (c / N) * N;  // hvy_s at u4 + (2 + s) N
+                            const int i = c % N;
+#pragma unroll
+                            for (int j = 0; j < N; ++j) r4v = fma(hv[j], tA[j * N + i], r4v);
+                        }
+                        mu4[c] = r4v;
+                    }
                     group_sync(bar_id, G::GS);
-                    R tv = R(0);
+                    // second pass: t[(b, a)] = sum_j Wy[j][b] [(j, a)]; and u from r
                     if (c < n) {
                         const int a2 = c % N, b = c / N;
+                        R tv = R(0);
 #pragma unroll
-                        for (int j = 0; j < N; ++j) tv = fma(WyT[b * N + j], tB[a2 * N + j], tv);
+                        for (int j = 0; j < N; ++j) tv = fma(Wy[j * N + b], tB[a2 * N + j], tv);
                         tA[c] = tv;
                     }
-                    group_sync(bar_id, G::GS);
-                    // u = E0 t: x faces sum_b Wy[k][b] sum_a gx_s[a] t[(b, a)]; y faces sum_a Wx[k][a] sum_b gy_s[b] t[(b, a)]
                     if (c < 4 * N) {
-                        const int s2 = (c / N) & 1, k = c % N;
+                        const R *Mm = c < 2 * N ? My : Mx;
+                        const R *rv = mu4 + (c / N) * N;
+                        const int k = c % N;
                         R uv = R(0);
-                        if (c < 2 * N) {
-                            const R *g = gx0 + s2 * R4N;
 #pragma unroll
-                            for (int b = 0; b < N; ++b) {
-                                R inner = R(0);
-#pragma unroll
-                                for (int a2 = 0; a2 < N; ++a2) inner = fma(g[a2], tA[b * N + a2], inner);
-                                uv = fma(Wy[k * N + b], inner, uv);
-                            }
-                        } else {
-                            const R *g = gy0 + s2 * R4N;
-#pragma unroll
-                            for (int a2 = 0; a2 < N; ++a2) {
-                                R inner = R(0);
-#pragma unroll
-                                for (int b = 0; b < N; ++b) inner = fma(g[b], tA[b * N + a2], inner);
-                                uv = fma(Wx[k * N + a2], inner, uv);
-                            }
-                        }
-                        u4[c] = uv;
+                        for (int m = 0; m < N; ++m) uv = fma(Mm[k * N + m], rv[m], uv);
+                        uu4[c] = uv;
                     }
                     group_sync(bar_id, G::GS);
-                    if (c < 4 * N) {  // mu = C^{-1} u
-                        R m = R(0);
-#pragma unroll
-                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
-                            const VT cv = *reinterpret_cast<const VT *>(Ci + c * G::CIS + f2);
-                            const VT uv = *reinterpret_cast<const VT *>(u4 + f2);
-#pragma unroll
-                            for (int i = 0; i < VW; ++i)
-                                if (f2 + i < 4 * N) m = fma(VV::at(cv, i), VV::at(uv, i), m);
-                        }
-                        mu4[c] = m;
-                    }
-                    group_sync(bar_id, G::GS);
-                    // t - E0^T mu at particle (a, b)
-                    if (c < n) {
-                        const int a2 = c % N, b = c / N;
-                        R sx0 = R(0), sx1 = R(0), sy0 = R(0), sy1 = R(0);
-#pragma unroll
-                        for (int j = 0; j < N; ++j) {
-                            sx0 = fma(WyT[b * N + j], mu4[j], sx0);
-                            sx1 = fma(WyT[b * N + j], mu4[N + j], sx1);
-                            sy0 = fma(WxT[a2 * N + j], mu4[2 * N + j], sy0);
-                            sy1 = fma(WxT[a2 * N + j], mu4[3 * N + j], sy1);
-                        }
-                        R corr = gx0[a2] * sx0;
-                        corr = fma(gx1[a2], sx1, corr);
-                        corr = fma(gy0[b], sy0, corr);
-                        corr = fma(gy1[b], sy1, corr);
-                        tA[c] = tv - corr;
-                    }
-                    group_sync(bar_id, G::GS);
-                    // V0^{-1}: [(b, i)] = sum_a Wx[i][a] t[(b, a)] (stored at [i][b]), then sum_b Wy[j][b] [(b, i)]
+                    // V0^{-1} t, first pass: [(b, i)] = sum_a Wx[i][a] t[(b, a)] (stored at [i][b]);
+                    // and mu = C^{-1} u
                     if (c < n) {
                         const int i = c % N, b = c / N;
                         R t = R(0);
@@ -1248,12 +1221,39 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         for (int a2 = 0; a2 < N; ++a2) t = fma(Wx[i * N + a2], tA[b * N + a2], t);
                         tB[i * N + b] = t;
                     }
+                    if (c < 4 * N) {
+                        R m = R(0);
+#pragma unroll
+                        for (int f2 = 0; f2 < 4 * N; f2 += VW) {
+                            const VT cv = *reinterpret_cast<const VT *>(Ci + c * G::CIS + f2);
+                            const VT uv = *reinterpret_cast<const VT *>(uu4 + f2);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i)
+                                if (f2 + i < 4 * N) m = fma(VV::at(cv, i), VV::at(uv, i), m);
+                        }
+                        mu4[c] = m;  // r was last read in the previous stage
+                    }
                     group_sync(bar_id, G::GS);
+                    // second pass, less V0^{-1} E0^T mu, which at node (i, j) is
+                    // sum_s (My mu_x,s)_j hvx_s[i] + hvy_s[j] (Mx mu_y,s)_i
                     R d = R(0);
                     if (c < n) {
                         const int i = c % N, j = c / N;
 #pragma unroll
                         for (int b = 0; b < N; ++b) d = fma(Wy[j * N + b], tB[i * N + b], d);
+                        R mx0 = R(0), mx1 = R(0), my0 = R(0), my1 = R(0);
+#pragma unroll
+                        for (int k = 0; k < N; ++k) {
+                            mx0 = fma(My[j * N + k], mu4[k], mx0);
+                            mx1 = fma(My[j * N + k], mu4[N + k], mx1);
+                            my0 = fma(Mx[i * N + k], mu4[2 * N + k], my0);
+                            my1 = fma(Mx[i * N + k], mu4[3 * N + k], my1);
+                        }
+                        R corr = mx0 * u4[i];
+                        corr = fma(mx1, u4[N + i], corr);
+                        corr = fma(u4[2 * N + j], my0, corr);
+                        corr = fma(u4[3 * N + j], my1, corr);
+                        d -= corr;
                         q += d;
                     }
                     publish_maxima(it, d, q);
