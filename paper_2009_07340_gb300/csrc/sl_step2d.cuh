@@ -137,11 +137,13 @@ struct Geo2D {
     // rows of C^{-1} (FP64 N = 10 unpadded: the padding would leave room for
     // one CTA per SM instead of two)
     static constexpr int CIS = sizeof(R) == 8 && N == 10 ? r4(4 * N) : odd16(4 * N);
-    // pivot block of the inversion of C (divides 4N; the published block rows,
-    // 2 CB r4(4N) values, fit in the space of C^{-1}).  Measured on 16 x 16
-    // meshes: 4 x 4 blocks are 3-9 % faster than 2 x 2 for FP32 N >= 8 and
-    // 4-7 % slower in FP64 (its extra FP64 block inversions); below N = 8 a tie.
-    static constexpr int kCB = sizeof(R) == 4 && N >= 8 ? 4 : 2;
+    // pivot block of the inversion of C (divides 4N; the published block rows
+    // fit in the space of C^{-1}).  Measured on 16 x 16 meshes: 4 x 4 blocks
+    // are 3-9 % faster than 2 x 2 for FP32 N = 8, 9, and 4-7 % slower in FP64
+    // (its extra FP64 block inversions); below N = 8 a tie.  From N = 10 the
+    // rows of C are split over two or three threads, each of which inverts
+    // every pivot block: there 2 x 2 blocks are 3-9 % faster.
+    static constexpr int kCB = sizeof(R) == 4 && (N == 8 || N == 9) ? 4 : 2;
     // threads per row of C in its assembly and inversion (measured on 16 x 16
     // meshes in FP32): one up to N = 9, two at N = 10 and 11 (5 and 8 %
     // faster than one), three at N = 12 (7 % faster than one, level with
@@ -764,7 +766,12 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 // double-buffered in the space of C^{-1}, written only after the
                 // last step.
                 constexpr int CB = G::kCB;
-                constexpr int CR = G::r4(QB * CW);  // stride of the published rows (elements of RC)
+                // published rows: column block q at q (CW + GAP), the gap putting the
+                // blocks that threads of one row read at the same time in different banks
+                constexpr int GAP = QB > 1 ? 4 : 0;
+                constexpr int CR = G::r4(QB * (CW + GAP));  // stride of the published rows (elements of RC)
+                auto pcol = [&](int j) { return j + (j / CW) * GAP; };  // column j's place in a published row
+                const int pcol0 = pcol(col0);
                 static_assert(2 * CB * CR * sizeof(RC) <= 4 * N * G::CIS * sizeof(R), "published rows fit in C^{-1}");
                 if (!kOneWarp || wig == 0)  // uniform per warp; above one warp, every thread
 #pragma unroll
@@ -777,7 +784,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             RC v4[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) v4[i] = i < VWC ? creg[jj + i] : RC(0);
-                            *reinterpret_cast<VCT *>(pb + (row - K) * CR + col0 + jj) =
+                            *reinterpret_cast<VCT *>(pb + (row - K) * CR + pcol0 + jj) =
                                 VC::make(v4[0], v4[1], v4[2], v4[3]);
                         }
                     if constexpr (kOneWarp) __syncwarp();
@@ -787,7 +794,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
 #pragma unroll
                         for (int t2 = 0; t2 < CB; ++t2)
 #pragma unroll
-                            for (int m = 0; m < CB; ++m) Pm[t2][m] = pb[t2 * CR + K + m];
+                            for (int m = 0; m < CB; ++m) Pm[t2][m] = pb[t2 * CR + pcol(K) + m];
 #pragma unroll
                         for (int p = 0; p < CB; ++p) {
                             const RC d = RC(1) / Pm[p][p];
@@ -808,7 +815,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             RC other = RC(0), own = RC(0);
 #pragma unroll
                             for (int t2 = 0; t2 < CB; ++t2) {
-                                other = fma(-sgn * pb[t2 * CR + row], Pm[t2][m], other);
+                                other = fma(-sgn * pb[t2 * CR + pcol(row)], Pm[t2][m], other);
                                 own = row == K + t2 ? Pm[t2][m] : own;
                             }
                             w[m] = pivot ? own : other;
@@ -817,7 +824,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         for (int jj = 0; jj < CW; jj += VWC) {
                             VCT v[CB];
 #pragma unroll
-                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VCT *>(pb + m * CR + col0 + jj);
+                            for (int m = 0; m < CB; ++m) v[m] = *reinterpret_cast<const VCT *>(pb + m * CR + pcol0 + jj);
 #pragma unroll
                             for (int i = 0; i < VWC; ++i) {
                                 const int j = col0 + jj + i;
