@@ -160,7 +160,14 @@ struct Geo2D {
     static_assert((4 * N) % kCB == 0 && 2 * kCB * r4(4 * N) <= 4 * N * CIS, "pivot blocks of C");
     // the mixed form's FP64 factor (MODE 3), per group after all groups (floats):
     // [4][N][N] and [4][2][N] and [8][N] doubles, 88 doubles, [4][N][N] + [4N][4] + 56 floats
-    static constexpr int kX3 = FASTONLY ? r4(2 * (4 * N * N + 8 * N + 8 * N + 88) + 4 * N * N + 16 * N + 56) : 0;
+    // (FP64 kernels: [4][N][N], [4][2][N], [8][N], 88, then [4N][4] and 56 doubles, the
+    // rounded copy of the inverses being the inverses themselves)
+    static constexpr int kX3 = !FASTONLY ? 0
+                               : sizeof(R) == 4 ? r4(2 * (4 * N * N + 8 * N + 8 * N + 88) + 4 * N * N + 16 * N + 56)
+                                                : r4(4 * N * N + 16 * N + 88 + 16 * N + 56);
+    // the FP64 kernels invert C by the same structure (about (4N)^3 / 8 FP64
+    // FMA less), except at N = 5, 7, 10, where its buffers would cost a CTA per SM
+    static constexpr bool kStructC64 = sizeof(R) == 8 && N != 5 && N != 7 && N != 10;
     // rhs, vec and res hold one P4-long array per field
     static constexpr int kRows0 = P * LD;
     // the fast-path kernel holds no stacked rows: only the basis values and its buffers
@@ -705,7 +712,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     u4[c] = v;
                 }
                 group_sync(bar_id, G::GS);
-                if constexpr (MODE != 3) {
+                if constexpr (!(MODE == 3 || (MODE == 1 && G::kStructC64))) {
                 // C's rows are held by QB threads each (thread c: row c / QB, its
                 // columns [q CW, q CW + CW), q = c % QB), which assemble them from
                 // the 1D products and invert C in place (C is symmetric positive
@@ -861,7 +868,8 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             *reinterpret_cast<VT *>(Ci + row * G::CIS + col0 + jj) = VV::make(v4[0], v4[1], v4[2], v4[3]);
                         }
                 } else {
-                // MODE 3: C^{-1} from its structure, the factors in FP64.  C =
+                // MODE 3 (and the FP64 kernels): C^{-1} from its structure, the factors
+                // in FP64.  C =
                 // w^-2 I + [[Gx (x) My, Cxy], [Cxy^T, Gy (x) Mx]] with Gx = [gx_s . gx_s']
                 // (2 x 2), My = Wy Wy^T and Cxy of rank 4 (its (s, s') blocks are
                 // hvy_s' hvx_s^T).  The Kronecker blocks invert through the
@@ -872,7 +880,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 // P = A^T Cxx^{-1} A, Qm = B^T Cyy^{-1} B (Cxy = A B^T) and
                 // T = P^{-1} - Qm.  The N x N and 4 x 4 inverses and the products
                 // that form P and Qm run in FP64; C^{-1}'s entries are assembled
-                // in FP32 from them.  Same result as the inverse of the dense C
+                // from them in the kernel's precision.  Same result as the inverse of the dense C
                 // (checked in a NumPy model with these index conventions).
                 double *xd = reinterpret_cast<double *>(tab + ((G::kTables + 3) & ~3) + G::GPC * G::kGroup +
                                                         grp * G::kX3);
@@ -880,9 +888,10 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                 double *piv64 = Ainv + 4 * N * N;  // [4][2][N] pivot rows of their Gauss-Jordan
                 double *yz = piv64 + 8 * N;        // [8][N]: y_{t,tp} = Ainv_t hvy_tp, z_{t,tg} = Ainv_{2+t} hvx_tg
                 double *sm64 = yz + 8 * N;         // Qx [2][2], lx [2], Qy [2][2], ly [2], then warp-0 scratch
-                float *A32 = reinterpret_cast<float *>(sm64 + 88);  // [4][N][N] Ainv rounded
-                float *Z32 = A32 + 4 * N * N;      // [4N][4]: rows of Cxx^{-1} A (x faces), Cyy^{-1} B (y faces)
-                float *s32 = Z32 + 16 * N;         // Qx [4], Qy [4], Mxx [16], M1 [16], Ti [16]
+                constexpr bool kAlias = std::is_same<R, double>::value;  // FP64: Ainv is its own copy
+                R *A32 = kAlias ? reinterpret_cast<R *>(Ainv) : reinterpret_cast<R *>(sm64 + 88);  // [4][N][N] Ainv in R
+                R *Z32 = kAlias ? reinterpret_cast<R *>(sm64 + 88) : A32 + 4 * N * N;  // [4N][4]: rows of Cxx^{-1} A, Cyy^{-1} B
+                R *s32 = Z32 + 16 * N;             // Qx [4], Qy [4], Mxx [16], M1 [16], Ti [16]
                 const R *hvx = u4, *hvy = u4 + 2 * N;  // hvx[s N + i] = (Wx gx_s)_i, hvy[s N + j] = (Wy gy_s)_j
                 // GB300 runs FP64 at 2 lanes per clock per SM, so a warp-wide FP64
                 // instruction costs the same whatever its active lanes: the small
@@ -918,10 +927,10 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                         q[3] = cs;
                         q[4] = l0;
                         q[5] = l1;
-                        s32[4 * d + 0] = float(cs);
-                        s32[4 * d + 1] = float(sn);
-                        s32[4 * d + 2] = float(-sn);
-                        s32[4 * d + 3] = float(cs);
+                        s32[4 * d + 0] = R(cs);
+                        s32[4 * d + 1] = R(sn);
+                        s32[4 * d + 2] = R(-sn);
+                        s32[4 * d + 3] = R(cs);
                     }
                 }
                 group_sync(bar_id, G::GS);
@@ -966,7 +975,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
 #pragma unroll
                         for (int j = 0; j < N; ++j) {
                             Ainv[(mat * N + row) * N + j] = arow[j];
-                            A32[(mat * N + row) * N + j] = float(arow[j]);
+                            if constexpr (!kAlias) A32[(mat * N + row) * N + j] = R(arow[j]);
                         }
                 }
                 group_sync(bar_id, G::GS);
@@ -1033,15 +1042,15 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
 #pragma unroll
                     for (int m = 0; m < 4; ++m) mxx = fma(QT[4 * i4 + m], Qm[4 * m + j4], mxx);
                     if (lane < 16) {
-                        s32[8 + e] = float(mxx);                                   // Mxx = Qm + Qm T^-1 Qm
-                        s32[24 + e] = float((i4 == j4 ? 1.0 : 0.0) + QT[e]);      // M1 = I + Qm T^-1
-                        s32[40 + e] = float(Pm[e]);                                // T^-1
+                        s32[8 + e] = R(mxx);                                   // Mxx = Qm + Qm T^-1 Qm
+                        s32[24 + e] = R((i4 == j4 ? 1.0 : 0.0) + QT[e]);      // M1 = I + Qm T^-1
+                        s32[40 + e] = R(Pm[e]);                                // T^-1
                     }
                 }
                 if (c < 4 * N) {  // row c of Cxx^{-1} A (x faces) or Cyy^{-1} B (y faces)
                     const int f = c, s = (f / N) & 1, k = f % N;
                     const double *Qd = f < 2 * N ? sm64 : sm64 + 6;
-                    float zr[4];
+                    R zr[4];
 #pragma unroll
                     for (int a1 = 0; a1 < 2; ++a1)
 #pragma unroll
@@ -1051,56 +1060,70 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             for (int t = 0; t < 2; ++t)
                                 acc = f < 2 * N ? fma(Qd[2 * s + t] * Qd[2 * a1 + t], yz[(2 * t + a2) * N + k], acc)
                                                 : fma(Qd[2 * s + t] * Qd[2 * a2 + t], yz[(4 + 2 * t + a1) * N + k], acc);
-                            zr[2 * a1 + a2] = float(acc);
+                            zr[2 * a1 + a2] = R(acc);
                         }
-                    *reinterpret_cast<float4 *>(Z32 + 4 * f) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+#pragma unroll
+                    for (int i = 0; i < 4; i += VW)
+                        *reinterpret_cast<VT *>(Z32 + 4 * f + i) = VV::make(zr[i], zr[(i + 1) & 3], zr[(i + 2) & 3], zr[(i + 3) & 3]);
                 }
                 group_sync(bar_id, G::GS);
-                if (c < 4 * N) {  // row c of C^{-1}, assembled in FP32
+                auto load4 = [&](const R *p, R (&z)[4]) {  // four values from a 16-byte-aligned row
+#pragma unroll
+                    for (int i = 0; i < 4; i += VW) {
+                        const VT v = *reinterpret_cast<const VT *>(p + i);
+#pragma unroll
+                        for (int i2 = 0; i2 < VW; ++i2) z[i + i2] = VV::at(v, i2);
+                    }
+                };
+                if (c < 4 * N) {  // row c of C^{-1}, assembled in the kernel's precision
                     const int f = c, s = (f / N) & 1, k = f % N;
                     const bool fx = f < 2 * N;
-                    const float4 zv = *reinterpret_cast<const float4 *>(Z32 + 4 * f);
-                    const float zr[4] = {zv.x, zv.y, zv.z, zv.w};
-                    const float *Mxx = s32 + 8, *M1 = s32 + 24, *Tinv = s32 + 40;
-                    float rr[4], rp[4];  // the row's coefficients for its own block and the other
+                    R zr[4];
+                    load4(Z32 + 4 * f, zr);
+                    const R *Mxx = s32 + 8, *M1 = s32 + 24, *Tinv = s32 + 40;
+                    R rr[4], rp[4];  // the row's coefficients for its own block and the other
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        float a1 = 0.f, a2 = 0.f;
+                        R a1 = R(0), a2 = R(0);
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
-                            a1 = fmaf(zr[m], fx ? Mxx[4 * m + j] : Tinv[4 * m + j], a1);
-                            a2 = fmaf(fx ? zr[m] : zr[m], fx ? M1[4 * m + j] : M1[4 * j + m], a2);
+                            a1 = fma(zr[m], fx ? Mxx[4 * m + j] : Tinv[4 * m + j], a1);
+                            a2 = fma(zr[m], fx ? M1[4 * m + j] : M1[4 * j + m], a2);
                         }
                         rr[j] = a1;
                         rp[j] = -a2;
                     }
-                    const float *Q32 = fx ? s32 : s32 + 4;
-                    float cq[2][2];  // Q[s][t] Q[s2][t]
+                    const R *Q32 = fx ? s32 : s32 + 4;
+                    R cq[2][2];  // Q[s][t] Q[s2][t]
 #pragma unroll
                     for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
                         for (int t = 0; t < 2; ++t) cq[s2][t] = Q32[2 * s + t] * Q32[2 * s2 + t];
-                    const float *Ab = A32 + (fx ? 0 : 2) * N * N + k * N;  // row k of the block's inverses t = 0, 1
+                    const R *Ab = A32 + (fx ? 0 : 2) * N * N + k * N;  // row k of the block's inverses t = 0, 1
 #pragma unroll
                     for (int f2 = 0; f2 < 4 * N; f2 += 4) {
-                        float v4[4];
+                        R v4[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int g2 = f2 + i, s2 = (g2 / N) & 1, k2 = g2 % N;
                             const bool same = fx == (g2 < 2 * N);
-                            const float4 z2 = *reinterpret_cast<const float4 *>(Z32 + 4 * g2);
-                            const float *cf = same ? rr : rp;
-                            float v = cf[0] * z2.x;
-                            v = fmaf(cf[1], z2.y, v);
-                            v = fmaf(cf[2], z2.z, v);
-                            v = fmaf(cf[3], z2.w, v);
+                            R z2[4];
+                            load4(Z32 + 4 * g2, z2);
+                            const R *cf = same ? rr : rp;
+                            R v = cf[0] * z2[0];
+                            v = fma(cf[1], z2[1], v);
+                            v = fma(cf[2], z2[2], v);
+                            v = fma(cf[3], z2[3], v);
                             if (same) {
-                                v = fmaf(cq[s2][0], Ab[k2], v);
-                                v = fmaf(cq[s2][1], Ab[N * N + k2], v);
+                                v = fma(cq[s2][0], Ab[k2], v);
+                                v = fma(cq[s2][1], Ab[N * N + k2], v);
                             }
                             v4[i] = v;
                         }
-                        *reinterpret_cast<float4 *>(Ci + f * G::CIS + f2) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+#pragma unroll
+                        for (int i = 0; i < 4; i += VW)
+                            *reinterpret_cast<VT *>(Ci + f * G::CIS + f2 + i) =
+                                VV::make(v4[i], v4[(i + 1) & 3], v4[(i + 2) & 3], v4[(i + 3) & 3]);
                     }
                 }
                 }
@@ -1867,7 +1890,8 @@ template <int N, typename R, int NCOMP, int MODE>
 size_t smem2d()
 {
     using G = Geo2D<N, R, NCOMP, MODE != 2>;
-    return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * (G::kGroup + (MODE == 3 ? G::kX3 : 0)));
+    constexpr bool kX = MODE == 3 || (MODE == 1 && G::kStructC64);
+    return sizeof(R) * (((G::kTables + 3) & ~3) + size_t(G::GPC) * (G::kGroup + (kX ? G::kX3 : 0)));
 }
 
 // One phase over groups [g0, g1): for orders with the fast path, the fast
