@@ -71,6 +71,14 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Quotients inside the fast path's preconditioner (the tensor factors Wx, Wy,
+// the face basis and the inverse of C): FP32 takes the fast approximate
+// division (__fdividef, within a few ulp for these magnitudes), which changes
+// only how fast the iteration converges, never what it converges to; FP64
+// divides exactly.
+__device__ __forceinline__ float pdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pdiv(double a, double b) { return a / b; }
+
 // 16-byte vectors of R for shared-memory rows (every row and sub-array of a
 // group starts on a 16-byte boundary; rows are LD >= n (rounded to 4) long).
 template <typename R>
@@ -574,7 +582,9 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     ny *= sZ[i * N + m] - dby[m];
                     dy_ *= sZ[a2 * N + m] + (dby[a2] - dby[m]);
                 }
-            const R wx = nx / dx_, wy = ny / dy_;
+            // the preconditioner's factors: an FP32 quotient within a few ulp serves
+            // as well as the correctly rounded one (the iteration's residual decides)
+            const R wx = pdiv(nx, dx_), wy = pdiv(ny, dy_);
             Wx[i * N + a2] = wx;
             Wy[i * N + a2] = wy;
         }
@@ -589,7 +599,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                     num *= X[m] - db[m];
                     den *= sZ[a2 * N + m] + (db[a2] - db[m]);
                 }
-            gx0[s2 * R4N + a2] = num / den;
+            gx0[s2 * R4N + a2] = pdiv(num, den);
         }
         group_sync(bar_id, G::GS);
         {
@@ -804,7 +814,7 @@ __device__ __forceinline__ void sl2d_cta(const Step2DArgs &a0, const Step2DArgs 
                             for (int m = 0; m < CB; ++m) Pm[t2][m] = pb[t2 * CR + pcol(K) + m];
 #pragma unroll
                         for (int p = 0; p < CB; ++p) {
-                            const RC d = RC(1) / Pm[p][p];
+                            const RC d = pdiv(RC(1), Pm[p][p]);
 #pragma unroll
                             for (int m = 0; m < CB; ++m) Pm[p][m] = m == p ? d : Pm[p][m] * d;
 #pragma unroll
